@@ -1,0 +1,373 @@
+#!/usr/bin/env python
+"""Benchmark of the TNS amplitude path on one GB300 per rank.
+
+Workload (one "step"): the 53-qubit staggered diagonal-coupled grid (6 rows x
+9 columns minus one seeded site), 10 cycles ABCDCDABAB, two-sided evolution
+split after cycle 5, bonds truncated to chi = 64 or singular values below
+1e-8 s_0; one step = the ket evolution + the batched bra evolution, overlap
+network, sliced contraction and FP64 slice sum for 65536 seeded random
+bitstrings. Synthetic seeded inputs stand in for the Sycamore layout and
+circuits, which are not available.
+
+Prints ONE JSON line (rank 0). ``--impl reference`` times the CPU oracle
+instead (the reference arm of this benchmark).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "amplitudes/s @ rel.err≤1e-5 vs FP64 (53q d10); contraction TFLOP/s; p99 latency"
+UNIT = "amplitudes/s"
+WORKLOAD = ("53-qubit staggered grid (6x9 minus 1 seeded site), 10 cycles ABCDCDABAB, split 5, chi 64, "
+            "cutoff 1e-8, 65536 random bitstrings per step")
+TOL = 1e-5
+NOMINAL = {"tf32_over_bf16": 1.1 / 2.25, "fp32_simt_tflops": 152 * 128 * 2 * 2.07e9 / 1e12,
+           "fp64_tflops": 1.25}
+
+
+def env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return dict(hbm_gbs=float(d["hbm_gbs"]), bf16_tflops=float(d["bf16_tflops"]),
+                    bf16_tflops_sustained=float(d.get("bf16_tflops_sustained", d["bf16_tflops"])), source="measured")
+    return dict(hbm_gbs=6800.0, bf16_tflops=1900.0, bf16_tflops_sustained=1700.0, source="fallback")
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle leg (also the reference arm)
+# ---------------------------------------------------------------------------
+def _oracle_worker(payload):
+    """Runs in a spawned process with single-threaded BLAS: oracle amplitudes for a few bitstrings."""
+    import numpy as np  # noqa: F401
+    import gen
+    from oracle import tns
+    name, idx, n_bits, seed_off = payload
+    w = gen.workload(name, n_bits=n_bits)
+    bits = _rank_bits(w, seed_off)[list(idx)]
+    g1, g2 = tns.split_gates(w.gates, w.split)
+    ket = tns.evolve_ket(w.graph.n, w.graph.edges, g1, w.chi, w.cutoff)
+    t0 = time.perf_counter()
+    a, _ = tns.amplitudes(w.graph.n, w.graph.edges, w.gates, bits, w.split, w.chi, w.cutoff, ket=ket)
+    return list(idx), [complex(x) for x in a], time.perf_counter() - t0
+
+
+def _rank_bits(w, seed_off):
+    import gen
+    if seed_off == 0:
+        return w.bits
+    return gen.bitstrings(w.graph.n, len(w.bits), gen.rng(gen.BASE_SEED + 3 + 7919 * seed_off, 2))
+
+
+def cpu_oracle(name, n_bits, sample, seed_off=0, cores=None):
+    """Time the oracle (as it stands) on `sample` bitstrings over a spawned process pool."""
+    import multiprocessing as mp
+    import numpy as np
+    cores = cores or os.cpu_count() or 1
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+    per = max(1, math.ceil(sample / cores))
+    chunks = [(name, tuple(range(i, min(i + per, sample))), n_bits, seed_off) for i in range(0, sample, per)]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(min(cores, len(chunks))) as pool:
+        pool.map(_oracle_worker, [(name, (0,), n_bits, seed_off)] * min(cores, len(chunks)))   # warm imports
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_worker, chunks)
+        wall = time.perf_counter() - t0
+    amps = np.zeros(sample, dtype=np.complex128)
+    busy = 0.0
+    for idx, a, dt in res:
+        amps[list(idx)] = a
+        busy += dt
+    return dict(value=sample / wall, single_thread_value=sample / busy, cores=min(cores, len(chunks)),
+                wall_s=wall, cpu_s=busy, amps=amps)
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    sample = args.ref_sample
+    vals = []
+    for _ in range(args.warmup):
+        cpu_oracle("syc53", args.bits, max(2, sample // 8))
+    t_all = 0.0
+    for _ in range(args.steps):
+        r = cpu_oracle("syc53", args.bits, sample)
+        vals.append(r)
+        t_all += r["wall_s"]
+    value = sum(r["value"] for r in vals) / len(vals)
+    cores = vals[0]["cores"]
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000 * t_all / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample_per_step": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{sample} of the workload's bitstrings per step (ket evolution outside)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = [l.split(",") for l in open(self.f.name).read().splitlines() if l.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = max(mx, float(r[2]))
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def traffic_record(kind):
+    """dram bytes per launch of `kind` from the committed ncu summary, if the kernel source is unchanged."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    rec = d.get(kind)
+    if not rec or rec.get("source_sha") != source_sha():
+        return None
+    return rec
+
+
+def source_sha():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2011_02621_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".h", ".cpp")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="tf32x3", choices=["fp64", "fp32", "tf32", "tf32x3", "bf16x3"])
+    ap.add_argument("--bits", type=int, default=65536)
+    ap.add_argument("--check-bits", type=int, default=1024, help="bitstrings re-run on the FP64 path")
+    ap.add_argument("--cpu-sample", type=int, default=192, help="bitstrings timed on the CPU oracle")
+    ap.add_argument("--ref-sample", type=int, default=64, help="reference arm: oracle bitstrings per step")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--profile-only", action="store_true", help="short run for ncu captures")
+    args = ap.parse_args()
+    rank, world, local = env_int("RANK", 0), env_int("WORLD_SIZE", 1), env_int("LOCAL_RANK", 0)
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import numpy as np
+    import torch
+    import gen
+    assert args.warmup >= 1
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", rank=rank, world_size=world, device_id=torch.device("cuda", local))
+    from paper_2011_02621_gb300 import build
+    if rank == 0:
+        build.build()
+    if dist:
+        dist.barrier()
+    from paper_2011_02621_gb300 import tn
+
+    w = gen.workload("syc53", n_bits=args.bits)
+    bits_np = _rank_bits(w, rank)                 # weak scaling: each rank its own bitstrings
+    B = len(bits_np)
+    packed = tn.pack_bits(bits_np)
+    c = tn.tn_build(w.graph.n, w.graph.edges, w.gates)
+    tn.tn_evolve_two_sided(c, w.split, w.chi, w.cutoff)
+    plan = tn.tn_path(c, mem_budget_bytes=32.0 * 2 ** 30)
+    info = plan.info
+    stream = torch.cuda.current_stream()
+    bits_dev = torch.from_numpy(packed.view(np.int64).copy()).cuda()
+    out_dev = torch.empty(B, dtype=torch.complex128, device="cuda")
+    bits_pin = torch.from_numpy(packed.view(np.int64).copy()).pin_memory()
+    out_pin = torch.empty(B, dtype=torch.complex128).pin_memory()
+    flush = torch.empty(256 * 2 ** 20 // 4, dtype=torch.float32, device="cuda")   # 256 MB > 129 MB L2
+
+    def step(bits, out):
+        tn.tn_evolve_two_sided(c, w.split, w.chi, w.cutoff, stream)
+        tn.tn_amplitudes(plan, bits, args.prec, out=out, stream=stream)
+
+    def timed(steps, bits, out, profile=False):
+        total = 0.0
+        for _ in range(steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            if dist:
+                dist.barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step(bits, out)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            total += e0.elapsed_time(e1) / 1000.0
+        return total
+
+    for _ in range(args.warmup):
+        step(bits_dev, out_dev)
+    torch.cuda.synchronize()
+    if args.profile_only:
+        step(bits_dev, out_dev)
+        torch.cuda.synchronize()
+        if rank == 0:
+            print(json.dumps({"profile_only": True, "info": info}))
+        return 0
+
+    clocks = Clocks(local)
+    clocks.start()
+    tn.tn_launch_count(reset=True)
+    tn.tn_profile_enable(True)
+    t_dev = timed(args.steps, bits_dev, out_dev)
+    prof = tn.tn_profile_read()
+    tn.tn_profile_enable(False)
+    launches = tn.tn_launch_count() // args.steps
+    clk = clocks.stop()
+    a_tc = out_dev.cpu().numpy()
+    # end to end through the public call with pinned host buffers (copies inside the timed region)
+    timed(1, bits_pin, out_pin)
+    t_e2e = timed(args.steps, bits_pin, out_pin)
+    if dist:
+        t = torch.tensor([t_dev, t_e2e], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_dev, t_e2e = float(t[0]), float(t[1])
+
+    # accuracy: re-run a sample on the FP64 path; only amplitudes within 1e-5 of FP64 count
+    nchk = min(args.check_bits, B)
+    a64 = tn.tn_amplitudes(plan, packed[:nchk], "fp64")
+    rms = float(np.sqrt(np.mean(np.abs(a64) ** 2)))
+    rel = np.abs(a_tc[:nchk] - a64) / rms
+    ok_frac = float(np.mean(rel <= TOL))
+    if dist:
+        t = torch.tensor([ok_frac], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MIN)
+        ok_frac = float(t[0])
+    value = world * B * args.steps / t_dev * ok_frac
+    e2e_value = world * B * args.steps / t_e2e * ok_frac
+    if rank != 0:
+        return 0
+
+    pk = peaks()
+    dom = max(prof.items(), key=lambda kv: kv[1]["ms"])
+    kind, rec = dom
+    per_launch_s = rec["ms"] / 1000.0 / max(rec["launches"], 1)
+    bytes_pl = rec["bytes"] / max(rec["launches"], 1)
+    flops_pl = rec["flops"] / max(rec["launches"], 1)
+    if "tcgen05" in kind:
+        tf_peak = pk["bf16_tflops_sustained"] * NOMINAL["tf32_over_bf16"]
+        ridge = tf_peak * 1e12 / (pk["hbm_gbs"] * 1e9)
+        tensor_bound = flops_pl / max(bytes_pl, 1) > ridge
+    else:
+        tensor_bound = False
+    if tensor_bound:
+        roof = {"bound": "tensor", "achieved": flops_pl / per_launch_s / 1e12, "peak": tf_peak, "unit": "TFLOP/s"}
+    else:
+        roof = {"bound": "hbm", "achieved": bytes_pl / per_launch_s / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    tr = traffic_record(kind)
+    roof["traffic"] = tr["dram_bytes_per_launch"] if tr else None
+    roof.update({"kernel": kind, "launches_per_step": rec["launches"] / args.steps,
+                 "algorithmic_bytes_per_launch": bytes_pl, "algorithmic_flops_per_launch": flops_pl,
+                 "avg_launch_ms": per_launch_s * 1000, "peak_source": pk["source"] + " (sustained for tensor)"})
+    kernels = {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps,
+                   "GB/s": v["bytes"] / max(v["ms"], 1e-9) / 1e6, "TFLOP/s": v["flops"] / max(v["ms"], 1e-9) / 1e9}
+               for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000 * t_dev / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp64": "c128", "fp32": "c64"}.get(args.prec, "c64/" + args.prec),
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "bitstrings_per_gpu": B, "precision": args.prec,
+                   "l2": "256 MB buffer written between timed steps; intermediates exceed L2",
+                   "plan": {k: info[k] for k in ("n_steps", "n_cuts", "n_slices", "cmacs", "flops", "bytes_c64",
+                                                 "max_intermediate", "chunk_bitstrings", "max_rank_used")}},
+        "contraction_tflops": world * B * args.steps * info["flops"] / t_dev / 1e12,
+        "accuracy": {"checked": nchk, "within_1e-5": ok_frac, "max_rel_err_vs_fp64": float(rel.max())},
+        "roofline": roof,
+        "kernels": kernels,
+        "gpu_launches": launches,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(packed.nbytes),
+                "d2h_bytes_per_step": int(B * 16)},
+        "clocks": clk,
+    }
+    if not args.no_cpu and world == 1:
+        cs = min(args.cpu_sample, B)
+        r = cpu_oracle("syc53", args.bits, cs)
+        err = np.abs(a_tc[:cs] - r["amps"]) / float(np.sqrt(np.mean(np.abs(r["amps"]) ** 2)))
+        line["cpu_baseline"] = {"value": r["value"], "unit": UNIT, "cores": r["cores"], "kind": "oracle",
+                                "sample": f"first {cs} of the 65536 bitstrings (ket evolution outside the timing)",
+                                "single_thread_value": r["single_thread_value"], "wall_s": r["wall_s"]}
+        line["oracle_check"] = {"bitstrings": cs, "max_rel_err": float(err.max())}
+    print(json.dumps(line))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,253 @@
+/*
+ * tn.h -- C ABI of the GB300 tensor-network-states amplitude library.
+ *
+ * The library computes amplitudes a(s) = <s| U |0...0> of a quantum circuit U
+ * on an arbitrary connected qubit graph with the tensor-network-states method
+ * of Guo, Zhao and Huang (arXiv:2011.02621):
+ *
+ *   tn_build             graph + gate list (problem statement; Eq. gatesplit)
+ *   tn_evolve_two_sided  two-sided evolution with SVD compression
+ *                        (Eqs. result1, result2, svd, svd2; Fig. 2a)
+ *   tn_path              cuts + contraction path by Algorithm 1 (supplement)
+ *   tn_amplitudes        batched bra evolution, overlap network (Eq. overlap),
+ *                        sliced path-ordered contraction, sum over slices
+ *
+ * plus a serving loop (tn_server_*) that batches amplitude requests for
+ * resident plans.
+ *
+ * Conventions shared by every call:
+ *  - Every call returns a tn_status; nothing is thrown across the ABI.
+ *    tn_last_error() gives a thread-local message for the last failure.
+ *  - Inputs are copied during the call; the caller keeps ownership of every
+ *    pointer it passes. Handles are owned by the library and released with
+ *    the matching tn_*_free.
+ *  - Device memory is obtained through the caller's tn_allocator when one is
+ *    given (e.g. PyTorch's caching allocator), else with cudaMalloc / cudaFree.
+ *  - Streams are the caller's (a cudaStream_t passed as void*; NULL = the
+ *    legacy default stream). Work on one tn_plan must be serialised by the
+ *    caller (one stream, or host synchronisation between calls): the plan
+ *    owns a single workspace.
+ *  - Asynchronous CUDA errors surface as TN_ERR_CUDA at the next call that
+ *    synchronises. A bounded device-side wait that expires gives
+ *    TN_ERR_TIMEOUT.
+ *  - The library needs a CUDA device of compute capability 10.3 (sm_103a)
+ *    for every call that touches the device; there is no CPU fallback.
+ *    tn_path_search and tn_gate_split are host-only.
+ */
+#ifndef TN_H
+#define TN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TN_OK = 0,
+  TN_ERR_ARG = 1,        /* bad argument (NULL, negative size, out of range) */
+  TN_ERR_GRAPH = 2,      /* graph disconnected, gate on a non-edge, qubit out of range */
+  TN_ERR_OOM = 3,        /* allocator returned NULL or admission refused */
+  TN_ERR_NO_PATH = 4,    /* Algorithm 1 found no path within its limits */
+  TN_ERR_STATE = 5,      /* call order (e.g. tn_path before tn_evolve_two_sided) */
+  TN_ERR_CUDA = 6,       /* a CUDA runtime error */
+  TN_ERR_TIMEOUT = 7,    /* a bounded wait expired */
+  TN_ERR_UNSUPPORTED = 8 /* shape outside the implemented limits */
+} tn_status;
+
+typedef struct { double re, im; } tn_c128;
+
+/* Qubit graph G = {V, E} (paper: lattice geometry paragraph). Qubits are
+ * 0..n_qubits-1; edges[2*i], edges[2*i+1] are the endpoints of edge i (its id
+ * is i). The graph must be connected and simple. */
+typedef struct {
+  int32_t n_qubits;
+  int32_t n_edges;
+  const int32_t *edges;
+} tn_graph;
+
+/* One gate. arity 1: m[0..3] is the 2x2 matrix (row-major, rows = outputs).
+ * arity 2: m[0..15] is the 4x4 matrix in the basis |q[0] q[1]>, q[0] the
+ * high bit; {q[0], q[1]} must be an edge. cycle >= 1 orders the gates into
+ * cycles for the two-sided split; gates are applied in array order. */
+typedef struct {
+  int32_t cycle;
+  int32_t arity;
+  int32_t q[2];
+  tn_c128 m[16];
+} tn_gate;
+
+/* Device allocator. alloc returns device memory of `bytes` usable on
+ * `stream` (NULL on failure); free releases it (stream-ordered). */
+typedef struct {
+  void *(*alloc)(size_t bytes, void *stream, void *ctx);
+  void (*free)(void *ptr, size_t bytes, void *stream, void *ctx);
+  void *ctx;
+} tn_allocator;
+
+/* Arithmetic of the contraction GEMMs (the evolution SVDs, the truncation
+ * decision and the cross-slice sum are always FP64). */
+typedef enum {
+  TN_FP64 = 0,   /* complex128 tensors, FP64 SIMT GEMMs */
+  TN_FP32 = 1,   /* complex64 tensors, FP32 SIMT GEMMs */
+  TN_TF32 = 2,   /* complex64 tensors, single-pass TF32 tcgen05 GEMMs, FP32 accumulate */
+  TN_TF32X3 = 3, /* complex64, compensated hi/lo TF32 (3 products), FP32 accumulate */
+  TN_BF16X3 = 4  /* complex64, compensated hi/lo BF16 (3 products), FP32 accumulate */
+} tn_precision;
+
+typedef struct tn_circuit tn_circuit;
+typedef struct tn_plan tn_plan;
+
+/* Options of tn_path (supplement: Assumptions 1-3, Algorithm 1; cutting). */
+typedef struct {
+  int32_t max_rank;      /* M of Assumption 2 (max open legs of an intermediate);
+                            0 = smallest M >= max degree that completes within max_states */
+  int32_t boundary_only; /* 1 = Assumption 1 (start at nodes of degree < max degree); 0 = any node */
+  int32_t connected;     /* 1 = Assumption 3 (almost-connected partial paths); 0 = unconstrained */
+  int64_t max_states;    /* cap on Algorithm 1 expansions; 0 = 4,000,000 */
+  int32_t n_cuts;        /* -1 = automatic (fit max_intermediate); >= 0 = this many cuts */
+  const int32_t *cut_edges; /* explicit cut list (edge ids); overrides n_cuts when n_cut_edges > 0 */
+  int32_t n_cut_edges;
+  int64_t max_intermediate; /* automatic cuts keep every intermediate <= this many elements
+                               per (bitstring, slice); 0 = 2^24 */
+  double mem_budget_bytes;  /* workspace budget of tn_amplitudes; 0 = 8 GiB */
+} tn_path_opts;
+
+/* Summary of a plan. All counts are per amplitude unless stated. */
+typedef struct {
+  int32_t n_qubits;
+  int32_t n_steps;            /* pairwise contraction steps (n_qubits - 1) */
+  int32_t n_cuts;
+  int64_t n_slices;           /* product of the cut edges' dimensions */
+  double score;               /* Algorithm 1 score of the path (complex MACs per slice) */
+  double cmacs;               /* complex multiply-adds over all steps and slices */
+  double flops;               /* 8 * cmacs (real flops) */
+  double bytes_c64;           /* algorithmic bytes: sum over steps of 8*(M*K + M*N), times slices */
+  int64_t max_intermediate;   /* largest intermediate, elements per (bitstring, slice) */
+  int64_t states_expanded;    /* Algorithm 1 pops */
+  int32_t max_rank_used;      /* M that Algorithm 1 ran with */
+  int32_t chunk_bitstrings;   /* bitstrings per device batch */
+  int64_t workspace_bytes;    /* device workspace for the widest precision */
+} tn_plan_info;
+
+/* Build a circuit: validates the graph (connected, simple, endpoints in
+ * range) and the gates (2-qubit gates only on edges), and copies both.
+ * Host only; no device memory is touched. `alloc` may be NULL.
+ * Errors: TN_ERR_ARG, TN_ERR_GRAPH. */
+tn_status tn_build(const tn_graph *g, const tn_gate *gates, int64_t n_gates,
+                   const tn_allocator *alloc, tn_circuit **out);
+
+/* Two-sided evolution (Fig. 2a): gates of cycles 1..split_cycle act on
+ * |0...0> (the ket half, evolved now on the device in FP64 by
+ * Eqs. result1/result2 + svd/svd2); gates of cycles split_cycle+1.. are
+ * recorded as the bra program (their transposes, last to first) that
+ * tn_amplitudes runs per bitstring. Single-qubit gates are fused into the
+ * next two-qubit gate on that qubit in each half's processing order.
+ * Compression keeps singular values > cutoff_rel * s_0, at most chi_max
+ * (0 = no cap); bond shapes are the static structural bounds
+ * min(chi, dim*chi_o, 2*prod(other legs)) with rank deficits zero-padded.
+ * May be called again with other arguments (plans made before are invalid).
+ * Errors: TN_ERR_ARG, TN_ERR_CUDA, TN_ERR_OOM, TN_ERR_UNSUPPORTED. */
+tn_status tn_evolve_two_sided(tn_circuit *c, int32_t split_cycle, int32_t chi_max,
+                              double cutoff_rel, void *cuda_stream);
+
+/* Structural bond dimensions after evolution: side 0 = ket, 1 = bra;
+ * out[n_edges]. Errors: TN_ERR_STATE before tn_evolve_two_sided. */
+tn_status tn_circuit_bond_dims(const tn_circuit *c, int32_t side, int32_t *out);
+
+/* Cuts and contraction path (supplement, Algorithm 1 with Assumptions 1-3;
+ * cutting as in the overlap paragraph), compiled into static per-step
+ * shapes and uploaded. `opts` may be NULL (defaults). `info` may be NULL.
+ * Errors: TN_ERR_STATE, TN_ERR_NO_PATH, TN_ERR_ARG, TN_ERR_CUDA, TN_ERR_OOM. */
+tn_status tn_path(tn_circuit *c, const tn_path_opts *opts, tn_plan **out, tn_plan_info *info);
+
+/* Plan details: order[n_qubits] (contraction order), cuts[n_cuts] (edge
+ * ids), steps[3*n_steps] = (M, K, N) per step per slice. Any pointer may be NULL. */
+tn_status tn_plan_details(const tn_plan *p, int32_t *order, int32_t *cuts, int64_t *steps);
+
+/* Amplitudes of n bitstrings. bits: n rows of ceil(n_qubits/64) uint64 words,
+ * bit q of word q/64 = s_q; host or device memory. out: n tn_c128, host or
+ * device memory. Runs the bra program per bitstring (FP64), the overlap
+ * network and the sliced contraction in `prec`, and the FP64 slice sum, in
+ * device batches of info.chunk_bitstrings on `cuda_stream`; returns after
+ * the results are in `out` (the stream is synchronised).
+ * Errors: TN_ERR_ARG, TN_ERR_CUDA, TN_ERR_OOM, TN_ERR_UNSUPPORTED. */
+tn_status tn_amplitudes(tn_plan *p, const uint64_t *bits, int64_t n, tn_precision prec,
+                        tn_c128 *out, void *cuda_stream);
+
+/* Kernel launches issued since the last reset (all threads). */
+int64_t tn_launch_count(int32_t reset);
+
+/* Per-kernel timing (tracing): while enabled, every launch is bracketed by
+ * CUDA events on its own stream and attributed to a kernel kind together
+ * with its algorithmic bytes and flops. tn_profile_enable(1) clears the
+ * records; tn_profile_read synchronises the recorded events and returns kind
+ * `idx` (TN_ERR_ARG past the last kind): name (NUL-terminated, at most
+ * name_len bytes), launches, total milliseconds, algorithmic bytes and flops. */
+tn_status tn_profile_enable(int32_t on);
+tn_status tn_profile_read(int32_t idx, char *name, int32_t name_len, int64_t *launches, double *ms,
+                          double *bytes, double *flops);
+
+void tn_circuit_free(tn_circuit *c);
+void tn_plan_free(tn_plan *p);
+const char *tn_last_error(void);
+
+/* ---- host-only pieces, usable without a GPU ------------------------------ */
+
+/* Eq. gatesplit: O[(k',l'),(k,l)] = sum_s P[k',k,s] Q[l',l,s] with chi_o = the
+ * number of singular values > 1e-12 s_0 of O regrouped as (k',k) x (l',l).
+ * m: 16 entries (4x4 row-major). P, Q: 16 entries each, index (a*2+b)*4+s for
+ * P[a][b][s]; unused s are zero. */
+tn_status tn_gate_split(const tn_c128 *m, tn_c128 *P, tn_c128 *Q, int32_t *chi_o);
+
+/* Algorithm 1 on an arbitrary graph with per-edge dimensions `dims`
+ * (n_edges entries, >= 1). order[n_qubits] receives the path, *score its
+ * score (Cost = product of the dims of all legs of both tensors).
+ * Errors: TN_ERR_ARG, TN_ERR_GRAPH, TN_ERR_NO_PATH. */
+tn_status tn_path_search(const tn_graph *g, const double *dims, const tn_path_opts *opts,
+                         int32_t *order, double *score, int64_t *states_expanded);
+
+/* ---- serving loop (continuous batching over resident plans) -------------- */
+
+typedef struct tn_server tn_server;
+
+typedef struct {
+  double hbm_budget_bytes;  /* admission budget for in-flight work; 0 = 16 GiB */
+  int32_t max_inflight;     /* concurrently running requests; 0 = 4 */
+  int32_t n_streams;        /* device streams the worker threads use; 0 = max_inflight */
+} tn_server_cfg;
+
+typedef struct {
+  int64_t submitted, completed, failed, rejected;
+  int64_t amplitudes;
+  double busy_seconds;       /* wall time with >= 1 request in flight */
+  double p50_latency_s, p99_latency_s;   /* completion - submission, over completed requests */
+  double max_inflight_seen;
+  double peak_admitted_bytes;
+} tn_server_stats;
+
+/* Create a server; its worker threads run tn_amplitudes-equivalent work for
+ * admitted requests on their own streams. Errors: TN_ERR_ARG, TN_ERR_CUDA. */
+tn_status tn_server_create(const tn_server_cfg *cfg, tn_server **out);
+
+/* Queue a request (the bits are copied; out must stay valid until the ticket
+ * completes). The plan must stay alive until then and may be shared by
+ * several requests (each running request gets its own workspace).
+ * Errors: TN_ERR_ARG, TN_ERR_OOM (footprint above the whole budget). */
+tn_status tn_server_submit(tn_server *s, tn_plan *p, const uint64_t *bits, int64_t n,
+                           tn_precision prec, tn_c128 *out, uint64_t *ticket);
+
+/* Wait for a ticket; timeout_ms < 0 waits forever. Returns the request's
+ * own status, or TN_ERR_TIMEOUT if it has not completed in time. */
+tn_status tn_server_wait(tn_server *s, uint64_t ticket, int64_t timeout_ms);
+
+tn_status tn_server_stats_get(tn_server *s, tn_server_stats *st);
+
+/* Drains queued work, joins the workers and frees the server. */
+void tn_server_free(tn_server *s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TN_H */

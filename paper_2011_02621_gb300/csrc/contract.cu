@@ -1,0 +1,273 @@
+// Path-ordered contraction of the overlap network, batched over
+// (bitstring, slice) items: the first node's C tensor, one SIMT complex GEMM
+// per absorption step, and the FP64 sum over slices.
+//
+// The overlap tensor C^i = sum_sigma A^sigma (ket) B^sigma (bra) of Eq. overlap
+// is never stored: each GEMM forms its B operand tile on the fly from the
+// node's ket and bra tensors through per-step offset tables, with the cut
+// legs fixed by the item's slice. The A operand is gathered from the previous
+// intermediate through a row decomposition over the "rest" legs and a column
+// table over the shared legs, so the transposes of a transpose-transpose-GEMM
+// step cost no extra pass over memory.
+#include <cuda_runtime.h>
+
+#include "tn_internal.h"
+
+namespace {
+
+template <typename R> struct C2T;
+template <> struct C2T<double> { using T = double2; };
+template <> struct C2T<float> { using T = float2; };
+
+template <typename V> __device__ __forceinline__ V cz() { V v; v.x = 0; v.y = 0; return v; }
+template <typename V> __device__ __forceinline__ V cfma(V a, V b, V c) {
+  c.x = fma(a.x, b.x, fma(-a.y, b.y, c.x));
+  c.y = fma(a.x, b.y, fma(a.y, b.x, c.y));
+  return c;
+}
+
+struct ItemCtx {
+  int64_t b, sl;
+  int32_t sa, sb;
+};
+
+__device__ __forceinline__ ItemCtx item_ctx(const ContractArgs &a, const StepParams &s, int64_t item) {
+  ItemCtx c;
+  c.b = item / a.n_slices;
+  c.sl = a.slice0 + item % a.n_slices;
+  c.sa = a.tab[s.t_sa + c.sl];
+  c.sb = a.tab[s.t_sb + c.sl];
+  return c;
+}
+
+// C element (Eq. overlap) at table offsets
+template <typename V>
+__device__ __forceinline__ V overlap_elem(const V *ket, const V *bra, int64_t ia, int64_t ib, int64_t ksig,
+                                          int64_t bsig) {
+  return cfma(ket[ia + ksig], bra[ib + bsig], cfma(ket[ia], bra[ib], cz<V>()));
+}
+
+template <typename R>
+__global__ void form_kernel(StepParams s, ContractArgs a, const typename C2T<R>::T *ket,
+                            const typename C2T<R>::T *bra, typename C2T<R>::T *tout) {
+  using V = typename C2T<R>::T;
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= a.items * s.N) return;
+  int64_t item = idx / s.N, n = idx % s.N;
+  ItemCtx c = item_ctx(a, s, item);
+  const V *kp = ket + s.ket_off + c.sa;
+  const V *bp = bra + c.b * a.bra_stride + s.bra_off + c.sb;
+  tout[item * a.t_stride + n] = overlap_elem(kp, bp, a.tab[s.t_bna + n], a.tab[s.t_bnb + n], s.ket_sig, s.bra_sig);
+}
+
+// Tiled SIMT complex GEMM: one CTA per (item, BM x BN output tile).
+template <typename R, int BM, int BN, int BK, int TM, int TN>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+step_kernel(StepParams s, ContractArgs a, const typename C2T<R>::T *ket, const typename C2T<R>::T *bra,
+            const typename C2T<R>::T *tin, typename C2T<R>::T *tout) {
+  using V = typename C2T<R>::T;
+  constexpr int NT = (BM / TM) * (BN / TN);
+  __shared__ V As[BK][BM + 1];
+  __shared__ V Bs[BK][BN];
+  __shared__ int rowoff[BM];
+  const int tid = threadIdx.x;
+  const int64_t tiles_m = (s.M + BM - 1) / BM, tiles_n = (s.N + BN - 1) / BN;
+  const int64_t blk = blockIdx.x;
+  const int64_t item = blk / (tiles_m * tiles_n);
+  const int64_t rem = blk % (tiles_m * tiles_n);
+  const int64_t m0 = (rem / tiles_n) * BM, n0 = (rem % tiles_n) * BN;
+  ItemCtx c = item_ctx(a, s, item);
+  const V *kp = ket + s.ket_off + c.sa;
+  const V *bp = bra + c.b * a.bra_stride + s.bra_off + c.sb;
+  const V *tp = tin + item * a.t_stride;
+  const int32_t *ak = a.tab + s.t_ak, *bka = a.tab + s.t_bka, *bkb = a.tab + s.t_bkb;
+  const int32_t *bna = a.tab + s.t_bna, *bnb = a.tab + s.t_bnb;
+
+  for (int mm = tid; mm < BM; mm += NT) {
+    int64_t m = m0 + mm;
+    int off = -1;
+    if (m < s.M) {
+      off = 0;
+      int64_t r = m;
+      for (int j = s.n_rest - 1; j >= 0; --j) {
+        int d = s.rest_dim[j];
+        off += (int)(r % d) * s.rest_stride[j];
+        r /= d;
+      }
+    }
+    rowoff[mm] = off;
+  }
+  const int tx = tid % (BN / TN), ty = tid / (BN / TN);
+  V acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = cz<V>();
+  __syncthreads();
+
+  for (int64_t k0 = 0; k0 < s.K; k0 += BK) {
+    for (int idx = tid; idx < BM * BK; idx += NT) {
+      int mm = idx / BK, kk = idx % BK;
+      int64_t k = k0 + kk;
+      int ro = rowoff[mm];
+      As[kk][mm] = (ro >= 0 && k < s.K) ? tp[ro + ak[k]] : cz<V>();
+    }
+    for (int idx = tid; idx < BK * BN; idx += NT) {
+      int kk = idx / BN, nn = idx % BN;
+      int64_t k = k0 + kk, n = n0 + nn;
+      V v = cz<V>();
+      if (k < s.K && n < s.N)
+        v = overlap_elem(kp, bp, (int64_t)bka[k] + bna[n], (int64_t)bkb[k] + bnb[n], s.ket_sig, s.bra_sig);
+      Bs[kk][nn] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      V af[TM], bf[TN];
+#pragma unroll
+      for (int i = 0; i < TM; ++i) af[i] = As[kk][ty * TM + i];
+#pragma unroll
+      for (int j = 0; j < TN; ++j) bf[j] = Bs[kk][tx * TN + j];
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = cfma(af[i], bf[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  V *op = tout + item * a.t_stride;
+#pragma unroll
+  for (int i = 0; i < TM; ++i) {
+    int64_t m = m0 + ty * TM + i;
+    if (m >= s.M) continue;
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      int64_t n = n0 + tx * TN + j;
+      if (n < s.N) op[m * s.N + n] = acc[i][j];
+    }
+  }
+}
+
+// Small outputs (M*N <= 16, e.g. the last step): one CTA per item reduces over K.
+template <typename R>
+__global__ void __launch_bounds__(256)
+step_small_kernel(StepParams s, ContractArgs a, const typename C2T<R>::T *ket, const typename C2T<R>::T *bra,
+                  const typename C2T<R>::T *tin, typename C2T<R>::T *tout) {
+  using V = typename C2T<R>::T;
+  __shared__ V red[256 / 32];
+  const int64_t item = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  ItemCtx c = item_ctx(a, s, item);
+  const V *kp = ket + s.ket_off + c.sa;
+  const V *bp = bra + c.b * a.bra_stride + s.bra_off + c.sb;
+  const V *tp = tin + item * a.t_stride;
+  const int32_t *ak = a.tab + s.t_ak, *bka = a.tab + s.t_bka, *bkb = a.tab + s.t_bkb;
+  const int32_t *bna = a.tab + s.t_bna, *bnb = a.tab + s.t_bnb;
+  for (int64_t out = 0; out < s.M * s.N; ++out) {
+    int64_t m = out / s.N, n = out % s.N;
+    int ro = 0;
+    int64_t r = m;
+    for (int j = s.n_rest - 1; j >= 0; --j) {
+      int d = s.rest_dim[j];
+      ro += (int)(r % d) * s.rest_stride[j];
+      r /= d;
+    }
+    V acc = cz<V>();
+    for (int64_t k = tid; k < s.K; k += 256) {
+      V cv = overlap_elem(kp, bp, (int64_t)bka[k] + bna[n], (int64_t)bkb[k] + bnb[n], s.ket_sig, s.bra_sig);
+      acc = cfma(tp[ro + ak[k]], cv, acc);
+    }
+    for (int o = 16; o; o >>= 1) {
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+    }
+    if (lane == 0) red[warp] = acc;
+    __syncthreads();
+    if (tid == 0) {
+      V t = cz<V>();
+      for (int w = 0; w < 256 / 32; ++w) { t.x += red[w].x; t.y += red[w].y; }
+      tout[item * a.t_stride + out] = t;
+    }
+    __syncthreads();
+  }
+}
+
+template <typename R>
+__global__ void slice_sum_kernel(const typename C2T<R>::T *res, int64_t stride, int64_t n_bits, int64_t n_slices,
+                                 int accumulate, double2 *out) {
+  int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n_bits) return;
+  double sr = 0, si = 0;
+  if (accumulate) { sr = out[b].x; si = out[b].y; }
+  for (int64_t sl = 0; sl < n_slices; ++sl) {   // fixed order, FP64
+    auto v = res[(b * n_slices + sl) * stride];
+    sr += (double)v.x;
+    si += (double)v.y;
+  }
+  out[b] = make_double2(sr, si);
+}
+
+template <typename R, int BM, int BN, int BK, int TM, int TN>
+cudaError_t launch_tiled(const StepParams &s, const ContractArgs &a, const void *ket, const void *bra,
+                         const void *t_in, void *t_out, cudaStream_t st) {
+  using V = typename C2T<R>::T;
+  int64_t tiles = ((s.M + BM - 1) / BM) * ((s.N + BN - 1) / BN);
+  int64_t grid = tiles * a.items;
+  if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  step_kernel<R, BM, BN, BK, TM, TN><<<(unsigned)grid, (BM / TM) * (BN / TN), 0, st>>>(
+      s, a, (const V *)ket, (const V *)bra, (const V *)t_in, (V *)t_out);
+  tn_count_launch(1);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+template <typename R>
+cudaError_t launch_form(const StepParams &s, const ContractArgs &a, const void *ket, const void *bra, void *t_out,
+                        cudaStream_t st) {
+  using V = typename C2T<R>::T;
+  int64_t total = a.items * s.N;
+  if (total <= 0) return cudaSuccess;
+  form_kernel<R><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(s, a, (const V *)ket, (const V *)bra, (V *)t_out);
+  tn_count_launch(1);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_step(const StepParams &s, const ContractArgs &a, const void *ket, const void *bra,
+                        const void *t_in, void *t_out, cudaStream_t st) {
+  using V = typename C2T<R>::T;
+  if (a.items <= 0) return cudaSuccess;
+  if (s.M * s.N <= 16) {
+    if (a.items > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    step_small_kernel<R><<<(unsigned)a.items, 256, 0, st>>>(s, a, (const V *)ket, (const V *)bra, (const V *)t_in,
+                                                            (V *)t_out);
+    tn_count_launch(1);
+    return cudaGetLastError();
+  }
+  if (s.N >= 48) return launch_tiled<R, 64, 64, 8, 4, 4>(s, a, ket, bra, t_in, t_out, st);
+  if (s.N >= 12) return launch_tiled<R, 128, 16, 8, 8, 2>(s, a, ket, bra, t_in, t_out, st);
+  return launch_tiled<R, 256, 4, 8, 8, 1>(s, a, ket, bra, t_in, t_out, st);
+}
+
+template <typename R>
+cudaError_t launch_slice_sum(const void *res, int64_t items_stride, int64_t n_bits, int64_t n_slices,
+                             int accumulate, double2 *out, cudaStream_t st) {
+  using V = typename C2T<R>::T;
+  if (n_bits <= 0) return cudaSuccess;
+  slice_sum_kernel<R><<<(unsigned)((n_bits + 255) / 256), 256, 0, st>>>((const V *)res, items_stride, n_bits,
+                                                                        n_slices, accumulate, out);
+  tn_count_launch(1);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_form<double>(const StepParams &, const ContractArgs &, const void *, const void *, void *,
+                                         cudaStream_t);
+template cudaError_t launch_form<float>(const StepParams &, const ContractArgs &, const void *, const void *, void *,
+                                        cudaStream_t);
+template cudaError_t launch_step<double>(const StepParams &, const ContractArgs &, const void *, const void *,
+                                         const void *, void *, cudaStream_t);
+template cudaError_t launch_step<float>(const StepParams &, const ContractArgs &, const void *, const void *,
+                                        const void *, void *, cudaStream_t);
+template cudaError_t launch_slice_sum<double>(const void *, int64_t, int64_t, int64_t, int, double2 *, cudaStream_t);
+template cudaError_t launch_slice_sum<float>(const void *, int64_t, int64_t, int64_t, int, double2 *, cudaStream_t);

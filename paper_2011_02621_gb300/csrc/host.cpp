@@ -1,0 +1,1292 @@
+// Host side of the C ABI in include/tn.h: validation, single-qubit fusion and
+// gate split (Eq. gatesplit), the two-sided evolution programs with static
+// structural bond bounds (Eqs. result1/result2, svd/svd2, shouwei; Fig. 2a),
+// Algorithm 1 of the supplement (best-first path search over qubit subsets
+// under Assumptions 1-3), cutting, the plan compiler, and the device driver
+// of tn_amplitudes.
+#include <algorithm>
+#include <array>
+#include <atomic>
+#include <cmath>
+#include <complex>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <queue>
+#include <string>
+#include <unordered_set>
+#include <vector>
+
+#include "tn_host.h"
+
+typedef std::complex<double> cd;
+
+// ---------------------------------------------------------------------------
+// errors and launch accounting
+// ---------------------------------------------------------------------------
+static thread_local std::string g_err;
+static std::atomic<int64_t> g_launches{0};
+
+tn_status tn_fail(tn_status s, const char *fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+void tn_count_launch(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+extern "C" int64_t tn_launch_count(int32_t reset) {
+  return reset ? g_launches.exchange(0) : g_launches.load();
+}
+
+extern "C" const char *tn_last_error(void) { return g_err.c_str(); }
+
+#define CUDA_TRY(x)                                                                        \
+  do {                                                                                     \
+    cudaError_t e_ = (x);                                                                  \
+    if (e_ != cudaSuccess) return tn_fail(TN_ERR_CUDA, "%s: %s", #x, cudaGetErrorString(e_)); \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// tracing
+// ---------------------------------------------------------------------------
+namespace {
+struct ProfKind {
+  std::string name;
+  int64_t launches = 0;
+  double ms = 0, bytes = 0, flops = 0;
+};
+struct ProfRec {
+  int kind;
+  cudaEvent_t a, b;
+};
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<ProfKind> g_kinds;
+std::vector<ProfRec> g_recs;
+std::vector<cudaEvent_t> g_event_pool;
+
+cudaEvent_t prof_event() {
+  if (!g_event_pool.empty()) {
+    cudaEvent_t e = g_event_pool.back();
+    g_event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+void prof_drain() {   // caller holds the mutex
+  for (auto &r : g_recs) {
+    float ms = 0;
+    if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess)
+      g_kinds[r.kind].ms += ms;
+    g_event_pool.push_back(r.a);
+    g_event_pool.push_back(r.b);
+  }
+  g_recs.clear();
+  cudaGetLastError();
+}
+}  // namespace
+
+ProfScope::ProfScope(const char *kind, cudaStream_t stream, double bytes, double flops) {
+  if (!g_prof_on) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (!g_prof_on) return;
+  int k = -1;
+  for (size_t i = 0; i < g_kinds.size(); ++i)
+    if (g_kinds[i].name == kind) k = (int)i;
+  if (k < 0) {
+    g_kinds.push_back(ProfKind());
+    g_kinds.back().name = kind;
+    k = (int)g_kinds.size() - 1;
+  }
+  g_kinds[k].launches += 1;
+  g_kinds[k].bytes += bytes;
+  g_kinds[k].flops += flops;
+  ProfRec r{k, prof_event(), prof_event()};
+  cudaEventRecord(r.a, stream);
+  g_recs.push_back(r);
+  slot = (int)g_recs.size() - 1;
+  st = stream;
+}
+
+ProfScope::~ProfScope() {
+  if (slot < 0) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (slot < (int)g_recs.size()) cudaEventRecord(g_recs[slot].b, st);
+}
+
+extern "C" tn_status tn_profile_enable(int32_t on) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  prof_drain();
+  g_kinds.clear();
+  g_prof_on = on != 0;
+  return TN_OK;
+}
+
+extern "C" tn_status tn_profile_read(int32_t idx, char *name, int32_t name_len, int64_t *launches, double *ms,
+                                     double *bytes, double *flops) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  prof_drain();
+  if (idx < 0 || idx >= (int)g_kinds.size()) return TN_ERR_ARG;
+  const ProfKind &k = g_kinds[idx];
+  if (name && name_len > 0) {
+    std::strncpy(name, k.name.c_str(), name_len - 1);
+    name[name_len - 1] = 0;
+  }
+  if (launches) *launches = k.launches;
+  if (ms) *ms = k.ms;
+  if (bytes) *bytes = k.bytes;
+  if (flops) *flops = k.flops;
+  return TN_OK;
+}
+
+// ---------------------------------------------------------------------------
+// device memory
+// ---------------------------------------------------------------------------
+void *DevMem::alloc(size_t bytes, cudaStream_t st) {
+  if (!bytes) return nullptr;
+  if (has) return a.alloc(bytes, (void *)st, a.ctx);
+  void *p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+
+void DevMem::release(Buf &b) {
+  if (!b.p) return;
+  if (has) a.free(b.p, b.bytes, (void *)b.stream, a.ctx);
+  else cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
+tn_status DevMem::ensure(Buf &b, size_t bytes, cudaStream_t st) {
+  if (b.p && b.bytes >= bytes) return TN_OK;
+  release(b);
+  if (!bytes) return TN_OK;
+  b.p = alloc(bytes, st);
+  if (!b.p) return tn_fail(TN_ERR_OOM, "device allocation of %zu bytes failed", bytes);
+  b.bytes = bytes;
+  b.stream = st;
+  return TN_OK;
+}
+
+// ---------------------------------------------------------------------------
+// small host SVD (one-sided Jacobi, complex) for the 4x4 gate split
+// ---------------------------------------------------------------------------
+// X: m x n column-major (n <= m). On return X holds U (unit columns, sorted by
+// descending singular value), S the singular values, V (n x n, column-major)
+// with X_in = U diag(S) V^H.
+static void host_svd(int m, int n, std::vector<cd> &X, std::vector<double> &S, std::vector<cd> &V) {
+  V.assign((size_t)n * n, cd(0, 0));
+  for (int i = 0; i < n; ++i) V[(size_t)i * n + i] = 1.0;
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    bool rot = false;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        double al = 0, be = 0;
+        cd ga = 0;
+        for (int r = 0; r < m; ++r) {
+          cd a = X[(size_t)p * m + r], b = X[(size_t)q * m + r];
+          al += std::norm(a);
+          be += std::norm(b);
+          ga += std::conj(a) * b;
+        }
+        double g = std::abs(ga);
+        if (!(g > 2.0 * std::sqrt((double)m) * 2.220446049250313e-16 * std::sqrt(al * be)) || g == 0.0) continue;
+        rot = true;
+        double zeta = (be - al) / (2 * g);
+        double t = (zeta >= 0 ? 1.0 : -1.0) / (std::fabs(zeta) + std::sqrt(1 + zeta * zeta));
+        double c = 1 / std::sqrt(1 + t * t), s = c * t;
+        cd e = std::conj(ga) / g;
+        for (int r = 0; r < m; ++r) {
+          cd a = X[(size_t)p * m + r], b = X[(size_t)q * m + r] * e;
+          X[(size_t)p * m + r] = c * a - s * b;
+          X[(size_t)q * m + r] = s * a + c * b;
+        }
+        for (int r = 0; r < n; ++r) {
+          cd a = V[(size_t)p * n + r], b = V[(size_t)q * n + r] * e;
+          V[(size_t)p * n + r] = c * a - s * b;
+          V[(size_t)q * n + r] = s * a + c * b;
+        }
+      }
+    if (!rot) break;
+  }
+  S.assign(n, 0.0);
+  for (int j = 0; j < n; ++j) {
+    double s2 = 0;
+    for (int r = 0; r < m; ++r) s2 += std::norm(X[(size_t)j * m + r]);
+    S[j] = std::sqrt(s2);
+  }
+  std::vector<int> idx(n);
+  for (int j = 0; j < n; ++j) idx[j] = j;
+  std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return S[a] > S[b]; });
+  std::vector<cd> X2((size_t)m * n), V2((size_t)n * n);
+  std::vector<double> S2(n);
+  for (int t = 0; t < n; ++t) {
+    int j = idx[t];
+    S2[t] = S[j];
+    for (int r = 0; r < m; ++r) X2[(size_t)t * m + r] = S[j] > 0 ? X[(size_t)j * m + r] / S[j] : cd(0, 0);
+    for (int r = 0; r < n; ++r) V2[(size_t)t * n + r] = V[(size_t)j * n + r];
+  }
+  X.swap(X2);
+  V.swap(V2);
+  S.swap(S2);
+}
+
+// Eq. gatesplit on a 4x4 matrix O[(k' l'), (k l)]: P[k'][k][s], Q[l'][l][s].
+static int gate_split(const cd *O, cd P[16], cd Q[16]) {
+  std::vector<cd> R(16);   // column-major, rows (k'k), cols (l'l)
+  for (int kp = 0; kp < 2; ++kp)
+    for (int lp = 0; lp < 2; ++lp)
+      for (int k = 0; k < 2; ++k)
+        for (int l = 0; l < 2; ++l) R[(size_t)(lp * 2 + l) * 4 + (kp * 2 + k)] = O[(kp * 2 + lp) * 4 + (k * 2 + l)];
+  std::vector<double> S;
+  std::vector<cd> V;
+  host_svd(4, 4, R, S, V);
+  int chi = 0;
+  for (int s = 0; s < 4; ++s) chi += (S[s] > 1e-12 * S[0]) ? 1 : 0;
+  for (int i = 0; i < 16; ++i) P[i] = Q[i] = 0;
+  for (int s = 0; s < chi; ++s) {
+    double r = std::sqrt(S[s]);
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b) {
+        P[(a * 2 + b) * 4 + s] = R[(size_t)s * 4 + (a * 2 + b)] * r;
+        Q[(a * 2 + b) * 4 + s] = std::conj(V[(size_t)s * 4 + (a * 2 + b)]) * r;
+      }
+  }
+  return chi;
+}
+
+extern "C" tn_status tn_gate_split(const tn_c128 *m, tn_c128 *P, tn_c128 *Q, int32_t *chi_o) {
+  if (!m || !P || !Q || !chi_o) return tn_fail(TN_ERR_ARG, "tn_gate_split: NULL argument");
+  cd O[16], Pc[16], Qc[16];
+  for (int i = 0; i < 16; ++i) O[i] = cd(m[i].re, m[i].im);
+  *chi_o = gate_split(O, Pc, Qc);
+  for (int i = 0; i < 16; ++i) {
+    P[i].re = Pc[i].real(); P[i].im = Pc[i].imag();
+    Q[i].re = Qc[i].real(); Q[i].im = Qc[i].imag();
+  }
+  return TN_OK;
+}
+
+// ---------------------------------------------------------------------------
+// graph checks
+// ---------------------------------------------------------------------------
+static tn_status check_graph(const tn_graph *g, std::vector<int> &eu, std::vector<int> &ev,
+                             std::vector<std::vector<int>> &legs) {
+  if (!g || g->n_qubits <= 0 || g->n_edges < 0 || (g->n_edges > 0 && !g->edges))
+    return tn_fail(TN_ERR_ARG, "graph: bad sizes or NULL edges");
+  const int n = g->n_qubits, ne = g->n_edges;
+  if (n > 128) return tn_fail(TN_ERR_UNSUPPORTED, "graph: at most 128 qubits are supported (got %d)", n);
+  eu.resize(ne);
+  ev.resize(ne);
+  legs.assign(n, {});
+  std::unordered_set<int64_t> seen;
+  for (int i = 0; i < ne; ++i) {
+    int u = g->edges[2 * i], v = g->edges[2 * i + 1];
+    if (u < 0 || v < 0 || u >= n || v >= n) return tn_fail(TN_ERR_GRAPH, "edge %d: endpoint out of range", i);
+    if (u == v) return tn_fail(TN_ERR_GRAPH, "edge %d: self loop", i);
+    int64_t key = (int64_t)std::min(u, v) * 1024 + std::max(u, v);
+    if (!seen.insert(key).second) return tn_fail(TN_ERR_GRAPH, "edge %d: duplicate edge", i);
+    eu[i] = u;
+    ev[i] = v;
+    legs[u].push_back(i);
+    legs[v].push_back(i);
+  }
+  for (int q = 0; q < n; ++q)
+    if ((int)legs[q].size() > TN_MAXLEG)
+      return tn_fail(TN_ERR_UNSUPPORTED, "qubit %d has degree %zu > %d", q, legs[q].size(), TN_MAXLEG);
+  // connectivity
+  std::vector<int> comp(n, 0), st{0};
+  comp[0] = 1;
+  while (!st.empty()) {
+    int x = st.back();
+    st.pop_back();
+    for (int e : legs[x]) {
+      int y = eu[e] == x ? ev[e] : eu[e];
+      if (!comp[y]) { comp[y] = 1; st.push_back(y); }
+    }
+  }
+  for (int q = 0; q < n; ++q)
+    if (!comp[q]) return tn_fail(TN_ERR_GRAPH, "graph is not connected (qubit %d unreachable)", q);
+  return TN_OK;
+}
+
+static int find_edge(const tn_circuit *c, int a, int b) {
+  for (int e : c->legs[a])
+    if ((c->eu[e] == a && c->ev[e] == b) || (c->eu[e] == b && c->ev[e] == a)) return e;
+  return -1;
+}
+
+extern "C" tn_status tn_build(const tn_graph *g, const tn_gate *gates, int64_t n_gates, const tn_allocator *alloc,
+                              tn_circuit **out) {
+  if (!out) return tn_fail(TN_ERR_ARG, "tn_build: out is NULL");
+  *out = nullptr;
+  if (n_gates < 0 || (n_gates > 0 && !gates)) return tn_fail(TN_ERR_ARG, "tn_build: bad gate list");
+  tn_circuit *c = new tn_circuit();
+  tn_status s = check_graph(g, c->eu, c->ev, c->legs);
+  if (s != TN_OK) { delete c; return s; }
+  c->n = g->n_qubits;
+  c->ne = g->n_edges;
+  for (int64_t i = 0; i < n_gates; ++i) {
+    const tn_gate &gt = gates[i];
+    if (gt.arity != 1 && gt.arity != 2) { delete c; return tn_fail(TN_ERR_ARG, "gate %lld: arity %d", (long long)i, gt.arity); }
+    if (gt.cycle < 1) { delete c; return tn_fail(TN_ERR_ARG, "gate %lld: cycle must be >= 1", (long long)i); }
+    for (int j = 0; j < gt.arity; ++j)
+      if (gt.q[j] < 0 || gt.q[j] >= c->n) { delete c; return tn_fail(TN_ERR_GRAPH, "gate %lld: qubit out of range", (long long)i); }
+    if (gt.arity == 2 && find_edge(c, gt.q[0], gt.q[1]) < 0) {
+      delete c;
+      return tn_fail(TN_ERR_GRAPH, "gate %lld acts on (%d,%d), which is not an edge", (long long)i, gt.q[0], gt.q[1]);
+    }
+    for (int j = 0; j < (gt.arity == 2 ? 16 : 4); ++j)
+      if (!std::isfinite(gt.m[j].re) || !std::isfinite(gt.m[j].im)) {
+        delete c;
+        return tn_fail(TN_ERR_ARG, "gate %lld: non-finite matrix entry", (long long)i);
+      }
+    c->gates.push_back(gt);
+  }
+  c->max_deg = 0;
+  for (int q = 0; q < c->n; ++q) c->max_deg = std::max(c->max_deg, (int)c->legs[q].size());
+  if (alloc) { c->mem.a = *alloc; c->mem.has = alloc->alloc && alloc->free; }
+  *out = c;
+  return TN_OK;
+}
+
+// ---------------------------------------------------------------------------
+// evolution programs
+// ---------------------------------------------------------------------------
+typedef std::array<cd, 4> M2;
+
+static M2 mul2(const M2 &a, const M2 &b) {
+  M2 r;
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j) r[i * 2 + j] = a[i * 2] * b[j] + a[i * 2 + 1] * b[2 + j];
+  return r;
+}
+
+// Build one half: `seq` in processing order, matrices transposed for the bra.
+// Single-qubit gates accumulate per qubit and fuse into the next two-qubit
+// gate on that qubit (its input side); leftovers become tail applications.
+static void build_half(const tn_circuit *c, const std::vector<const tn_gate *> &seq, bool transpose, int chi,
+                       double cutoff, Half &h) {
+  const int n = c->n;
+  h = Half();
+  h.dims.assign(c->ne, 1);
+  std::vector<M2> pend(n, M2{1, 0, 0, 1});
+  std::vector<char> has(n, 0);
+  std::vector<int64_t> cap(n, 2);
+  auto node_size = [&](int q) {
+    int64_t s = 2;
+    for (int e : c->legs[q]) s *= h.dims[e];
+    return s;
+  };
+  for (const tn_gate *g : seq) {
+    if (g->arity == 1) {
+      M2 u;
+      for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) {
+          const tn_c128 &x = transpose ? g->m[j * 2 + i] : g->m[i * 2 + j];
+          u[i * 2 + j] = cd(x.re, x.im);
+        }
+      pend[g->q[0]] = mul2(u, pend[g->q[0]]);
+      has[g->q[0]] = 1;
+      continue;
+    }
+    const int k = g->q[0], l = g->q[1];
+    cd O[16], F[16];
+    for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 4; ++j) {
+        const tn_c128 &x = transpose ? g->m[j * 4 + i] : g->m[i * 4 + j];
+        O[i * 4 + j] = cd(x.re, x.im);
+      }
+    // F = O (pend_k (x) pend_l), basis |k l>, k the high bit
+    const M2 &pk = pend[k], &pl = pend[l];
+    for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 4; ++j) {
+        cd acc = 0;
+        for (int t = 0; t < 4; ++t) acc += O[i * 4 + t] * pk[(t >> 1) * 2 + (j >> 1)] * pl[(t & 1) * 2 + (j & 1)];
+        F[i * 4 + j] = acc;
+      }
+    pend[k] = pend[l] = M2{1, 0, 0, 1};
+    has[k] = has[l] = 0;
+    cd P[16], Q[16];
+    int chi_o = gate_split(F, P, Q);
+    const int e = find_edge(c, k, l);
+    GateParams gp;
+    std::memset(&gp, 0, sizeof gp);
+    gp.nk = (int)c->legs[k].size();
+    gp.nl = (int)c->legs[l].size();
+    int64_t ok = 1, ol = 1;
+    for (int j = 0; j < gp.nk; ++j) {
+      int ej = c->legs[k][j];
+      gp.dk[j] = h.dims[ej];
+      if (ej == e) gp.pk = j; else ok *= h.dims[ej];
+    }
+    for (int j = 0; j < gp.nl; ++j) {
+      int ej = c->legs[l][j];
+      gp.dl[j] = h.dims[ej];
+      if (ej == e) gp.pl = j; else ol *= h.dims[ej];
+    }
+    gp.din = h.dims[e];
+    gp.chi_o = chi_o;
+    gp.n = gp.din * chi_o;
+    gp.m_k = (int)(2 * ok);
+    gp.m_l = (int)(2 * ol);
+    gp.sv_is_k = gp.m_k <= gp.m_l ? 1 : 0;     // SVD the endpoint with fewer rows (ties: q[0])
+    int dout = std::min(gp.n, std::min(gp.m_k, gp.m_l));
+    if (chi > 0) dout = std::min(dout, chi);
+    gp.dout = dout;
+    gp.cutoff = cutoff;
+    for (int i = 0; i < 16; ++i) {
+      gp.P[i] = make_double2(P[i].real(), P[i].imag());
+      gp.Q[i] = make_double2(Q[i].real(), Q[i].imag());
+    }
+    h.dims[e] = dout;
+    cap[k] = std::max(cap[k], node_size(k));
+    cap[l] = std::max(cap[l], node_size(l));
+    h.gp.push_back(gp);
+    h.gate_nodes.push_back({k, l});
+    h.seq.push_back({2, (int)h.gp.size() - 1});
+    h.max_gate_mn = std::max<int64_t>(h.max_gate_mn, (int64_t)std::max(gp.m_k, gp.m_l) * gp.n);
+  }
+  for (int q = 0; q < n; ++q) {
+    if (!has[q]) continue;
+    Apply1Params a;
+    std::memset(&a, 0, sizeof a);
+    for (int i = 0; i < 4; ++i) a.u[i] = make_double2(pend[q][i].real(), pend[q][i].imag());
+    a.size_rest = node_size(q) / 2;
+    h.ap.push_back(a);
+    h.ap_node.push_back(q);
+    h.seq.push_back({1, (int)h.ap.size() - 1});
+  }
+  // node slots
+  h.node_off.assign(n, 0);
+  int64_t off = 0;
+  for (int q = 0; q < n; ++q) {
+    h.node_off[q] = off;
+    off += (cap[q] + 1) & ~1LL;      // keep 32-byte alignment of double2 slots
+  }
+  h.item_elems = std::max<int64_t>(off, 2);
+  h.max_work = 0;
+  for (size_t i = 0; i < h.gp.size(); ++i) {
+    GateParams &gp = h.gp[i];
+    gp.off_k = h.node_off[h.gate_nodes[i].first];
+    gp.off_l = h.node_off[h.gate_nodes[i].second];
+    int64_t w = gate_work_elems(gp);
+    gp.use_smem = (w * (int64_t)sizeof(double2) <= 200 * 1024) ? 1 : 0;
+    gp.work_stride = w;
+    if (!gp.use_smem) h.max_work = std::max(h.max_work, w);
+  }
+  for (size_t i = 0; i < h.ap.size(); ++i) h.ap[i].off = h.node_off[h.ap_node[i]];
+}
+
+static double gate_bytes(const GateParams &g) {   // node tensors in and out (complex128)
+  double in = (double)g.m_k / 2 * g.din * 2 + (double)g.m_l / 2 * g.din * 2;
+  double out = (double)g.m_k / 2 * g.dout * 2 + (double)g.m_l / 2 * g.dout * 2;
+  return 16.0 * (in + out);
+}
+
+static double gate_flops(const GateParams &g) {
+  // complex gate application (2 terms per element) + one-sided Jacobi thin SVD of an m x n
+  // matrix (Golub & Van Loan's count for the one-sided Jacobi method, ~ 2 m n^2 per sweep,
+  // 6 sweeps, complex = 4x real) + absorption GEMM
+  const double m = g.sv_is_k ? g.m_k : g.m_l, mo = g.sv_is_k ? g.m_l : g.m_k;
+  const double r = std::max(m, (double)g.n), c = std::min(m, (double)g.n);
+  return 8.0 * 2 * (g.m_k + g.m_l) * g.n + 4.0 * 6 * 2 * r * c * c + 8.0 * mo * g.n * g.dout;
+}
+
+tn_status run_half(const Half &h, int n_qubits, double2 *base, int items, const int64_t *node_off_dev,
+                   const uint64_t *bits_dev, int words, double2 *gwork, int *errflag, cudaStream_t st) {
+  {
+    ProfScope ps("init_product", st, 32.0 * items * n_qubits, 0);
+    CUDA_TRY(launch_init_product(base, h.item_elems, items, node_off_dev, n_qubits, bits_dev, words, st));
+  }
+  for (const auto &op : h.seq) {
+    if (op.first == 2) {
+      const GateParams &g = h.gp[op.second];
+      ProfScope ps("gate_svd_fp64", st, gate_bytes(g) * items, gate_flops(g) * items);
+      CUDA_TRY(launch_gate(g, base, h.item_elems, items, gwork, errflag, st));
+    } else {
+      const Apply1Params &a = h.ap[op.second];
+      ProfScope ps("apply_1q_fp64", st, 64.0 * a.size_rest * items, 16.0 * a.size_rest * items);
+      CUDA_TRY(launch_apply1(a, base, h.item_elems, items, st));
+    }
+  }
+  return TN_OK;
+}
+
+static tn_status init_device(int &dev) {
+  int count = 0;
+  cudaError_t e = cudaGetDeviceCount(&count);
+  if (e != cudaSuccess || count == 0) {
+    cudaGetLastError();
+    return tn_fail(TN_ERR_CUDA, "no CUDA device available: this library has no CPU fallback");
+  }
+  CUDA_TRY(cudaGetDevice(&dev));
+  return TN_OK;
+}
+
+extern "C" tn_status tn_evolve_two_sided(tn_circuit *c, int32_t split_cycle, int32_t chi_max, double cutoff_rel,
+                                         void *cuda_stream) {
+  if (!c) return tn_fail(TN_ERR_ARG, "tn_evolve_two_sided: NULL circuit");
+  if (split_cycle < 0 || chi_max < 0 || !(cutoff_rel >= 0) || cutoff_rel >= 1)
+    return tn_fail(TN_ERR_ARG, "tn_evolve_two_sided: bad split/chi/cutoff");
+  tn_status s = init_device(c->device);
+  if (s != TN_OK) return s;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  // the same program again keeps plans valid (same static shapes); anything else rebuilds it
+  const bool same = c->evolved && c->split == split_cycle && c->chi == chi_max && c->cutoff == cutoff_rel;
+  if (!same) {
+    std::vector<const tn_gate *> g1, g2;
+    for (const auto &g : c->gates) (g.cycle <= split_cycle ? g1 : g2).push_back(&g);
+    std::reverse(g2.begin(), g2.end());
+    build_half(c, g1, false, chi_max, cutoff_rel, c->ket);
+    build_half(c, g2, true, chi_max, cutoff_rel, c->bra);
+    c->split = split_cycle;
+    c->chi = chi_max;
+    c->cutoff = cutoff_rel;
+  }
+  c->evolved = false;
+  // upload node offsets, run the ket half (one item)
+  DevMem &mem = c->mem;
+  if ((s = mem.ensure(c->ket_dev, c->ket.item_elems * sizeof(double2), st)) != TN_OK) return s;
+  if ((s = mem.ensure(c->ket_c64, c->ket.item_elems * sizeof(float2), st)) != TN_OK) return s;
+  if ((s = mem.ensure(c->ket_off_dev, c->n * sizeof(int64_t), st)) != TN_OK) return s;
+  if ((s = mem.ensure(c->bra_off_dev, c->n * sizeof(int64_t), st)) != TN_OK) return s;
+  if ((s = mem.ensure(c->err_dev, sizeof(int), st)) != TN_OK) return s;
+  if ((s = mem.ensure(c->ket_work, std::max<int64_t>(c->ket.max_work, 1) * sizeof(double2), st)) != TN_OK) return s;
+  CUDA_TRY(cudaMemcpyAsync(c->ket_off_dev.p, c->ket.node_off.data(), c->n * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(c->bra_off_dev.p, c->bra.node_off.data(), c->n * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemsetAsync(c->ket_dev.p, 0, c->ket.item_elems * sizeof(double2), st));
+  CUDA_TRY(cudaMemsetAsync(c->err_dev.p, 0, sizeof(int), st));
+  s = run_half(c->ket, c->n, (double2 *)c->ket_dev.p, 1, (const int64_t *)c->ket_off_dev.p, nullptr, 1,
+               (double2 *)c->ket_work.p, (int *)c->err_dev.p, st);
+  if (s != TN_OK) return s;
+  CUDA_TRY(launch_to_c64((const double2 *)c->ket_dev.p, (float2 *)c->ket_c64.p, c->ket.item_elems, st));
+  int err = 0;
+  CUDA_TRY(cudaMemcpyAsync(&err, c->err_dev.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  if (err) return tn_fail(TN_ERR_TIMEOUT, "Jacobi SVD did not converge within its sweep limit (ket half)");
+  c->evolved = true;
+  if (!same) c->generation++;
+  return TN_OK;
+}
+
+extern "C" tn_status tn_circuit_bond_dims(const tn_circuit *c, int32_t side, int32_t *out) {
+  if (!c || !out || (side != 0 && side != 1)) return tn_fail(TN_ERR_ARG, "tn_circuit_bond_dims: bad argument");
+  if (!c->evolved) return tn_fail(TN_ERR_STATE, "tn_circuit_bond_dims: call tn_evolve_two_sided first");
+  const Half &h = side == 0 ? c->ket : c->bra;
+  for (int e = 0; e < c->ne; ++e) out[e] = h.dims[e];
+  return TN_OK;
+}
+
+extern "C" void tn_circuit_free(tn_circuit *c) {
+  if (!c) return;
+  c->mem.release(c->ket_dev);
+  c->mem.release(c->ket_c64);
+  c->mem.release(c->ket_off_dev);
+  c->mem.release(c->bra_off_dev);
+  c->mem.release(c->err_dev);
+  c->mem.release(c->ket_work);
+  delete c;
+}
+
+// ---------------------------------------------------------------------------
+// Algorithm 1 (supplement): best-first search over qubit subsets
+// ---------------------------------------------------------------------------
+namespace {
+struct Mask {
+  uint64_t w[2] = {0, 0};
+  bool get(int i) const { return (w[i >> 6] >> (i & 63)) & 1; }
+  void set(int i) { w[i >> 6] |= 1ull << (i & 63); }
+  bool operator==(const Mask &o) const { return w[0] == o.w[0] && w[1] == o.w[1]; }
+  bool any_and(const Mask &o) const { return (w[0] & o.w[0]) || (w[1] & o.w[1]); }
+};
+struct MaskHash {
+  size_t operator()(const Mask &m) const {
+    uint64_t h = m.w[0] * 0x9E3779B97F4A7C15ull ^ (m.w[1] + 0x632BE59BD9B4E019ull + (m.w[0] << 6));
+    h ^= h >> 31;
+    h *= 0xBF58476D1CE4E5B9ull;
+    return (size_t)(h ^ (h >> 29));
+  }
+};
+struct PEntry {
+  Mask mask;
+  double score, prod_open;
+  int32_t parent;
+  uint8_t last, m, rank;
+  int8_t c;
+};
+struct HeapKey {
+  double score;
+  int m;
+  int64_t seq;
+  int32_t idx;
+  bool operator<(const HeapKey &o) const {   // priority_queue: "less" = lower priority
+    if (score != o.score) return score > o.score;
+    if (m != o.m) return m < o.m;
+    return seq > o.seq;
+  }
+};
+}  // namespace
+
+struct PathGraph {
+  int n;
+  std::vector<std::vector<std::pair<int, int>>> adj;   // (neighbour, edge)
+  std::vector<double> dims;
+  std::vector<Mask> nb;                                 // neighbour masks
+};
+
+static PathGraph make_pg(int n, const std::vector<int> &eu, const std::vector<int> &ev, const std::vector<double> &dims) {
+  PathGraph pg;
+  pg.n = n;
+  pg.adj.assign(n, {});
+  pg.nb.assign(n, Mask());
+  pg.dims = dims;
+  for (size_t e = 0; e < eu.size(); ++e) {
+    pg.adj[eu[e]].push_back({ev[e], (int)e});
+    pg.adj[ev[e]].push_back({eu[e], (int)e});
+    pg.nb[eu[e]].set(ev[e]);
+    pg.nb[ev[e]].set(eu[e]);
+  }
+  return pg;
+}
+
+static tn_status alg1(const PathGraph &pg, int max_rank, bool boundary_only, bool connected, int64_t max_states,
+                      std::vector<int> &order, double &score, int64_t &pops) {
+  const int n = pg.n;
+  std::vector<PEntry> arena;
+  arena.reserve(1 << 16);
+  std::priority_queue<HeapKey> pq;
+  int64_t seq = 0;
+  const int64_t arena_cap = std::max<int64_t>(8 * max_states, 1 << 20);
+  int maxdeg = 0;
+  for (int q = 0; q < n; ++q) maxdeg = std::max(maxdeg, (int)pg.adj[q].size());
+  std::vector<int> starts;
+  for (int q = 0; q < n; ++q)
+    if (!boundary_only || (int)pg.adj[q].size() < maxdeg) starts.push_back(q);
+  if (starts.empty())
+    for (int q = 0; q < n; ++q) starts.push_back(q);
+  for (int q : starts) {
+    PEntry e;
+    e.mask.set(q);
+    e.score = 0;
+    double po = 1;
+    int rk = 0;
+    for (auto &pr : pg.adj[q]) { po *= pg.dims[pr.second]; rk += pg.dims[pr.second] > 1 ? 1 : 0; }
+    e.prod_open = po;
+    e.parent = -1;
+    e.last = (uint8_t)q;
+    e.m = 1;
+    e.rank = (uint8_t)rk;
+    e.c = -1;
+    arena.push_back(e);
+    pq.push({0.0, 1, seq++, (int32_t)arena.size() - 1});
+  }
+  std::unordered_set<Mask, MaskHash> seen;
+  pops = 0;
+  while (!pq.empty()) {
+    HeapKey hk = pq.top();
+    pq.pop();
+    const PEntry cur = arena[hk.idx];
+    if (seen.count(cur.mask)) continue;
+    seen.insert(cur.mask);
+    if (++pops > max_states) return tn_fail(TN_ERR_NO_PATH, "Algorithm 1: more than %lld states", (long long)max_states);
+    if (cur.m == n) {
+      order.assign(n, -1);
+      int idx = hk.idx, pos = n - 1;
+      while (idx >= 0) { order[pos--] = arena[idx].last; idx = arena[idx].parent; }
+      score = cur.score;
+      return TN_OK;
+    }
+    // members other than the isolated qubit
+    Mask main = cur.mask;
+    if (cur.c >= 0) main.w[cur.c >> 6] &= ~(1ull << (cur.c & 63));
+    for (int i = 0; i < n; ++i) {
+      if (cur.mask.get(i)) continue;
+      const bool adj_s = pg.nb[i].any_and(cur.mask);
+      int8_t c_new = -1;
+      if (connected) {
+        if (cur.c >= 0) {
+          if (!pg.nb[i].get(cur.c) || !pg.nb[i].any_and(main)) continue;   // must reconnect the isolated qubit
+        } else if (!adj_s) {
+          bool dist2 = false;            // an isolated qubit must be reconnectable by the next step
+          for (auto &pr : pg.adj[i])
+            if (pg.nb[pr.first].any_and(cur.mask)) { dist2 = true; break; }
+          if (!dist2) continue;
+          c_new = (int8_t)i;
+        }
+      }
+      double shared = 1, fresh = 1;
+      int rk = cur.rank;
+      for (auto &pr : pg.adj[i]) {
+        const double d = pg.dims[pr.second];
+        if (cur.mask.get(pr.first)) { shared *= d; rk -= d > 1 ? 1 : 0; }
+        else { fresh *= d; rk += d > 1 ? 1 : 0; }
+      }
+      if (max_rank > 0 && rk > max_rank) continue;
+      PEntry e;
+      e.mask = cur.mask;
+      e.mask.set(i);
+      e.score = cur.score + cur.prod_open * fresh;     // Cost = prod of dims over legs of C^S and C^i
+      e.prod_open = cur.prod_open / shared * fresh;
+      e.parent = hk.idx;
+      e.last = (uint8_t)i;
+      e.m = (uint8_t)(cur.m + 1);
+      e.rank = (uint8_t)std::max(rk, 0);
+      e.c = c_new;
+      if ((int64_t)arena.size() >= arena_cap)
+        return tn_fail(TN_ERR_NO_PATH, "Algorithm 1: state arena exceeded %lld entries", (long long)arena_cap);
+      arena.push_back(e);
+      pq.push({e.score, e.m, seq++, (int32_t)arena.size() - 1});
+    }
+  }
+  return tn_fail(TN_ERR_NO_PATH, "Algorithm 1: no path satisfies the assumptions (max_rank %d)", max_rank);
+}
+
+static tn_status path_auto(const PathGraph &pg, const tn_path_opts &o, std::vector<int> &order, double &score,
+                           int64_t &pops, int &rank_used) {
+  const int64_t cap = o.max_states > 0 ? o.max_states : 4000000;
+  if (o.max_rank > 0 || !o.connected) {
+    rank_used = o.max_rank;
+    return alg1(pg, o.max_rank, o.boundary_only != 0, o.connected != 0, cap, order, score, pops);
+  }
+  int maxdeg = 0;
+  for (int q = 0; q < pg.n; ++q) maxdeg = std::max(maxdeg, (int)pg.adj[q].size());
+  int64_t total = 0;
+  tn_status s = TN_ERR_NO_PATH;
+  for (int M = std::max(maxdeg, 1); M <= pg.n + 1; ++M) {
+    int64_t p = 0;
+    s = alg1(pg, M, o.boundary_only != 0, true, cap, order, score, p);
+    total += p;
+    if (s == TN_OK) { rank_used = M; break; }
+  }
+  pops = total;
+  return s;
+}
+
+extern "C" tn_status tn_path_search(const tn_graph *g, const double *dims, const tn_path_opts *opts, int32_t *order,
+                                    double *score, int64_t *states_expanded) {
+  if (!g || !dims || !order) return tn_fail(TN_ERR_ARG, "tn_path_search: NULL argument");
+  std::vector<int> eu, ev;
+  std::vector<std::vector<int>> legs;
+  tn_status s = check_graph(g, eu, ev, legs);
+  if (s != TN_OK) return s;
+  std::vector<double> d(dims, dims + g->n_edges);
+  for (double x : d)
+    if (!(x >= 1)) return tn_fail(TN_ERR_ARG, "tn_path_search: dims must be >= 1");
+  tn_path_opts o = tn_default_opts();
+  if (opts) o = *opts;
+  PathGraph pg = make_pg(g->n_qubits, eu, ev, d);
+  std::vector<int> ord;
+  double sc = 0;
+  int64_t pops = 0;
+  int ru = 0;
+  s = path_auto(pg, o, ord, sc, pops, ru);
+  if (states_expanded) *states_expanded = pops;
+  if (s != TN_OK) return s;
+  for (int i = 0; i < g->n_qubits; ++i) order[i] = ord[i];
+  if (score) *score = sc;
+  return TN_OK;
+}
+
+tn_path_opts tn_default_opts() {
+  tn_path_opts o;
+  std::memset(&o, 0, sizeof o);
+  o.max_rank = 0;
+  o.boundary_only = 1;
+  o.connected = 1;
+  o.max_states = 0;
+  o.n_cuts = -1;
+  o.max_intermediate = 0;
+  o.mem_budget_bytes = 0;
+  return o;
+}
+
+// ---------------------------------------------------------------------------
+// cuts and the plan compiler
+// ---------------------------------------------------------------------------
+// sizes of the intermediates along `order` (elements), with per-edge dims
+static std::vector<double> frontier_sizes(const tn_circuit *c, const std::vector<int> &order,
+                                          const std::vector<double> &dims, std::vector<std::vector<int>> *open_out) {
+  std::vector<char> in(c->n, 0);
+  std::vector<double> sizes;
+  std::vector<char> open(c->ne, 0);
+  for (size_t j = 0; j < order.size(); ++j) {
+    int i = order[j];
+    in[i] = 1;
+    for (int e : c->legs[i]) open[e] = !open[e] ? 1 : 0;   // toggles: opened by first endpoint, closed by second
+    double s = 1;
+    std::vector<int> op;
+    for (int e = 0; e < c->ne; ++e)
+      if (open[e]) { s *= dims[e]; op.push_back(e); }
+    sizes.push_back(s);
+    if (open_out) open_out->push_back(op);
+  }
+  return sizes;
+}
+
+static tn_status choose_cuts(const tn_circuit *c, const std::vector<int> &order, std::vector<double> dims,
+                             int want, double limit, std::vector<int> &cuts) {
+  cuts.clear();
+  for (int it = 0; it < c->ne; ++it) {
+    std::vector<std::vector<int>> open;
+    std::vector<double> sz = frontier_sizes(c, order, dims, &open);
+    double mx = *std::max_element(sz.begin(), sz.end());
+    if (want >= 0 ? (int)cuts.size() >= want : mx <= limit) return TN_OK;
+    // the edge with the largest dim among the open legs of the widest frontier,
+    // preferring edges open in the most oversized frontiers (the thinnest cut)
+    size_t arg = std::max_element(sz.begin(), sz.end()) - sz.begin();
+    int best = -1;
+    double best_key = -1;
+    for (int e : open[arg]) {
+      if (dims[e] <= 1) continue;
+      int cnt = 0;
+      for (size_t j = 0; j < sz.size(); ++j)
+        if (sz[j] > limit && std::find(open[j].begin(), open[j].end(), e) != open[j].end()) ++cnt;
+      double key = cnt * 1e6 + dims[e];
+      if (key > best_key) { best_key = key; best = e; }
+    }
+    if (best < 0) return want >= 0 ? TN_OK : tn_fail(TN_ERR_NO_PATH, "cutting cannot reach the intermediate limit");
+    cuts.push_back(best);
+    dims[best] = 1;
+  }
+  return TN_OK;
+}
+
+static int64_t dc_of(const tn_circuit *c, int e) { return (int64_t)c->ket.dims[e] * c->bra.dims[e]; }
+
+static tn_status compile_plan(tn_circuit *c, tn_plan *p) {
+  const int n = c->n;
+  std::vector<int> pos(n);
+  for (int j = 0; j < n; ++j) pos[p->order[j]] = j;
+  std::vector<char> is_cut(c->ne, 0);
+  for (int e : p->cuts) is_cut[e] = 1;
+  std::vector<int64_t> cut_stride(p->cuts.size());
+  {
+    int64_t s = 1;
+    for (int j = (int)p->cuts.size() - 1; j >= 0; --j) { cut_stride[j] = s; s *= dc_of(c, p->cuts[j]); }
+    p->n_slices = s;
+  }
+  auto &tab = p->tab_host;
+  tab.clear();
+  auto push_tab = [&](const std::vector<int64_t> &v) -> int64_t {
+    int64_t off = (int64_t)tab.size();
+    for (int64_t x : v) tab.push_back((int32_t)x);
+    return off;
+  };
+  // per-node ket/bra strides of each leg
+  auto leg_strides = [&](int i, const Half &h, std::vector<int64_t> &st) -> int64_t {
+    const auto &L = c->legs[i];
+    st.assign(L.size(), 1);
+    int64_t s = 1;
+    for (int j = (int)L.size() - 1; j >= 0; --j) { st[j] = s; s *= h.dims[L[j]]; }
+    return s;
+  };
+  // tables over a list of legs of node i: offsets into ket / bra for each multi-index
+  auto leg_tables = [&](int i, const std::vector<int> &legs, std::vector<int64_t> &ta, std::vector<int64_t> &tb) {
+    std::vector<int64_t> sk, sb;
+    leg_strides(i, c->ket, sk);
+    leg_strides(i, c->bra, sb);
+    int64_t total = 1;
+    for (int e : legs) total *= dc_of(c, e);
+    ta.assign(total, 0);
+    tb.assign(total, 0);
+    for (int64_t idx = 0; idx < total; ++idx) {
+      int64_t r = idx, oa = 0, ob = 0;
+      for (int j = (int)legs.size() - 1; j >= 0; --j) {
+        int e = legs[j];
+        int64_t d = dc_of(c, e), cval = r % d;
+        r /= d;
+        int li = (int)(std::find(c->legs[i].begin(), c->legs[i].end(), e) - c->legs[i].begin());
+        int64_t db = c->bra.dims[e];
+        oa += (cval / db) * sk[li];
+        ob += (cval % db) * sb[li];
+      }
+      ta[idx] = oa;
+      tb[idx] = ob;
+    }
+  };
+  auto slice_tables = [&](int i, std::vector<int64_t> &sa, std::vector<int64_t> &sbv) {
+    std::vector<int64_t> sk, sb;
+    leg_strides(i, c->ket, sk);
+    leg_strides(i, c->bra, sb);
+    sa.assign(p->n_slices, 0);
+    sbv.assign(p->n_slices, 0);
+    for (int64_t s = 0; s < p->n_slices; ++s) {
+      for (size_t j = 0; j < p->cuts.size(); ++j) {
+        int e = p->cuts[j];
+        auto it = std::find(c->legs[i].begin(), c->legs[i].end(), e);
+        if (it == c->legs[i].end()) continue;
+        int li = (int)(it - c->legs[i].begin());
+        int64_t cval = (s / cut_stride[j]) % dc_of(c, e);
+        int64_t db = c->bra.dims[e];
+        sa[s] += (cval / db) * sk[li];
+        sbv[s] += (cval % db) * sb[li];
+      }
+    }
+  };
+  auto new_legs_of = [&](int i, const std::vector<char> &open) {
+    std::vector<int> nl;
+    for (int e : c->legs[i])
+      if (!is_cut[e] && !open[e]) nl.push_back(e);
+    // later-absorbed neighbours first, so the next consumer's legs are innermost
+    std::sort(nl.begin(), nl.end(), [&](int a, int b) {
+      int oa = c->eu[a] == i ? c->ev[a] : c->eu[a];
+      int ob = c->eu[b] == i ? c->ev[b] : c->eu[b];
+      return pos[oa] > pos[ob];
+    });
+    return nl;
+  };
+  p->steps.clear();
+  p->step_mkn.clear();
+  std::vector<char> open(c->ne, 0);
+  std::vector<int> L;   // current leg order of the intermediate
+  double cmacs = 0, bytes = 0;
+  int64_t maxT = 1;
+  for (int j = 0; j < n; ++j) {
+    const int i = p->order[j];
+    StepParams s;
+    std::memset(&s, 0, sizeof s);
+    std::vector<int> shared, rest;
+    for (int e : L) {
+      bool inc = (c->eu[e] == i || c->ev[e] == i);
+      (inc ? shared : rest).push_back(e);
+    }
+    std::vector<int> nl = new_legs_of(i, open);
+    int64_t M = 1, K = 1, N = 1;
+    for (int e : rest) M *= dc_of(c, e);
+    for (int e : shared) K *= dc_of(c, e);
+    for (int e : nl) N *= dc_of(c, e);
+    s.M = M; s.K = K; s.N = N;
+    if ((int)rest.size() > TN_MAXREST) return tn_fail(TN_ERR_UNSUPPORTED, "step %d has %zu rest legs", j, rest.size());
+    // T_in strides
+    std::vector<int64_t> tstr(L.size());
+    {
+      int64_t st = 1;
+      for (int q = (int)L.size() - 1; q >= 0; --q) { tstr[q] = st; st *= dc_of(c, L[q]); }
+    }
+    s.n_rest = (int)rest.size();
+    for (size_t r = 0; r < rest.size(); ++r) {
+      int li = (int)(std::find(L.begin(), L.end(), rest[r]) - L.begin());
+      s.rest_dim[r] = (int)dc_of(c, rest[r]);
+      s.rest_stride[r] = (int)tstr[li];
+    }
+    std::vector<int64_t> ak(K, 0);
+    for (int64_t k = 0; k < K; ++k) {
+      int64_t r = k, off = 0;
+      for (int q = (int)shared.size() - 1; q >= 0; --q) {
+        int li = (int)(std::find(L.begin(), L.end(), shared[q]) - L.begin());
+        int64_t d = dc_of(c, shared[q]);
+        off += (r % d) * tstr[li];
+        r /= d;
+      }
+      ak[k] = off;
+    }
+    std::vector<int64_t> ka, kb, na, nb, sa, sb;
+    leg_tables(i, shared, ka, kb);
+    leg_tables(i, nl, na, nb);
+    slice_tables(i, sa, sb);
+    s.t_ak = push_tab(ak);
+    s.t_bka = push_tab(ka);
+    s.t_bkb = push_tab(kb);
+    s.t_bna = push_tab(na);
+    s.t_bnb = push_tab(nb);
+    s.t_sa = push_tab(sa);
+    s.t_sb = push_tab(sb);
+    std::vector<int64_t> skk, sbb;
+    s.ket_sig = leg_strides(i, c->ket, skk);
+    s.bra_sig = leg_strides(i, c->bra, sbb);
+    s.ket_off = c->ket.node_off[i];
+    s.bra_off = c->bra.node_off[i];
+    p->steps.push_back(s);
+    p->step_mkn.push_back({M, K, N});
+    if (j > 0) {
+      cmacs += (double)M * K * N;
+      bytes += 8.0 * ((double)M * K + (double)M * N);
+    }
+    maxT = std::max(maxT, M * N);
+    // next leg order
+    for (int e : shared) open[e] = 0;
+    for (int e : nl) open[e] = 1;
+    L = rest;
+    L.insert(L.end(), nl.begin(), nl.end());
+  }
+  if (maxT >= (1LL << 31) || (int64_t)tab.size() >= (1LL << 31))
+    return tn_fail(TN_ERR_UNSUPPORTED, "intermediate of %lld elements exceeds the 2^31 index range; add cuts",
+                   (long long)maxT);
+  p->maxT = maxT;
+  p->cmacs = cmacs * (double)p->n_slices;
+  p->bytes = bytes * (double)p->n_slices;
+  return TN_OK;
+}
+
+static void fill_info(const tn_plan *p, tn_plan_info *info) {
+  if (!info) return;
+  std::memset(info, 0, sizeof *info);
+  info->n_qubits = p->c->n;
+  info->n_steps = p->c->n - 1;
+  info->n_cuts = (int32_t)p->cuts.size();
+  info->n_slices = p->n_slices;
+  info->score = p->score;
+  info->cmacs = p->cmacs;
+  info->flops = 8.0 * p->cmacs;
+  info->bytes_c64 = p->bytes;
+  info->max_intermediate = p->maxT;
+  info->states_expanded = p->pops;
+  info->max_rank_used = p->rank_used;
+  info->chunk_bitstrings = p->chunk[0];
+  info->workspace_bytes = p->ws_bytes[0];
+}
+
+// workspace of `chunk` bitstrings with `slices` slices each per launch group
+int64_t plan_ws_bytes(const tn_plan *p, int kind, int64_t chunk, int64_t slices) {
+  const tn_circuit *c = p->c;
+  const int64_t el = kind == 0 ? 16 : 8;
+  const int words = (c->n + 63) / 64;
+  int64_t b = 0;
+  b += chunk * words * 8;                                   // bits
+  b += chunk * c->bra.item_elems * 16;                      // bra FP64
+  if (kind) b += chunk * c->bra.item_elems * 8;             // bra c64 copy
+  b += chunk * std::max<int64_t>(c->bra.max_work, 1) * 16;  // SVD work beyond shared memory
+  b += 2 * chunk * slices * p->maxT * el;                   // ping-pong intermediates
+  b += chunk * 16 + 4096;                                   // results, flags
+  return b;
+}
+
+extern "C" tn_status tn_path(tn_circuit *c, const tn_path_opts *opts, tn_plan **out, tn_plan_info *info) {
+  if (!c || !out) return tn_fail(TN_ERR_ARG, "tn_path: NULL argument");
+  *out = nullptr;
+  if (!c->evolved) return tn_fail(TN_ERR_STATE, "tn_path: call tn_evolve_two_sided first");
+  tn_path_opts o = opts ? *opts : tn_default_opts();
+  const double limit = o.max_intermediate > 0 ? (double)o.max_intermediate : (double)(1LL << 24);
+  std::vector<double> dims(c->ne);
+  for (int e = 0; e < c->ne; ++e) dims[e] = (double)dc_of(c, e);
+  tn_plan *p = new tn_plan();
+  p->c = c;
+  p->generation = c->generation;
+  PathGraph pg = make_pg(c->n, c->eu, c->ev, dims);
+  int64_t pops = 0;
+  tn_status s = path_auto(pg, o, p->order, p->score, pops, p->rank_used);
+  p->pops = pops;
+  if (s != TN_OK) { delete p; return s; }
+  // cuts: explicit, counted or automatic (thinnest frontier first), then the path of the cut network
+  if (o.n_cut_edges > 0) {
+    if (!o.cut_edges) { delete p; return tn_fail(TN_ERR_ARG, "tn_path: cut_edges is NULL"); }
+    for (int j = 0; j < o.n_cut_edges; ++j) {
+      int e = o.cut_edges[j];
+      if (e < 0 || e >= c->ne || std::find(p->cuts.begin(), p->cuts.end(), e) != p->cuts.end()) {
+        delete p;
+        return tn_fail(TN_ERR_ARG, "tn_path: bad or repeated cut edge %d", e);
+      }
+      p->cuts.push_back(e);
+    }
+  } else {
+    s = choose_cuts(c, p->order, dims, o.n_cuts, limit, p->cuts);
+    if (s != TN_OK) { delete p; return s; }
+  }
+  if (!p->cuts.empty()) {
+    std::vector<double> cd2 = dims;
+    for (int e : p->cuts) cd2[e] = 1;
+    PathGraph pg2 = make_pg(c->n, c->eu, c->ev, cd2);
+    s = path_auto(pg2, o, p->order, p->score, pops, p->rank_used);
+    p->pops += pops;
+    if (s != TN_OK) { delete p; return s; }
+  }
+  s = compile_plan(c, p);
+  if (s != TN_OK) { delete p; return s; }
+  const double budget = o.mem_budget_bytes > 0 ? o.mem_budget_bytes : 8.0 * (1ull << 30);
+  for (int kind = 0; kind < 2; ++kind) {
+    // as many whole bitstrings (all slices) as fit; else one bitstring and groups of its slices
+    const int64_t grid_cap = 1LL << 40;   // items * maxT bound keeping every launch grid < 2^31 CTAs
+    int64_t per = plan_ws_bytes(p, kind, 1, p->n_slices);
+    int64_t ch = (int64_t)std::floor(budget / (double)per);
+    ch = std::min<int64_t>(ch, 1 << 16);
+    while (ch > 1 && ch * p->n_slices * std::max<int64_t>(p->maxT, 1) >= grid_cap) ch /= 2;
+    int64_t sc = p->n_slices;
+    if (ch < 1) {
+      ch = 1;
+      const int64_t per_slice = plan_ws_bytes(p, kind, 1, 2) - plan_ws_bytes(p, kind, 1, 1);
+      sc = (int64_t)std::floor((budget - (double)plan_ws_bytes(p, kind, 1, 0)) / (double)per_slice);
+      sc = std::max<int64_t>(1, std::min(sc, p->n_slices));
+      while (sc > 1 && sc * std::max<int64_t>(p->maxT, 1) >= grid_cap) sc /= 2;
+    }
+    p->chunk[kind] = (int)ch;
+    p->slice_chunk[kind] = sc;
+    p->ws_bytes[kind] = plan_ws_bytes(p, kind, ch, sc);
+  }
+  // upload tables
+  cudaStream_t st = 0;
+  s = c->mem.ensure(p->tab_dev, std::max<size_t>(p->tab_host.size(), 1) * sizeof(int32_t), st);
+  if (s != TN_OK) { delete p; return s; }
+  cudaError_t ce = cudaMemcpy(p->tab_dev.p, p->tab_host.data(), p->tab_host.size() * sizeof(int32_t),
+                              cudaMemcpyHostToDevice);
+  if (ce != cudaSuccess) {
+    c->mem.release(p->tab_dev);
+    delete p;
+    return tn_fail(TN_ERR_CUDA, "table upload: %s", cudaGetErrorString(ce));
+  }
+  fill_info(p, info);
+  *out = p;
+  return TN_OK;
+}
+
+extern "C" tn_status tn_plan_details(const tn_plan *p, int32_t *order, int32_t *cuts, int64_t *steps) {
+  if (!p) return tn_fail(TN_ERR_ARG, "tn_plan_details: NULL plan");
+  if (order)
+    for (int j = 0; j < p->c->n; ++j) order[j] = p->order[j];
+  if (cuts)
+    for (size_t j = 0; j < p->cuts.size(); ++j) cuts[j] = p->cuts[j];
+  if (steps)
+    for (size_t j = 1; j < p->step_mkn.size(); ++j)
+      for (int t = 0; t < 3; ++t) steps[3 * (j - 1) + t] = p->step_mkn[j][t];
+  return TN_OK;
+}
+
+// ---------------------------------------------------------------------------
+// tn_amplitudes
+// ---------------------------------------------------------------------------
+void ws_release(DevMem &mem, Workspace &w) {
+  mem.release(w.bits);
+  mem.release(w.bra64);
+  mem.release(w.bra32);
+  mem.release(w.gwork);
+  mem.release(w.t0);
+  mem.release(w.t1);
+  mem.release(w.res);
+  mem.release(w.err);
+}
+
+tn_status ws_ensure(tn_plan *p, Workspace &w, int kind, cudaStream_t st) {
+  tn_circuit *c = p->c;
+  DevMem &mem = c->mem;
+  const int64_t ch = p->chunk[kind];
+  const int64_t sc = p->slice_chunk[kind];
+  const int words = (c->n + 63) / 64;
+  const int64_t el = kind == 0 ? 16 : 8;
+  tn_status s;
+  if ((s = mem.ensure(w.bits, ch * words * 8, st)) != TN_OK) return s;
+  if ((s = mem.ensure(w.bra64, ch * c->bra.item_elems * 16, st)) != TN_OK) return s;
+  if (kind && (s = mem.ensure(w.bra32, ch * c->bra.item_elems * 8, st)) != TN_OK) return s;
+  if ((s = mem.ensure(w.gwork, ch * std::max<int64_t>(c->bra.max_work, 1) * 16, st)) != TN_OK) return s;
+  if ((s = mem.ensure(w.t0, ch * sc * p->maxT * el, st)) != TN_OK) return s;
+  if ((s = mem.ensure(w.t1, ch * sc * p->maxT * el, st)) != TN_OK) return s;
+  if ((s = mem.ensure(w.res, ch * 16, st)) != TN_OK) return s;
+  if ((s = mem.ensure(w.err, 64, st)) != TN_OK) return s;
+  w.chunk = (int)ch;
+  w.slice_chunk = sc;
+  return TN_OK;
+}
+
+static bool is_device_ptr(const void *p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+tn_status run_amplitudes(tn_plan *p, Workspace &w, const uint64_t *bits, int64_t n, tn_precision prec,
+                         tn_c128 *out, cudaStream_t st) {
+  tn_circuit *c = p->c;
+  if (p->generation != c->generation) return tn_fail(TN_ERR_STATE, "plan is stale: the circuit was re-evolved");
+  if (prec < TN_FP64 || prec > TN_BF16X3) return tn_fail(TN_ERR_ARG, "unknown precision %d", (int)prec);
+  if (n == 0) return TN_OK;
+  if (n < 0 || !bits || !out) return tn_fail(TN_ERR_ARG, "tn_amplitudes: bad arguments");
+  const int kind = prec == TN_FP64 ? 0 : 1;
+  tn_status s = ws_ensure(p, w, kind, st);
+  if (s != TN_OK) return s;
+  const int words = (c->n + 63) / 64;
+  const bool bits_dev = is_device_ptr(bits), out_dev = is_device_ptr(out);
+  const int64_t S = p->n_slices;
+  CUDA_TRY(cudaMemsetAsync(w.err.p, 0, 2 * sizeof(int), st));
+  for (int64_t start = 0; start < n; start += w.chunk) {
+    const int64_t nb = std::min<int64_t>(w.chunk, n - start);
+    CUDA_TRY(cudaMemcpyAsync(w.bits.p, bits + start * words, nb * words * 8,
+                             bits_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    s = run_half(c->bra, c->n, (double2 *)w.bra64.p, (int)nb, (const int64_t *)c->bra_off_dev.p,
+                 (const uint64_t *)w.bits.p, words, (double2 *)w.gwork.p, (int *)w.err.p, st);
+    if (s != TN_OK) return s;
+    const void *ket = kind ? c->ket_c64.p : c->ket_dev.p;
+    const void *bra = w.bra64.p;
+    if (kind) {
+      ProfScope ps("to_c64", st, 24.0 * nb * c->bra.item_elems, 0);
+      CUDA_TRY(launch_to_c64((const double2 *)w.bra64.p, (float2 *)w.bra32.p, nb * c->bra.item_elems, st));
+      bra = w.bra32.p;
+    }
+    for (int64_t s0 = 0; s0 < S; s0 += w.slice_chunk) {
+      const int64_t sg = std::min<int64_t>(w.slice_chunk, S - s0);
+      ContractArgs a;
+      a.tab = (const int32_t *)p->tab_dev.p;
+      a.n_slices = sg;
+      a.slice0 = s0;
+      a.items = nb * sg;
+      a.t_stride = p->maxT;
+      a.bra_stride = c->bra.item_elems;
+      void *tin = w.t0.p, *tout = w.t1.p;
+      const double el = kind ? 8.0 : 16.0;
+      {
+        ProfScope ps(kind ? "overlap_form_c64" : "overlap_form_c128", st, el * a.items * p->steps[0].N, 0);
+        if (kind) CUDA_TRY(launch_form<float>(p->steps[0], a, ket, bra, tin, st));
+        else CUDA_TRY(launch_form<double>(p->steps[0], a, ket, bra, tin, st));
+      }
+      for (size_t j = 1; j < p->steps.size(); ++j) {
+        const StepParams &sp = p->steps[j];
+        const double items = (double)a.items;
+        const double by = el * items * ((double)sp.M * sp.K + (double)sp.M * sp.N);
+        const double fl = 8.0 * items * (double)sp.M * sp.K * sp.N;
+        if (prec == TN_FP64) {
+          ProfScope ps("contract_step_fp64", st, by, fl);
+          CUDA_TRY(launch_step<double>(sp, a, ket, bra, tin, tout, st));
+        } else if (prec == TN_FP32 || !tc_step_supported(sp)) {
+          ProfScope ps(prec == TN_FP32 ? "contract_step_fp32" : "contract_step_fp32_tc_fallback", st, by, fl);
+          CUDA_TRY(launch_step<float>(sp, a, ket, bra, tin, tout, st));
+        } else {
+          ProfScope ps("contract_step_tcgen05", st, by, fl);
+          CUDA_TRY(launch_step_tc((int)prec, sp, a, (const float2 *)ket, (const float2 *)bra, (const float2 *)tin,
+                                  (float2 *)tout, (int *)w.err.p + 1, st));
+        }
+        std::swap(tin, tout);
+      }
+      {
+        ProfScope ps("slice_sum_fp64", st, (el * sg + 16.0) * nb, 0);
+        if (kind) CUDA_TRY(launch_slice_sum<float>(tin, p->maxT, nb, sg, s0 > 0, (double2 *)w.res.p, st));
+        else CUDA_TRY(launch_slice_sum<double>(tin, p->maxT, nb, sg, s0 > 0, (double2 *)w.res.p, st));
+      }
+    }
+    CUDA_TRY(cudaMemcpyAsync(out + start, w.res.p, nb * sizeof(tn_c128),
+                             out_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  }
+  int err[2] = {0, 0};
+  CUDA_TRY(cudaMemcpyAsync(err, w.err.p, sizeof err, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  if (err[0]) return tn_fail(TN_ERR_TIMEOUT, "Jacobi SVD did not converge within its sweep limit (bra half)");
+  if (err[1]) return tn_fail(TN_ERR_TIMEOUT, "tensor-core GEMM: a bounded pipeline wait expired (code %d)", err[1]);
+  return TN_OK;
+}
+
+extern "C" tn_status tn_amplitudes(tn_plan *p, const uint64_t *bits, int64_t n, tn_precision prec, tn_c128 *out,
+                                   void *cuda_stream) {
+  if (!p) return tn_fail(TN_ERR_ARG, "tn_amplitudes: NULL plan");
+  return run_amplitudes(p, p->ws, bits, n, prec, out, (cudaStream_t)cuda_stream);
+}
+
+extern "C" void tn_plan_free(tn_plan *p) {
+  if (!p) return;
+  cudaDeviceSynchronize();
+  ws_release(p->c->mem, p->ws);
+  p->c->mem.release(p->tab_dev);
+  delete p;
+}

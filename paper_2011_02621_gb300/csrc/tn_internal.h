@@ -1,0 +1,96 @@
+// Internal declarations shared by the host code (host.cpp, server.cpp) and the
+// CUDA translation units (evolve.cu, contract.cu, tc_gemm.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/tn.h"
+
+#define TN_MAXLEG 8     // legs (incident edges) per node
+#define TN_MAXREST 32   // rest legs of one contraction step
+
+// ---------------------------------------------------------------------------
+// evolution (Eqs. result1/result2, svd/svd2)
+// ---------------------------------------------------------------------------
+// Node tensors of one half live in a per-item region; node q at offset
+// node_off[q] (complex elements), layout [sigma, leg_0, ..., leg_{n-1}]
+// row-major with legs in increasing edge id.
+struct GateParams {
+  int64_t off_k, off_l;        // node offsets within an item region
+  int nk, nl;                  // leg counts of k and l
+  int dk[TN_MAXLEG];           // dims of k's legs before the gate (leg pk has din)
+  int dl[TN_MAXLEG];
+  int pk, pl;                  // position of the shared edge among the legs
+  int din, chi_o, dout;        // bond dim before the gate, gate rank, bond bound after
+  int sv_is_k;                 // 1: SVD node k and absorb S V into l; 0: the reverse
+  int m_k, m_l, n;             // rows of the matricised k and l (2*prod other legs), n = din*chi_o
+  int use_smem;                // work buffers in dynamic shared memory
+  double cutoff;               // keep singular values > cutoff * s_0
+  double2 P[16];               // P[s'][s][a] at (s'*2+s)*4+a  (Eq. gatesplit)
+  double2 Q[16];
+  int64_t work_stride;         // per-item global work size (complex elements) when !use_smem
+};
+
+struct Apply1Params {
+  int64_t off;                 // node offset
+  int64_t size_rest;           // prod of the node's leg dims
+  double2 u[4];                // 2x2, rows = outputs
+};
+
+// work (complex elements) the gate kernel needs per item
+int64_t gate_work_elems(const GateParams &g);
+
+cudaError_t launch_init_product(double2 *base, int64_t item_stride, int items, const int64_t *node_off_dev,
+                                int n_qubits, const uint64_t *bits, int words, cudaStream_t st);
+cudaError_t launch_gate(const GateParams &g, double2 *base, int64_t item_stride, int items,
+                        double2 *gwork, int *errflag, cudaStream_t st);
+cudaError_t launch_apply1(const Apply1Params &a, double2 *base, int64_t item_stride, int items, cudaStream_t st);
+cudaError_t launch_to_c64(const double2 *src, float2 *dst, int64_t n, cudaStream_t st);
+cudaError_t launch_pack_bits(const uint64_t *src, uint64_t *dst, int64_t n_words, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// contraction (Eq. overlap; path-ordered steps of Algorithm 1; cutting)
+// ---------------------------------------------------------------------------
+// One absorption step: T_out[item][m*N + n] = sum_k T_in[item][row(m) + ak[k]] * C[k][n]
+// with C[k][n] = sum_sigma ket[ka(k,n) + sigma*ket_sig] * bra_b[kb(k,n) + sigma*bra_sig]
+// (Eq. overlap formed on the fly), item = bitstring * n_slices + slice.
+struct StepParams {
+  int64_t M, K, N;
+  int n_rest;
+  int rest_dim[TN_MAXREST];     // rest legs of T_in, slowest first
+  int rest_stride[TN_MAXREST];  // their strides in T_in
+  int64_t ket_off, ket_sig;     // node tensor offset / sigma stride in the ket buffer
+  int64_t bra_off, bra_sig;     // same in one bitstring's bra region
+  // offsets of the int32 tables in the plan's table buffer
+  int64_t t_ak, t_bka, t_bkb, t_bna, t_bnb, t_sa, t_sb;
+};
+
+struct ContractArgs {
+  const int32_t *tab;           // plan table buffer (device)
+  int64_t n_slices;             // slices per bitstring in this launch group
+  int64_t slice0;               // first slice of the group (global slice index)
+  int64_t items;                // bitstrings_in_chunk * n_slices
+  int64_t t_stride;             // elements per item in T buffers
+  int64_t bra_stride;           // elements per bitstring region of the bra buffer
+};
+
+// precision-templated launchers (R = double or float)
+template <typename R>
+cudaError_t launch_form(const StepParams &s, const ContractArgs &a, const void *ket, const void *bra,
+                        void *t_out, cudaStream_t st);
+template <typename R>
+cudaError_t launch_step(const StepParams &s, const ContractArgs &a, const void *ket, const void *bra,
+                        const void *t_in, void *t_out, cudaStream_t st);
+// out[b] (+)= sum over the group's slices, in slice order, in FP64 (accumulate: add to out)
+template <typename R>
+cudaError_t launch_slice_sum(const void *res, int64_t items_stride, int64_t n_bits, int64_t n_slices,
+                             int accumulate, double2 *out, cudaStream_t st);
+
+// tensor-core step (tcgen05): prec = TN_TF32, TN_TF32X3 or TN_BF16X3
+cudaError_t launch_step_tc(int prec, const StepParams &s, const ContractArgs &a, const float2 *ket,
+                           const float2 *bra, const float2 *t_in, float2 *t_out, int *errflag, cudaStream_t st);
+bool tc_step_supported(const StepParams &s);
+
+// launch accounting
+void tn_count_launch(int64_t k);

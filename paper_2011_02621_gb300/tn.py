@@ -1,0 +1,420 @@
+"""Thin Python binding of the C ABI in include/tn.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of the method: all compute runs in libtn.so's CUDA kernels. The
+library is loaded from this package directory; importing this module when
+libtn.so is missing raises immediately (there is no CPU fallback).
+
+Device memory for the library comes from PyTorch's caching allocator unless
+``allocator=None`` is passed to :func:`tn_build`; streams are PyTorch streams
+(or raw ``cudaStream_t`` integers).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtn.so")
+
+TN_OK, TN_ERR_ARG, TN_ERR_GRAPH, TN_ERR_OOM, TN_ERR_NO_PATH, TN_ERR_STATE, TN_ERR_CUDA, TN_ERR_TIMEOUT, \
+    TN_ERR_UNSUPPORTED = range(9)
+STATUS_NAMES = {0: "TN_OK", 1: "TN_ERR_ARG", 2: "TN_ERR_GRAPH", 3: "TN_ERR_OOM", 4: "TN_ERR_NO_PATH",
+                5: "TN_ERR_STATE", 6: "TN_ERR_CUDA", 7: "TN_ERR_TIMEOUT", 8: "TN_ERR_UNSUPPORTED"}
+PRECISIONS = {"fp64": 0, "fp32": 1, "tf32": 2, "tf32x3": 3, "bf16x3": 4}
+
+
+class TNError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class c128(C.Structure):
+    _fields_ = [("re", C.c_double), ("im", C.c_double)]
+
+
+class tn_graph(C.Structure):
+    _fields_ = [("n_qubits", C.c_int32), ("n_edges", C.c_int32), ("edges", C.POINTER(C.c_int32))]
+
+
+class tn_gate(C.Structure):
+    _fields_ = [("cycle", C.c_int32), ("arity", C.c_int32), ("q", C.c_int32 * 2), ("m", c128 * 16)]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+
+
+class tn_allocator(C.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("ctx", C.c_void_p)]
+
+
+class tn_path_opts(C.Structure):
+    _fields_ = [("max_rank", C.c_int32), ("boundary_only", C.c_int32), ("connected", C.c_int32),
+                ("max_states", C.c_int64), ("n_cuts", C.c_int32), ("cut_edges", C.POINTER(C.c_int32)),
+                ("n_cut_edges", C.c_int32), ("max_intermediate", C.c_int64), ("mem_budget_bytes", C.c_double)]
+
+
+class tn_plan_info(C.Structure):
+    _fields_ = [("n_qubits", C.c_int32), ("n_steps", C.c_int32), ("n_cuts", C.c_int32), ("n_slices", C.c_int64),
+                ("score", C.c_double), ("cmacs", C.c_double), ("flops", C.c_double), ("bytes_c64", C.c_double),
+                ("max_intermediate", C.c_int64), ("states_expanded", C.c_int64), ("max_rank_used", C.c_int32),
+                ("chunk_bitstrings", C.c_int32), ("workspace_bytes", C.c_int64)]
+
+
+class tn_server_cfg(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_double), ("max_inflight", C.c_int32), ("n_streams", C.c_int32)]
+
+
+class tn_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64), ("rejected", C.c_int64),
+                ("amplitudes", C.c_int64), ("busy_seconds", C.c_double), ("p50_latency_s", C.c_double),
+                ("p99_latency_s", C.c_double), ("max_inflight_seen", C.c_double),
+                ("peak_admitted_bytes", C.c_double)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: run paper_2011_02621_gb300.build.build() first "
+                          "(this library has no CPU fallback)")
+    lib = C.CDLL(LIB_PATH)
+    vp, i32, i64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+    sig = {
+        "tn_build": (i32, [C.POINTER(tn_graph), C.POINTER(tn_gate), i64, C.POINTER(tn_allocator), C.POINTER(vp)]),
+        "tn_evolve_two_sided": (i32, [vp, i32, i32, dbl, vp]),
+        "tn_circuit_bond_dims": (i32, [vp, i32, C.POINTER(i32)]),
+        "tn_path": (i32, [vp, C.POINTER(tn_path_opts), C.POINTER(vp), C.POINTER(tn_plan_info)]),
+        "tn_plan_details": (i32, [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i64)]),
+        "tn_amplitudes": (i32, [vp, vp, i64, i32, vp, vp]),
+        "tn_launch_count": (i64, [i32]),
+        "tn_profile_enable": (i32, [i32]),
+        "tn_profile_read": (i32, [i32, C.c_char_p, i32, C.POINTER(i64), C.POINTER(dbl), C.POINTER(dbl),
+                                 C.POINTER(dbl)]),
+        "tn_circuit_free": (None, [vp]),
+        "tn_plan_free": (None, [vp]),
+        "tn_last_error": (C.c_char_p, []),
+        "tn_gate_split": (i32, [C.POINTER(c128), C.POINTER(c128), C.POINTER(c128), C.POINTER(i32)]),
+        "tn_path_search": (i32, [C.POINTER(tn_graph), C.POINTER(dbl), C.POINTER(tn_path_opts), C.POINTER(i32),
+                                 C.POINTER(dbl), C.POINTER(i64)]),
+        "tn_server_create": (i32, [C.POINTER(tn_server_cfg), C.POINTER(vp)]),
+        "tn_server_submit": (i32, [vp, vp, vp, i64, i32, vp, C.POINTER(C.c_uint64)]),
+        "tn_server_wait": (i32, [vp, C.c_uint64, i64]),
+        "tn_server_stats_get": (i32, [vp, C.POINTER(tn_server_stats)]),
+        "tn_server_free": (None, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+LIB = _load()
+
+
+def _check(status: int):
+    if status != TN_OK:
+        raise TNError(status, LIB.tn_last_error().decode(errors="replace"))
+
+
+def tn_last_error() -> str:
+    return LIB.tn_last_error().decode(errors="replace")
+
+
+def tn_launch_count(reset: bool = False) -> int:
+    return int(LIB.tn_launch_count(1 if reset else 0))
+
+
+def tn_profile_enable(on: bool = True):
+    _check(LIB.tn_profile_enable(1 if on else 0))
+
+
+def tn_profile_read() -> dict:
+    """{kind: {launches, ms, bytes, flops}} for every kernel kind recorded since tn_profile_enable."""
+    out = {}
+    i = 0
+    while True:
+        name = C.create_string_buffer(64)
+        la, ms, by, fl = C.c_int64(), C.c_double(), C.c_double(), C.c_double()
+        st = LIB.tn_profile_read(i, name, 64, C.byref(la), C.byref(ms), C.byref(by), C.byref(fl))
+        if st != TN_OK:
+            return out
+        out[name.value.decode()] = dict(launches=la.value, ms=ms.value, bytes=by.value, flops=fl.value)
+        i += 1
+
+
+# --------------------------------------------------------------------------
+# allocator bridge to PyTorch's caching allocator
+# --------------------------------------------------------------------------
+_torch_alloc = None
+
+
+def torch_allocator():
+    """A tn_allocator whose callbacks call torch.cuda.caching_allocator_alloc / _delete."""
+    global _torch_alloc
+    if _torch_alloc is None:
+        import torch
+
+        def _alloc(size, stream, ctx):
+            try:
+                return int(torch.cuda.caching_allocator_alloc(int(size), stream=int(stream or 0)))
+            except Exception:
+                return None
+
+        def _free(ptr, size, stream, ctx):
+            torch.cuda.caching_allocator_delete(int(ptr))
+
+        a_fn, f_fn = ALLOC_FN(_alloc), FREE_FN(_free)
+        _torch_alloc = (tn_allocator(a_fn, f_fn, None), a_fn, f_fn)
+    return _torch_alloc[0]
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            pass
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+# --------------------------------------------------------------------------
+# handles
+# --------------------------------------------------------------------------
+class Circuit:
+    """Owns a tn_circuit*; freed with tn_circuit_free."""
+
+    def __init__(self, ptr, n_qubits, n_edges, keep):
+        self.ptr = ptr
+        self.n_qubits = n_qubits
+        self.n_edges = n_edges
+        self._keep = keep
+
+    def __del__(self):
+        if getattr(self, "ptr", None):
+            LIB.tn_circuit_free(self.ptr)
+            self.ptr = None
+
+
+class Plan:
+    """Owns a tn_plan*; keeps its circuit alive; freed with tn_plan_free."""
+
+    def __init__(self, ptr, circuit, info: dict):
+        self.ptr = ptr
+        self.circuit = circuit
+        self.info = info
+
+    def __del__(self):
+        if getattr(self, "ptr", None):
+            LIB.tn_plan_free(self.ptr)
+            self.ptr = None
+
+
+def _graph_struct(n: int, edges):
+    e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1, 2))
+    g = tn_graph(int(n), int(e.shape[0]), e.ctypes.data_as(C.POINTER(C.c_int32)))
+    return g, e
+
+
+def gates_array(gates) -> C.Array:
+    """Marshal gate objects (``.cycle``, ``.qubits``, ``.m``) into a tn_gate array."""
+    arr = (tn_gate * max(len(gates), 1))()
+    for i, g in enumerate(gates):
+        arr[i].cycle = int(g.cycle)
+        arr[i].arity = len(g.qubits)
+        arr[i].q[0] = int(g.qubits[0])
+        arr[i].q[1] = int(g.qubits[1]) if len(g.qubits) > 1 else -1
+        m = np.asarray(g.m, dtype=np.complex128).ravel()
+        for j, x in enumerate(m):
+            arr[i].m[j].re = float(x.real)
+            arr[i].m[j].im = float(x.imag)
+    return arr
+
+
+def tn_build(n_qubits: int, edges, gates, allocator="torch") -> Circuit:
+    g, e = _graph_struct(n_qubits, edges)
+    arr = gates_array(gates)
+    alloc = torch_allocator() if allocator == "torch" else allocator
+    out = C.c_void_p()
+    _check(LIB.tn_build(C.byref(g), arr, len(gates), C.byref(alloc) if alloc is not None else None, C.byref(out)))
+    return Circuit(out, int(n_qubits), int(e.shape[0]), (alloc,))
+
+
+def tn_evolve_two_sided(c: Circuit, split_cycle: int, chi_max: int = 0, cutoff_rel: float = 1e-12, stream=None):
+    _check(LIB.tn_evolve_two_sided(c.ptr, int(split_cycle), int(chi_max), float(cutoff_rel), _stream_handle(stream)))
+
+
+def tn_circuit_bond_dims(c: Circuit, side: int) -> np.ndarray:
+    out = np.zeros(max(c.n_edges, 1), dtype=np.int32)
+    _check(LIB.tn_circuit_bond_dims(c.ptr, int(side), out.ctypes.data_as(C.POINTER(C.c_int32))))
+    return out[: c.n_edges]
+
+
+def _opts(max_rank=0, boundary_only=True, connected=True, max_states=0, n_cuts=-1, cut_edges=None,
+          max_intermediate=0, mem_budget_bytes=0.0):
+    o = tn_path_opts()
+    o.max_rank = int(max_rank)
+    o.boundary_only = 1 if boundary_only else 0
+    o.connected = 1 if connected else 0
+    o.max_states = int(max_states)
+    o.n_cuts = int(n_cuts)
+    keep = None
+    if cut_edges is not None and len(cut_edges):
+        keep = np.ascontiguousarray(np.asarray(cut_edges, dtype=np.int32))
+        o.cut_edges = keep.ctypes.data_as(C.POINTER(C.c_int32))
+        o.n_cut_edges = int(keep.size)
+    o.max_intermediate = int(max_intermediate)
+    o.mem_budget_bytes = float(mem_budget_bytes)
+    return o, keep
+
+
+def _info_dict(info: tn_plan_info) -> dict:
+    return {name: getattr(info, name) for name, _ in tn_plan_info._fields_}
+
+
+def tn_path(c: Circuit, **opts) -> Plan:
+    o, keep = _opts(**opts)
+    out = C.c_void_p()
+    info = tn_plan_info()
+    _check(LIB.tn_path(c.ptr, C.byref(o), C.byref(out), C.byref(info)))
+    return Plan(out, c, _info_dict(info))
+
+
+def tn_plan_details(p: Plan):
+    n = p.info["n_qubits"]
+    order = np.zeros(n, dtype=np.int32)
+    cuts = np.zeros(max(p.info["n_cuts"], 1), dtype=np.int32)
+    steps = np.zeros((max(p.info["n_steps"], 1), 3), dtype=np.int64)
+    _check(LIB.tn_plan_details(p.ptr, order.ctypes.data_as(C.POINTER(C.c_int32)),
+                               cuts.ctypes.data_as(C.POINTER(C.c_int32)),
+                               steps.ctypes.data_as(C.POINTER(C.c_int64))))
+    return order, cuts[: p.info["n_cuts"]], steps[: p.info["n_steps"]]
+
+
+def pack_bits(bits: np.ndarray) -> np.ndarray:
+    """(B, n) 0/1 -> (B, ceil(n/64)) uint64 words, bit q of word q//64 = s_q."""
+    bits = np.asarray(bits, dtype=np.uint64)
+    B, n = bits.shape
+    words = max((n + 63) // 64, 1)
+    out = np.zeros((B, words), dtype=np.uint64)
+    for q in range(n):
+        out[:, q // 64] |= bits[:, q] << np.uint64(q % 64)
+    return out
+
+
+def tn_amplitudes(p: Plan, bits, prec: str = "fp64", out=None, stream=None):
+    """Amplitudes of the bitstrings ``bits``.
+
+    ``bits``: numpy (B, n) 0/1 array, numpy (B, words) uint64 packed words, or a
+    torch int64/uint64 tensor of packed words (host or device). ``out``: None
+    (returns a numpy complex128 array) or a torch complex128 tensor of B
+    entries (host or device) that receives the results.
+    """
+    n = p.circuit.n_qubits
+    words = max((n + 63) // 64, 1)
+    keep = None
+    if hasattr(bits, "data_ptr"):
+        B = int(bits.shape[0])
+        bptr = bits.data_ptr()
+        keep = bits
+    else:
+        b = np.asarray(bits)
+        if b.dtype != np.uint64 or b.ndim != 2 or b.shape[1] != words:
+            b = pack_bits(b.reshape(-1, n))
+        b = np.ascontiguousarray(b)
+        B = int(b.shape[0])
+        bptr = b.ctypes.data
+        keep = b
+    if out is None:
+        res = np.zeros(B, dtype=np.complex128)
+        optr = res.ctypes.data
+    else:
+        res = out
+        optr = out.data_ptr()
+    _check(LIB.tn_amplitudes(p.ptr, C.c_void_p(bptr), B, PRECISIONS[prec], C.c_void_p(optr), _stream_handle(stream)))
+    del keep
+    return res
+
+
+def tn_gate_split(m):
+    mm = (c128 * 16)()
+    for j, x in enumerate(np.asarray(m, dtype=np.complex128).ravel()):
+        mm[j].re, mm[j].im = float(x.real), float(x.imag)
+    P, Q = (c128 * 16)(), (c128 * 16)()
+    chi = C.c_int32()
+    _check(LIB.tn_gate_split(mm, P, Q, C.byref(chi)))
+    to = lambda a: np.array([a[j].re + 1j * a[j].im for j in range(16)]).reshape(2, 2, 4)
+    return to(P), to(Q), int(chi.value)
+
+
+def tn_path_search(n_qubits: int, edges, dims, **opts):
+    g, e = _graph_struct(n_qubits, edges)
+    d = np.ascontiguousarray(np.asarray(dims, dtype=np.float64))
+    o, keep = _opts(**opts)
+    order = np.zeros(n_qubits, dtype=np.int32)
+    score = C.c_double()
+    states = C.c_int64()
+    _check(LIB.tn_path_search(C.byref(g), d.ctypes.data_as(C.POINTER(C.c_double)), C.byref(o),
+                              order.ctypes.data_as(C.POINTER(C.c_int32)), C.byref(score), C.byref(states)))
+    return order, float(score.value), int(states.value)
+
+
+# --------------------------------------------------------------------------
+# serving loop
+# --------------------------------------------------------------------------
+class Server:
+    def __init__(self, ptr):
+        self.ptr = ptr
+        self._pending = {}
+
+    def __del__(self):
+        if getattr(self, "ptr", None):
+            LIB.tn_server_free(self.ptr)
+            self.ptr = None
+
+
+def tn_server_create(hbm_budget_bytes: float = 0.0, max_inflight: int = 0, n_streams: int = 0) -> Server:
+    cfg = tn_server_cfg(float(hbm_budget_bytes), int(max_inflight), int(n_streams))
+    out = C.c_void_p()
+    _check(LIB.tn_server_create(C.byref(cfg), C.byref(out)))
+    return Server(out)
+
+
+def tn_server_submit(s: Server, p: Plan, bits, prec: str = "fp64", out=None) -> int:
+    n = p.circuit.n_qubits
+    words = max((n + 63) // 64, 1)
+    b = np.asarray(bits)
+    if b.dtype != np.uint64 or b.ndim != 2 or b.shape[1] != words:
+        b = pack_bits(b.reshape(-1, n))
+    b = np.ascontiguousarray(b)
+    res = np.zeros(b.shape[0], dtype=np.complex128) if out is None else out
+    optr = res.ctypes.data if isinstance(res, np.ndarray) else res.data_ptr()
+    t = C.c_uint64()
+    _check(LIB.tn_server_submit(s.ptr, p.ptr, C.c_void_p(b.ctypes.data), int(b.shape[0]), PRECISIONS[prec],
+                                C.c_void_p(optr), C.byref(t)))
+    s._pending[int(t.value)] = (res, p)
+    return int(t.value)
+
+
+def tn_server_wait(s: Server, ticket: int, timeout_ms: int = -1):
+    st = LIB.tn_server_wait(s.ptr, C.c_uint64(ticket), int(timeout_ms))
+    if st == TN_ERR_TIMEOUT:
+        raise TNError(st, "request not complete")
+    res, _ = s._pending.pop(ticket)
+    _check(st)
+    return res
+
+
+def tn_server_stats_get(s: Server) -> dict:
+    st = tn_server_stats()
+    _check(LIB.tn_server_stats_get(s.ptr, C.byref(st)))
+    return {name: getattr(st, name) for name, _ in tn_server_stats._fields_}

@@ -1,0 +1,175 @@
+"""C-ABI library on the CPU: it loads, exports every entry point declared in
+include/tn.h, and its host-only pieces (gate split, Algorithm 1, input
+validation) agree with the oracle and the paper. No device compute here."""
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import gen
+from oracle import path as opath
+from oracle import tns as otns
+
+
+@pytest.fixture(scope="module")
+def tn(repo_root):
+    from paper_2011_02621_gb300 import build
+    build.build()
+    from paper_2011_02621_gb300 import tn as _tn
+    return _tn
+
+
+def declared_symbols(repo_root):
+    txt = open(os.path.join(repo_root, "include", "tn.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(tn_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_library_exports_every_declared_symbol(tn, repo_root):
+    names = declared_symbols(repo_root)
+    assert len(names) >= 15
+    for name in names:
+        assert hasattr(tn.LIB, name), name
+
+
+def test_gate_split_matches_oracle_and_reconstructs(tn):
+    rng = gen.rng(5, 1)
+    for m in (gen.fsim(math.pi / 2, math.pi / 6), gen.fsim(0, math.pi), gen.haar_u4(rng), np.eye(4, dtype=complex)):
+        P, Q, chi = tn.tn_gate_split(m)
+        _, _, chi_o = otns.gate_split(m)
+        assert chi == chi_o
+        rec = np.einsum("aks,bls->abkl", P, Q).reshape(4, 4)
+        assert np.max(np.abs(rec - m)) < 1e-13
+
+
+def random_graph(n, rng):
+    edges = set()
+    for i in range(1, n):
+        edges.add((int(rng.integers(i)), i))
+    for _ in range(n):
+        u, v = sorted(rng.choice(n, 2, replace=False))
+        edges.add((int(u), int(v)))
+    return sorted(edges)
+
+
+def test_algorithm1_unconstrained_is_global_optimum(tn):
+    """Eq. optscore: without Assumptions 1-3 Algorithm 1 is a subset Dijkstra and finds the optimum."""
+    rng = np.random.default_rng(11)
+    for n in (4, 5, 6, 7, 8):
+        for _ in range(3):
+            edges = random_graph(n, rng)
+            dims = rng.integers(2, 17, size=len(edges)).astype(float)
+            order, score, _ = tn.tn_path_search(n, edges, dims, boundary_only=False, connected=False)
+            assert sorted(order) == list(range(n))
+            assert score == pytest.approx(opath.score(list(order), edges, dims), rel=1e-12)
+            assert score == pytest.approx(opath.subset_dp_optimum(n, edges, dims), rel=1e-12)
+            if n <= 7:
+                assert score == pytest.approx(opath.bruteforce_optimum(n, edges, dims), rel=1e-12)
+
+
+def test_algorithm1_with_assumptions_is_valid_and_not_below_optimum(tn):
+    rng = np.random.default_rng(12)
+    for n in (6, 7, 8, 9):
+        edges = random_graph(n, rng)
+        dims = rng.integers(2, 9, size=len(edges)).astype(float)
+        order, score, _ = tn.tn_path_search(n, edges, dims)
+        assert sorted(order) == list(range(n))
+        assert score == pytest.approx(opath.score(list(order), edges, dims), rel=1e-12)
+        assert score >= opath.subset_dp_optimum(n, edges, dims) * (1 - 1e-12)
+        deg = np.zeros(n, int)
+        for u, v in edges:
+            deg[u] += 1
+            deg[v] += 1
+        if (deg < deg.max()).any():
+            assert deg[order[0]] < deg.max()          # Assumption 1: start on the boundary
+
+
+def test_algorithm1_partial_paths_almost_connected(tn):
+    """Assumption 3: every prefix is connected, or connected plus one qubit that the next step reconnects."""
+    g = gen.staggered(6, 9, remove_seed=gen.BASE_SEED + 3)
+    dims = np.full(len(g.edges), 4.0)
+    order, score, _ = tn.tn_path_search(g.n, g.edges, dims)
+    adj = {q: set() for q in range(g.n)}
+    for u, v in g.edges:
+        adj[u].add(v)
+        adj[v].add(u)
+    seen = set()
+    for m, q in enumerate(order):
+        seen.add(int(q))
+        comps, todo = 0, set(seen)
+        while todo:
+            comps += 1
+            st = [todo.pop()]
+            while st:
+                x = st.pop()
+                for y in adj[x]:
+                    if y in todo:
+                        todo.discard(y)
+                        st.append(y)
+        assert comps <= 2
+        if comps == 2:
+            nxt = int(order[m + 1])
+            assert adj[nxt] & seen
+
+
+def test_algorithm1_rank_bound(tn):
+    """Assumption 2: with max_rank M no intermediate has more than M open legs."""
+    g = gen.grid(4, 5)
+    dims = np.full(len(g.edges), 3.0)
+    for M in (5, 6):
+        order, _, _ = tn.tn_path_search(g.n, g.edges, dims, max_rank=M)
+        S = set()
+        for q in order:
+            S.add(int(q))
+            open_legs = sum(1 for u, v in g.edges if (u in S) != (v in S))
+            assert open_legs <= M
+    with pytest.raises(tn.TNError) as ei:
+        tn.tn_path_search(g.n, g.edges, dims, max_rank=2)
+    assert ei.value.status == tn.TN_ERR_NO_PATH
+
+
+def test_build_validates_graph_and_gates(tn):
+    g = gen.grid(2, 2)
+    ok = gen.rqc(g, 2, gen.rng(1, 1))
+    c = tn.tn_build(g.n, g.edges, ok, allocator=None)
+    assert c.ptr
+    with pytest.raises(tn.TNError) as ei:                 # disconnected
+        tn.tn_build(4, [(0, 1), (2, 3)], [], allocator=None)
+    assert ei.value.status == tn.TN_ERR_GRAPH
+    with pytest.raises(tn.TNError) as ei:                 # gate on a non-edge (diagonal of the square)
+        tn.tn_build(g.n, g.edges, [gen.Gate(1, (0, 3), np.eye(4, dtype=complex))], allocator=None)
+    assert ei.value.status == tn.TN_ERR_GRAPH
+    with pytest.raises(tn.TNError) as ei:                 # qubit out of range
+        tn.tn_build(g.n, g.edges, [gen.Gate(1, (7,), np.eye(2, dtype=complex))], allocator=None)
+    assert ei.value.status == tn.TN_ERR_GRAPH
+    with pytest.raises(tn.TNError) as ei:                 # duplicate edge
+        tn.tn_build(3, [(0, 1), (1, 0), (1, 2)], [], allocator=None)
+    assert ei.value.status == tn.TN_ERR_GRAPH
+    with pytest.raises(tn.TNError) as ei:                 # cycle 0 is not a cycle
+        tn.tn_build(g.n, g.edges, [gen.Gate(0, (0,), np.eye(2, dtype=complex))], allocator=None)
+    assert ei.value.status == tn.TN_ERR_ARG
+
+
+def test_call_order_is_checked(tn):
+    g = gen.grid(2, 2)
+    c = tn.tn_build(g.n, g.edges, gen.rqc(g, 2, gen.rng(1, 1)), allocator=None)
+    with pytest.raises(tn.TNError) as ei:
+        tn.tn_path(c)
+    assert ei.value.status == tn.TN_ERR_STATE
+    with pytest.raises(tn.TNError) as ei:
+        tn.tn_circuit_bond_dims(c, 0)
+    assert ei.value.status == tn.TN_ERR_STATE
+
+
+def test_no_cpu_fallback_without_gpu(tn):
+    """On a machine without a CUDA device the device entry points fail loudly."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    g = gen.grid(2, 2)
+    c = tn.tn_build(g.n, g.edges, gen.rqc(g, 2, gen.rng(1, 1)), allocator=None)
+    with pytest.raises(tn.TNError) as ei:
+        tn.tn_evolve_two_sided(c, 1)
+    assert ei.value.status == tn.TN_ERR_CUDA
