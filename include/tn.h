@@ -93,7 +93,9 @@ typedef enum {
   TN_FP32 = 1,   /* complex64 tensors, FP32 SIMT GEMMs */
   TN_TF32 = 2,   /* complex64 tensors, single-pass TF32 tcgen05 GEMMs, FP32 accumulate */
   TN_TF32X3 = 3, /* complex64, compensated hi/lo TF32 (3 products), FP32 accumulate */
-  TN_BF16X3 = 4  /* complex64, compensated hi/lo BF16 (3 products), FP32 accumulate */
+  TN_BF16X3 = 4, /* complex64, compensated hi/lo BF16 (3 products), FP32 accumulate */
+  TN_BF16X6 = 5, /* complex64, three-piece BF16 split (6 products, ~24-bit products), FP32 accumulate */
+  TN_TF32X6 = 6  /* complex64, three-piece TF32 split (6 products), FP32 accumulate */
 } tn_precision;
 
 typedef struct tn_circuit tn_circuit;
@@ -207,6 +209,13 @@ tn_status tn_gate_split(const tn_c128 *m, tn_c128 *P, tn_c128 *Q, int32_t *chi_o
  * Errors: TN_ERR_ARG, TN_ERR_GRAPH, TN_ERR_NO_PATH. */
 tn_status tn_path_search(const tn_graph *g, const double *dims, const tn_path_opts *opts,
                          int32_t *order, double *score, int64_t *states_expanded);
+
+/* Cuts and path of tn_path on an arbitrary graph with per-edge dimensions:
+ * order[n_qubits], cuts[<= n_edges] (edge ids, *n_cuts of them) and the total
+ * complex multiply-adds (slices x score of the cut network). Host only.
+ * Errors: TN_ERR_ARG, TN_ERR_GRAPH, TN_ERR_NO_PATH. */
+tn_status tn_cut_search(const tn_graph *g, const double *dims, const tn_path_opts *opts, int32_t *order,
+                        int32_t *cuts, int32_t *n_cuts, double *total_cmacs);
 
 /* ---- serving loop (continuous batching over resident plans) -------------- */
 

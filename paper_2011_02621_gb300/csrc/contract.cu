@@ -3,12 +3,12 @@
 // per absorption step, and the FP64 sum over slices.
 //
 // The overlap tensor C^i = sum_sigma A^sigma (ket) B^sigma (bra) of Eq. overlap
-// is never stored: each GEMM forms its B operand tile on the fly from the
-// node's ket and bra tensors through per-step offset tables, with the cut
-// legs fixed by the item's slice. The A operand is gathered from the previous
-// intermediate through a row decomposition over the "rest" legs and a column
-// table over the shared legs, so the transposes of a transpose-transpose-GEMM
-// step cost no extra pass over memory.
+// is never stored by the SIMT kernels: each GEMM forms its B operand tile on
+// the fly from the node's ket and bra tensors through per-step offset tables,
+// with the cut legs fixed by the item's slice. Every intermediate is written by
+// its producer directly in the row-major [M][K] layout its consumer reads
+// (output offset orow(m) + ocol[n]), so the transposes of a
+// transpose-transpose-GEMM step cost no extra pass over memory.
 #include <cuda_runtime.h>
 
 #include "tn_internal.h"
@@ -33,11 +33,36 @@ struct ItemCtx {
 
 __device__ __forceinline__ ItemCtx item_ctx(const ContractArgs &a, const StepParams &s, int64_t item) {
   ItemCtx c;
-  c.b = item / a.n_slices;
-  c.sl = a.slice0 + item % a.n_slices;
+  if (a.n_slices == 1) {
+    c.b = item;
+    c.sl = a.slice0;
+  } else {
+    c.b = (unsigned)item / (unsigned)a.n_slices;
+    c.sl = a.slice0 + (unsigned)item % (unsigned)a.n_slices;
+  }
   c.sa = a.tab[s.t_sa + c.sl];
   c.sb = a.tab[s.t_sb + c.sl];
   return c;
+}
+
+// output offset of row m: m decomposed over the rest legs, weighted by their output strides
+__device__ __forceinline__ int orow_of(const StepParams &s, int64_t m64) {
+  unsigned m = (unsigned)m64;   // rows < 2^31 (checked when the plan is compiled)
+  int off = 0;
+  if (s.rest_pow2) {
+    for (int j = s.n_rest - 1; j >= 0; --j) {
+      const int lg = s.rest_log2[j];
+      off += (int)(m & ((1u << lg) - 1u)) * s.rest_ostride[j];
+      m >>= lg;
+    }
+  } else {
+    for (int j = s.n_rest - 1; j >= 0; --j) {
+      const unsigned d = (unsigned)s.rest_dim[j];
+      off += (int)(m % d) * s.rest_ostride[j];
+      m /= d;
+    }
+  }
+  return off;
 }
 
 // C element (Eq. overlap) at table offsets
@@ -57,7 +82,23 @@ __global__ void form_kernel(StepParams s, ContractArgs a, const typename C2T<R>:
   ItemCtx c = item_ctx(a, s, item);
   const V *kp = ket + s.ket_off + c.sa;
   const V *bp = bra + c.b * a.bra_stride + s.bra_off + c.sb;
-  tout[item * a.t_stride + n] = overlap_elem(kp, bp, a.tab[s.t_bna + n], a.tab[s.t_bnb + n], s.ket_sig, s.bra_sig);
+  tout[item * a.t_stride + a.tab[s.t_ocol + n]] =
+      overlap_elem(kp, bp, a.tab[s.t_bna + n], a.tab[s.t_bnb + n], s.ket_sig, s.bra_sig);
+}
+
+// the overlap tensor of the absorbed node, per item, as [N][K] complex64 (K contiguous)
+__global__ void form_c_kernel(StepParams s, ContractArgs a, const float2 *ket, const float2 *bra, float2 *cbuf,
+                              int64_t c_stride, int64_t item0) {
+  const unsigned kn = (unsigned)(s.K * s.N), K = (unsigned)s.K;
+  const unsigned r = blockIdx.x * blockDim.x + threadIdx.x;   // element within one item
+  const int64_t item = item0 + blockIdx.y;
+  if (r >= kn) return;
+  const unsigned n = r / K, k = r % K;
+  ItemCtx c = item_ctx(a, s, item);
+  const float2 *kp = ket + s.ket_off + c.sa;
+  const float2 *bp = bra + c.b * a.bra_stride + s.bra_off + c.sb;
+  cbuf[item * c_stride + r] = overlap_elem(kp, bp, (int64_t)a.tab[s.t_bka + k] + a.tab[s.t_bna + n],
+                                           (int64_t)a.tab[s.t_bkb + k] + a.tab[s.t_bnb + n], s.ket_sig, s.bra_sig);
 }
 
 // Tiled SIMT complex GEMM: one CTA per (item, BM x BN output tile).
@@ -80,22 +121,12 @@ step_kernel(StepParams s, ContractArgs a, const typename C2T<R>::T *ket, const t
   const V *kp = ket + s.ket_off + c.sa;
   const V *bp = bra + c.b * a.bra_stride + s.bra_off + c.sb;
   const V *tp = tin + item * a.t_stride;
-  const int32_t *ak = a.tab + s.t_ak, *bka = a.tab + s.t_bka, *bkb = a.tab + s.t_bkb;
-  const int32_t *bna = a.tab + s.t_bna, *bnb = a.tab + s.t_bnb;
+  const int32_t *bka = a.tab + s.t_bka, *bkb = a.tab + s.t_bkb;
+  const int32_t *bna = a.tab + s.t_bna, *bnb = a.tab + s.t_bnb, *ocol = a.tab + s.t_ocol;
 
-  for (int mm = tid; mm < BM; mm += NT) {
-    int64_t m = m0 + mm;
-    int off = -1;
-    if (m < s.M) {
-      off = 0;
-      int64_t r = m;
-      for (int j = s.n_rest - 1; j >= 0; --j) {
-        int d = s.rest_dim[j];
-        off += (int)(r % d) * s.rest_stride[j];
-        r /= d;
-      }
-    }
-    rowoff[mm] = off;
+  for (int mm = tid; mm < BM; mm += NT) {     // output row offsets
+    const int64_t m = m0 + mm;
+    rowoff[mm] = m < s.M ? orow_of(s, m) : -1;
   }
   const int tx = tid % (BN / TN), ty = tid / (BN / TN);
   V acc[TM][TN];
@@ -108,9 +139,8 @@ step_kernel(StepParams s, ContractArgs a, const typename C2T<R>::T *ket, const t
   for (int64_t k0 = 0; k0 < s.K; k0 += BK) {
     for (int idx = tid; idx < BM * BK; idx += NT) {
       int mm = idx / BK, kk = idx % BK;
-      int64_t k = k0 + kk;
-      int ro = rowoff[mm];
-      As[kk][mm] = (ro >= 0 && k < s.K) ? tp[ro + ak[k]] : cz<V>();
+      int64_t k = k0 + kk, m = m0 + mm;
+      As[kk][mm] = (m < s.M && k < s.K) ? tp[m * s.K + k] : cz<V>();
     }
     for (int idx = tid; idx < BK * BN; idx += NT) {
       int kk = idx / BN, nn = idx % BN;
@@ -138,12 +168,12 @@ step_kernel(StepParams s, ContractArgs a, const typename C2T<R>::T *ket, const t
   V *op = tout + item * a.t_stride;
 #pragma unroll
   for (int i = 0; i < TM; ++i) {
-    int64_t m = m0 + ty * TM + i;
-    if (m >= s.M) continue;
+    const int ro = rowoff[ty * TM + i];
+    if (ro < 0) continue;
 #pragma unroll
     for (int j = 0; j < TN; ++j) {
       int64_t n = n0 + tx * TN + j;
-      if (n < s.N) op[m * s.N + n] = acc[i][j];
+      if (n < s.N) op[ro + ocol[n]] = acc[i][j];
     }
   }
 }
@@ -161,21 +191,14 @@ step_small_kernel(StepParams s, ContractArgs a, const typename C2T<R>::T *ket, c
   const V *kp = ket + s.ket_off + c.sa;
   const V *bp = bra + c.b * a.bra_stride + s.bra_off + c.sb;
   const V *tp = tin + item * a.t_stride;
-  const int32_t *ak = a.tab + s.t_ak, *bka = a.tab + s.t_bka, *bkb = a.tab + s.t_bkb;
-  const int32_t *bna = a.tab + s.t_bna, *bnb = a.tab + s.t_bnb;
+  const int32_t *bka = a.tab + s.t_bka, *bkb = a.tab + s.t_bkb;
+  const int32_t *bna = a.tab + s.t_bna, *bnb = a.tab + s.t_bnb, *ocol = a.tab + s.t_ocol;
   for (int64_t out = 0; out < s.M * s.N; ++out) {
     int64_t m = out / s.N, n = out % s.N;
-    int ro = 0;
-    int64_t r = m;
-    for (int j = s.n_rest - 1; j >= 0; --j) {
-      int d = s.rest_dim[j];
-      ro += (int)(r % d) * s.rest_stride[j];
-      r /= d;
-    }
     V acc = cz<V>();
     for (int64_t k = tid; k < s.K; k += 256) {
       V cv = overlap_elem(kp, bp, (int64_t)bka[k] + bna[n], (int64_t)bkb[k] + bnb[n], s.ket_sig, s.bra_sig);
-      acc = cfma(tp[ro + ak[k]], cv, acc);
+      acc = cfma(tp[m * s.K + k], cv, acc);
     }
     for (int o = 16; o; o >>= 1) {
       acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
@@ -186,9 +209,54 @@ step_small_kernel(StepParams s, ContractArgs a, const typename C2T<R>::T *ket, c
     if (tid == 0) {
       V t = cz<V>();
       for (int w = 0; w < 256 / 32; ++w) { t.x += red[w].x; t.y += red[w].y; }
-      tout[item * a.t_stride + out] = t;
+      tout[item * a.t_stride + orow_of(s, m) + ocol[n]] = t;
     }
     __syncthreads();
+  }
+}
+
+// Streaming step for small K and N (K, N <= 16) and many rows: the item's C tile sits in shared
+// memory, each thread reads its row of T_in (K contiguous complex) and writes N outputs.
+template <typename R>
+__global__ void __launch_bounds__(256)
+step_stream_kernel(StepParams s, ContractArgs a, const typename C2T<R>::T *ket, const typename C2T<R>::T *bra,
+                   const typename C2T<R>::T *tin, typename C2T<R>::T *tout, int64_t rows_per_cta) {
+  using V = typename C2T<R>::T;
+  __shared__ V Cs[16 * 16];
+  __shared__ int oc[16];
+  const int tid = threadIdx.x;
+  const int64_t ctas_m = (s.M + rows_per_cta - 1) / rows_per_cta;
+  const int64_t item = blockIdx.x / ctas_m;
+  const int64_t m0 = (blockIdx.x % ctas_m) * rows_per_cta;
+  ItemCtx c = item_ctx(a, s, item);
+  const V *kp = ket + s.ket_off + c.sa;
+  const V *bp = bra + c.b * a.bra_stride + s.bra_off + c.sb;
+  const int K = (int)s.K, N = (int)s.N;
+  if (tid < K * N) {
+    const int k = tid / N, n = tid % N;
+    Cs[tid] = overlap_elem(kp, bp, (int64_t)a.tab[s.t_bka + k] + a.tab[s.t_bna + n],
+                           (int64_t)a.tab[s.t_bkb + k] + a.tab[s.t_bnb + n], s.ket_sig, s.bra_sig);
+  }
+  if (tid < N) oc[tid] = a.tab[s.t_ocol + tid];
+  __syncthreads();
+  const V *tp = tin + item * a.t_stride;
+  V *op = tout + item * a.t_stride;
+  const int64_t m1 = m0 + rows_per_cta < s.M ? m0 + rows_per_cta : s.M;
+  for (int64_t m = m0 + tid; m < m1; m += 256) {
+    V x[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k)
+      if (k < K) x[k] = tp[m * K + k];
+    const int ro = orow_of(s, m);
+#pragma unroll
+    for (int n = 0; n < 16; ++n) {
+      if (n >= N) break;
+      V acc = cz<V>();
+#pragma unroll
+      for (int k = 0; k < 16; ++k)
+        if (k < K) acc = cfma(x[k], Cs[k * N + n], acc);
+      op[ro + oc[n]] = acc;
+    }
   }
 }
 
@@ -233,11 +301,33 @@ cudaError_t launch_form(const StepParams &s, const ContractArgs &a, const void *
   return cudaGetLastError();
 }
 
+cudaError_t launch_form_c(const StepParams &s, const ContractArgs &a, const float2 *ket, const float2 *bra,
+                          float2 *cbuf, int64_t c_stride, cudaStream_t st) {
+  const int64_t kn = s.K * s.N;
+  if (kn <= 0 || a.items <= 0) return cudaSuccess;
+  for (int64_t i0 = 0; i0 < a.items; i0 += 65535) {
+    const int64_t ni = a.items - i0 < 65535 ? a.items - i0 : 65535;
+    form_c_kernel<<<dim3((unsigned)((kn + 255) / 256), (unsigned)ni), 256, 0, st>>>(s, a, ket, bra, cbuf, c_stride,
+                                                                                  i0);
+  }
+  tn_count_launch(1);
+  return cudaGetLastError();
+}
+
 template <typename R>
 cudaError_t launch_step(const StepParams &s, const ContractArgs &a, const void *ket, const void *bra,
                         const void *t_in, void *t_out, cudaStream_t st) {
   using V = typename C2T<R>::T;
   if (a.items <= 0) return cudaSuccess;
+  if (s.K <= 16 && s.N <= 16 && s.M >= 512) {
+    const int64_t rows = 1024;
+    const int64_t grid = ((s.M + rows - 1) / rows) * a.items;
+    if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    step_stream_kernel<R><<<(unsigned)grid, 256, 0, st>>>(s, a, (const V *)ket, (const V *)bra, (const V *)t_in,
+                                                          (V *)t_out, rows);
+    tn_count_launch(1);
+    return cudaGetLastError();
+  }
   if (s.M * s.N <= 16) {
     if (a.items > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     step_small_kernel<R><<<(unsigned)a.items, 256, 0, st>>>(s, a, (const V *)ket, (const V *)bra, (const V *)t_in,

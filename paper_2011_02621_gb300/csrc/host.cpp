@@ -837,31 +837,94 @@ static std::vector<double> frontier_sizes(const tn_circuit *c, const std::vector
   return sizes;
 }
 
-static tn_status choose_cuts(const tn_circuit *c, const std::vector<int> &order, std::vector<double> dims,
-                             int want, double limit, std::vector<int> &cuts) {
+// Cutting (overlap paragraph; positions "where the lattice is the thinnest", supplement):
+// greedily cut, among the open legs of the widest intermediate of the current path, the edge
+// whose cut network has the smallest total cost (slices x Algorithm 1 score of the cut
+// network), until every intermediate fits `limit` (or `want` cuts are made). Returns the
+// final path of the cut network.
+static tn_status choose_cuts(const tn_circuit *c, const tn_path_opts &o, std::vector<double> dims, int want,
+                             double limit, std::vector<int> &cuts, std::vector<int> &order, double &score,
+                             int64_t &pops, int &rank_used) {
   cuts.clear();
+  double slices = 1;
   for (int it = 0; it < c->ne; ++it) {
     std::vector<std::vector<int>> open;
     std::vector<double> sz = frontier_sizes(c, order, dims, &open);
-    double mx = *std::max_element(sz.begin(), sz.end());
+    const double mx = *std::max_element(sz.begin(), sz.end());
     if (want >= 0 ? (int)cuts.size() >= want : mx <= limit) return TN_OK;
-    // the edge with the largest dim among the open legs of the widest frontier,
-    // preferring edges open in the most oversized frontiers (the thinnest cut)
-    size_t arg = std::max_element(sz.begin(), sz.end()) - sz.begin();
+    const size_t arg = std::max_element(sz.begin(), sz.end()) - sz.begin();
     int best = -1;
-    double best_key = -1;
+    double best_cost = 0, best_max = 0;
+    std::vector<int> best_order;
+    int best_rank = 0;
     for (int e : open[arg]) {
       if (dims[e] <= 1) continue;
-      int cnt = 0;
-      for (size_t j = 0; j < sz.size(); ++j)
-        if (sz[j] > limit && std::find(open[j].begin(), open[j].end(), e) != open[j].end()) ++cnt;
-      double key = cnt * 1e6 + dims[e];
-      if (key > best_key) { best_key = key; best = e; }
+      std::vector<double> d2 = dims;
+      d2[e] = 1;
+      PathGraph pg = make_pg(c->n, c->eu, c->ev, d2);
+      std::vector<int> ord;
+      double sc = 0;
+      int64_t pp = 0;
+      int ru = 0;
+      if (path_auto(pg, o, ord, sc, pp, ru) != TN_OK) continue;
+      pops += pp;
+      std::vector<double> sz2 = frontier_sizes(c, ord, d2, nullptr);
+      const double mx2 = *std::max_element(sz2.begin(), sz2.end());
+      const double cost = slices * dims[e] * sc;
+      if (best < 0 || cost < best_cost || (cost == best_cost && mx2 < best_max)) {
+        best = e; best_cost = cost; best_max = mx2; best_order = ord; best_rank = ru;
+      }
     }
     if (best < 0) return want >= 0 ? TN_OK : tn_fail(TN_ERR_NO_PATH, "cutting cannot reach the intermediate limit");
-    cuts.push_back(best);
+    slices *= dims[best];
     dims[best] = 1;
+    cuts.push_back(best);
+    order = best_order;
+    score = best_cost / slices;
+    rank_used = best_rank;
   }
+  return TN_OK;
+}
+
+extern "C" tn_status tn_cut_search(const tn_graph *g, const double *dims, const tn_path_opts *opts, int32_t *order,
+                                   int32_t *cuts, int32_t *n_cuts, double *total_cmacs) {
+  if (!g || !dims || !order || !n_cuts) return tn_fail(TN_ERR_ARG, "tn_cut_search: NULL argument");
+  tn_circuit tmp;
+  tn_status s = check_graph(g, tmp.eu, tmp.ev, tmp.legs);
+  if (s != TN_OK) return s;
+  tmp.n = g->n_qubits;
+  tmp.ne = g->n_edges;
+  std::vector<double> d(dims, dims + g->n_edges);
+  for (double x : d)
+    if (!(x >= 1)) return tn_fail(TN_ERR_ARG, "tn_cut_search: dims must be >= 1");
+  tn_path_opts o = opts ? *opts : tn_default_opts();
+  const double limit = o.max_intermediate > 0 ? (double)o.max_intermediate : (double)(1LL << 24);
+  std::vector<int> ord, cut;
+  double score = 0;
+  int64_t pops = 0;
+  int ru = 0;
+  PathGraph pg = make_pg(tmp.n, tmp.eu, tmp.ev, d);
+  if ((s = path_auto(pg, o, ord, score, pops, ru)) != TN_OK) return s;
+  if (o.n_cut_edges > 0) {
+    std::vector<double> d2 = d;
+    for (int j = 0; j < o.n_cut_edges; ++j) {
+      int e = o.cut_edges[j];
+      if (e < 0 || e >= tmp.ne) return tn_fail(TN_ERR_ARG, "tn_cut_search: bad cut edge %d", e);
+      cut.push_back(e);
+      d2[e] = 1;
+    }
+    PathGraph pg2 = make_pg(tmp.n, tmp.eu, tmp.ev, d2);
+    if ((s = path_auto(pg2, o, ord, score, pops, ru)) != TN_OK) return s;
+  } else if ((s = choose_cuts(&tmp, o, d, o.n_cuts, limit, cut, ord, score, pops, ru)) != TN_OK) {
+    return s;
+  }
+  double slices = 1;
+  for (int e : cut) slices *= d[e];
+  for (int i = 0; i < tmp.n; ++i) order[i] = ord[i];
+  if (cuts)
+    for (size_t j = 0; j < cut.size(); ++j) cuts[j] = cut[j];
+  *n_cuts = (int32_t)cut.size();
+  if (total_cmacs) *total_cmacs = slices * score;
   return TN_OK;
 }
 
@@ -951,54 +1014,76 @@ static tn_status compile_plan(tn_circuit *c, tn_plan *p) {
   };
   p->steps.clear();
   p->step_mkn.clear();
-  std::vector<char> open(c->ne, 0);
-  std::vector<int> L;   // current leg order of the intermediate
+  // pass 1: per step the rest, shared and new legs; the input layout of step j is
+  // [rest_j, shared_j], both in the order the legs were created
+  std::vector<std::vector<int>> R(n), Sh(n), Nw(n);
+  {
+    std::vector<char> open(c->ne, 0);
+    std::vector<int> cur;
+    for (int j = 0; j < n; ++j) {
+      const int i = p->order[j];
+      for (int e : cur) ((c->eu[e] == i || c->ev[e] == i) ? Sh[j] : R[j]).push_back(e);
+      Nw[j] = new_legs_of(i, open);
+      for (int e : Sh[j]) open[e] = 0;
+      for (int e : Nw[j]) open[e] = 1;
+      cur = R[j];
+      cur.insert(cur.end(), Nw[j].begin(), Nw[j].end());
+    }
+  }
+  auto prod_dims = [&](const std::vector<int> &legs) {
+    int64_t x = 1;
+    for (int e : legs) x *= dc_of(c, e);
+    return x;
+  };
+  // pass 2: kernels' parameters; output strides are those of the next step's input layout
   double cmacs = 0, bytes = 0;
   int64_t maxT = 1;
   for (int j = 0; j < n; ++j) {
     const int i = p->order[j];
     StepParams s;
     std::memset(&s, 0, sizeof s);
-    std::vector<int> shared, rest;
-    for (int e : L) {
-      bool inc = (c->eu[e] == i || c->ev[e] == i);
-      (inc ? shared : rest).push_back(e);
-    }
-    std::vector<int> nl = new_legs_of(i, open);
-    int64_t M = 1, K = 1, N = 1;
-    for (int e : rest) M *= dc_of(c, e);
-    for (int e : shared) K *= dc_of(c, e);
-    for (int e : nl) N *= dc_of(c, e);
+    const int64_t M = prod_dims(R[j]), K = prod_dims(Sh[j]), N = prod_dims(Nw[j]);
     s.M = M; s.K = K; s.N = N;
-    if ((int)rest.size() > TN_MAXREST) return tn_fail(TN_ERR_UNSUPPORTED, "step %d has %zu rest legs", j, rest.size());
-    // T_in strides
-    std::vector<int64_t> tstr(L.size());
-    {
+    if ((int)R[j].size() > TN_MAXREST) return tn_fail(TN_ERR_UNSUPPORTED, "step %d has %zu rest legs", j, R[j].size());
+    std::vector<int> Lnext;   // input layout of step j+1 (empty after the last step)
+    if (j + 1 < n) {
+      Lnext = R[j + 1];
+      Lnext.insert(Lnext.end(), Sh[j + 1].begin(), Sh[j + 1].end());
+    }
+    auto ostride = [&](int e) -> int64_t {
       int64_t st = 1;
-      for (int q = (int)L.size() - 1; q >= 0; --q) { tstr[q] = st; st *= dc_of(c, L[q]); }
+      for (int q = (int)Lnext.size() - 1; q >= 0; --q) {
+        if (Lnext[q] == e) return st;
+        st *= dc_of(c, Lnext[q]);
+      }
+      return 0;
+    };
+    s.n_rest = (int)R[j].size();
+    s.rest_pow2 = 1;
+    for (size_t r = 0; r < R[j].size(); ++r) {
+      const int64_t d = dc_of(c, R[j][r]);
+      s.rest_dim[r] = (int)d;
+      s.rest_ostride[r] = (int)ostride(R[j][r]);
+      int lg = 0;
+      while ((1LL << lg) < d) ++lg;
+      s.rest_log2[r] = lg;
+      if ((1LL << lg) != d) s.rest_pow2 = 0;
     }
-    s.n_rest = (int)rest.size();
-    for (size_t r = 0; r < rest.size(); ++r) {
-      int li = (int)(std::find(L.begin(), L.end(), rest[r]) - L.begin());
-      s.rest_dim[r] = (int)dc_of(c, rest[r]);
-      s.rest_stride[r] = (int)tstr[li];
-    }
-    std::vector<int64_t> ak(K, 0);
-    for (int64_t k = 0; k < K; ++k) {
-      int64_t r = k, off = 0;
-      for (int q = (int)shared.size() - 1; q >= 0; --q) {
-        int li = (int)(std::find(L.begin(), L.end(), shared[q]) - L.begin());
-        int64_t d = dc_of(c, shared[q]);
-        off += (r % d) * tstr[li];
+    std::vector<int64_t> ocol(N, 0);
+    for (int64_t nn = 0; nn < N; ++nn) {
+      int64_t r = nn, off = 0;
+      for (int q = (int)Nw[j].size() - 1; q >= 0; --q) {
+        const int64_t d = dc_of(c, Nw[j][q]);
+        off += (r % d) * ostride(Nw[j][q]);
         r /= d;
       }
-      ak[k] = off;
+      ocol[nn] = off;
     }
     std::vector<int64_t> ka, kb, na, nb, sa, sb;
-    leg_tables(i, shared, ka, kb);
-    leg_tables(i, nl, na, nb);
+    leg_tables(i, Sh[j], ka, kb);
+    leg_tables(i, Nw[j], na, nb);
     slice_tables(i, sa, sb);
-    s.t_ak = push_tab(ak);
+    s.t_ocol = push_tab(ocol);
     s.t_bka = push_tab(ka);
     s.t_bkb = push_tab(kb);
     s.t_bna = push_tab(na);
@@ -1015,14 +1100,11 @@ static tn_status compile_plan(tn_circuit *c, tn_plan *p) {
     if (j > 0) {
       cmacs += (double)M * K * N;
       bytes += 8.0 * ((double)M * K + (double)M * N);
+      p->maxKN = std::max(p->maxKN, K * N);
     }
     maxT = std::max(maxT, M * N);
-    // next leg order
-    for (int e : shared) open[e] = 0;
-    for (int e : nl) open[e] = 1;
-    L = rest;
-    L.insert(L.end(), nl.begin(), nl.end());
   }
+  maxT = (maxT + 1) & ~1LL;   // even: 16-byte aligned item strides for complex64
   if (maxT >= (1LL << 31) || (int64_t)tab.size() >= (1LL << 31))
     return tn_fail(TN_ERR_UNSUPPORTED, "intermediate of %lld elements exceeds the 2^31 index range; add cuts",
                    (long long)maxT);
@@ -1061,6 +1143,7 @@ int64_t plan_ws_bytes(const tn_plan *p, int kind, int64_t chunk, int64_t slices)
   if (kind) b += chunk * c->bra.item_elems * 8;             // bra c64 copy
   b += chunk * std::max<int64_t>(c->bra.max_work, 1) * 16;  // SVD work beyond shared memory
   b += 2 * chunk * slices * p->maxT * el;                   // ping-pong intermediates
+  if (kind) b += chunk * slices * p->maxKN * 8;             // overlap tensors for the tensor-core steps
   b += chunk * 16 + 4096;                                   // results, flags
   return b;
 }
@@ -1093,10 +1176,10 @@ extern "C" tn_status tn_path(tn_circuit *c, const tn_path_opts *opts, tn_plan **
       p->cuts.push_back(e);
     }
   } else {
-    s = choose_cuts(c, p->order, dims, o.n_cuts, limit, p->cuts);
+    s = choose_cuts(c, o, dims, o.n_cuts, limit, p->cuts, p->order, p->score, p->pops, p->rank_used);
     if (s != TN_OK) { delete p; return s; }
   }
-  if (!p->cuts.empty()) {
+  if (o.n_cut_edges > 0) {   // path of the network with the given cuts
     std::vector<double> cd2 = dims;
     for (int e : p->cuts) cd2[e] = 1;
     PathGraph pg2 = make_pg(c->n, c->eu, c->ev, cd2);
@@ -1166,6 +1249,7 @@ void ws_release(DevMem &mem, Workspace &w) {
   mem.release(w.t1);
   mem.release(w.res);
   mem.release(w.err);
+  mem.release(w.cbuf);
 }
 
 tn_status ws_ensure(tn_plan *p, Workspace &w, int kind, cudaStream_t st) {
@@ -1182,6 +1266,7 @@ tn_status ws_ensure(tn_plan *p, Workspace &w, int kind, cudaStream_t st) {
   if ((s = mem.ensure(w.gwork, ch * std::max<int64_t>(c->bra.max_work, 1) * 16, st)) != TN_OK) return s;
   if ((s = mem.ensure(w.t0, ch * sc * p->maxT * el, st)) != TN_OK) return s;
   if ((s = mem.ensure(w.t1, ch * sc * p->maxT * el, st)) != TN_OK) return s;
+  if (kind && (s = mem.ensure(w.cbuf, ch * sc * p->maxKN * 8, st)) != TN_OK) return s;
   if ((s = mem.ensure(w.res, ch * 16, st)) != TN_OK) return s;
   if ((s = mem.ensure(w.err, 64, st)) != TN_OK) return s;
   w.chunk = (int)ch;
@@ -1202,7 +1287,7 @@ tn_status run_amplitudes(tn_plan *p, Workspace &w, const uint64_t *bits, int64_t
                          tn_c128 *out, cudaStream_t st) {
   tn_circuit *c = p->c;
   if (p->generation != c->generation) return tn_fail(TN_ERR_STATE, "plan is stale: the circuit was re-evolved");
-  if (prec < TN_FP64 || prec > TN_BF16X3) return tn_fail(TN_ERR_ARG, "unknown precision %d", (int)prec);
+  if (prec < TN_FP64 || prec > TN_TF32X6) return tn_fail(TN_ERR_ARG, "unknown precision %d", (int)prec);
   if (n == 0) return TN_OK;
   if (n < 0 || !bits || !out) return tn_fail(TN_ERR_ARG, "tn_amplitudes: bad arguments");
   const int kind = prec == TN_FP64 ? 0 : 1;
@@ -1254,8 +1339,12 @@ tn_status run_amplitudes(tn_plan *p, Workspace &w, const uint64_t *bits, int64_t
           ProfScope ps(prec == TN_FP32 ? "contract_step_fp32" : "contract_step_fp32_tc_fallback", st, by, fl);
           CUDA_TRY(launch_step<float>(sp, a, ket, bra, tin, tout, st));
         } else {
-          ProfScope ps("contract_step_tcgen05", st, by, fl);
-          CUDA_TRY(launch_step_tc((int)prec, sp, a, (const float2 *)ket, (const float2 *)bra, (const float2 *)tin,
+          {
+            ProfScope ps("overlap_form_c64", st, 8.0 * items * (double)sp.K * sp.N, 16.0 * items * (double)sp.K * sp.N);
+            CUDA_TRY(launch_form_c(sp, a, (const float2 *)ket, (const float2 *)bra, (float2 *)w.cbuf.p, p->maxKN, st));
+          }
+          ProfScope ps("contract_step_tcgen05", st, by + 8.0 * items * (double)sp.K * sp.N, fl);
+          CUDA_TRY(launch_step_tc((int)prec, sp, a, (const float2 *)w.cbuf.p, p->maxKN, (const float2 *)tin,
                                   (float2 *)tout, (int *)w.err.p + 1, st));
         }
         std::swap(tin, tout);

@@ -57,7 +57,7 @@ struct tn_circuit {
 struct Workspace {
   int chunk = 0;
   int64_t slice_chunk = 1;
-  Buf bits, bra64, bra32, gwork, t0, t1, res, err;
+  Buf bits, bra64, bra32, gwork, t0, t1, res, err, cbuf;
 };
 
 struct tn_plan {
@@ -73,6 +73,7 @@ struct tn_plan {
   std::vector<int32_t> tab_host;
   Buf tab_dev;
   int64_t maxT = 1;
+  int64_t maxKN = 1;                              // largest overlap tensor of a step (elements)
   double cmacs = 0, bytes = 0;
   int chunk[2] = {1, 1};                          // bitstrings per batch: [FP64, complex64]
   int64_t slice_chunk[2] = {1, 1};                // slices per launch group (all S when chunk > 1)

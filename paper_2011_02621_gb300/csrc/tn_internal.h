@@ -52,18 +52,24 @@ cudaError_t launch_pack_bits(const uint64_t *src, uint64_t *dst, int64_t n_words
 // ---------------------------------------------------------------------------
 // contraction (Eq. overlap; path-ordered steps of Algorithm 1; cutting)
 // ---------------------------------------------------------------------------
-// One absorption step: T_out[item][m*N + n] = sum_k T_in[item][row(m) + ak[k]] * C[k][n]
-// with C[k][n] = sum_sigma ket[ka(k,n) + sigma*ket_sig] * bra_b[kb(k,n) + sigma*bra_sig]
-// (Eq. overlap formed on the fly), item = bitstring * n_slices + slice.
+// One absorption step (TTGT with both transposes folded into the kernels):
+//   T_out[item][orow(m) + ocol[n]] = sum_k T_in[item][m*K + k] * C[k][n],
+//   C[k][n] = sum_sigma ket[ka(k,n) + sigma*ket_sig] * bra_b[kb(k,n) + sigma*bra_sig]   (Eq. overlap)
+// item = bitstring * n_slices + slice. Every intermediate is stored in the layout its consumer
+// reads as a row-major [M][K] matrix (rest legs, then shared legs): the producer of step j
+// writes element (m, n) at orow(m) + ocol[n], where orow decomposes m over the rest legs of
+// step j (mixed radix, last fastest) with their strides in step j+1's layout.
 struct StepParams {
   int64_t M, K, N;
   int n_rest;
-  int rest_dim[TN_MAXREST];     // rest legs of T_in, slowest first
-  int rest_stride[TN_MAXREST];  // their strides in T_in
+  int rest_pow2;                // 1: every rest dim is a power of two (decompose with shifts)
+  int rest_dim[TN_MAXREST];     // rest legs of step j, slowest first
+  int rest_log2[TN_MAXREST];    // log2 of the dims when rest_pow2
+  int rest_ostride[TN_MAXREST]; // their strides in the output layout
   int64_t ket_off, ket_sig;     // node tensor offset / sigma stride in the ket buffer
   int64_t bra_off, bra_sig;     // same in one bitstring's bra region
   // offsets of the int32 tables in the plan's table buffer
-  int64_t t_ak, t_bka, t_bkb, t_bna, t_bnb, t_sa, t_sb;
+  int64_t t_ocol, t_bka, t_bkb, t_bna, t_bnb, t_sa, t_sb;
 };
 
 struct ContractArgs {
@@ -87,9 +93,12 @@ template <typename R>
 cudaError_t launch_slice_sum(const void *res, int64_t items_stride, int64_t n_bits, int64_t n_slices,
                              int accumulate, double2 *out, cudaStream_t st);
 
-// tensor-core step (tcgen05): prec = TN_TF32, TN_TF32X3 or TN_BF16X3
-cudaError_t launch_step_tc(int prec, const StepParams &s, const ContractArgs &a, const float2 *ket,
-                           const float2 *bra, const float2 *t_in, float2 *t_out, int *errflag, cudaStream_t st);
+// the overlap tensor of one step for every item, complex64, [N][K] per item (K contiguous)
+cudaError_t launch_form_c(const StepParams &s, const ContractArgs &a, const float2 *ket, const float2 *bra,
+                          float2 *cbuf, int64_t c_stride, cudaStream_t st);
+// tensor-core step (tcgen05): prec = TN_TF32 .. TN_TF32X6; B from launch_form_c's buffer
+cudaError_t launch_step_tc(int prec, const StepParams &s, const ContractArgs &a, const float2 *cbuf,
+                           int64_t c_stride, const float2 *t_in, float2 *t_out, int *errflag, cudaStream_t st);
 bool tc_step_supported(const StepParams &s);
 
 // launch accounting

@@ -24,7 +24,7 @@ TN_OK, TN_ERR_ARG, TN_ERR_GRAPH, TN_ERR_OOM, TN_ERR_NO_PATH, TN_ERR_STATE, TN_ER
     TN_ERR_UNSUPPORTED = range(9)
 STATUS_NAMES = {0: "TN_OK", 1: "TN_ERR_ARG", 2: "TN_ERR_GRAPH", 3: "TN_ERR_OOM", 4: "TN_ERR_NO_PATH",
                 5: "TN_ERR_STATE", 6: "TN_ERR_CUDA", 7: "TN_ERR_TIMEOUT", 8: "TN_ERR_UNSUPPORTED"}
-PRECISIONS = {"fp64": 0, "fp32": 1, "tf32": 2, "tf32x3": 3, "bf16x3": 4}
+PRECISIONS = {"fp64": 0, "fp32": 1, "tf32": 2, "tf32x3": 3, "bf16x3": 4, "bf16x6": 5, "tf32x6": 6}
 
 
 class TNError(RuntimeError):
@@ -100,6 +100,8 @@ def _load():
         "tn_gate_split": (i32, [C.POINTER(c128), C.POINTER(c128), C.POINTER(c128), C.POINTER(i32)]),
         "tn_path_search": (i32, [C.POINTER(tn_graph), C.POINTER(dbl), C.POINTER(tn_path_opts), C.POINTER(i32),
                                  C.POINTER(dbl), C.POINTER(i64)]),
+        "tn_cut_search": (i32, [C.POINTER(tn_graph), C.POINTER(dbl), C.POINTER(tn_path_opts), C.POINTER(i32),
+                                C.POINTER(i32), C.POINTER(i32), C.POINTER(dbl)]),
         "tn_server_create": (i32, [C.POINTER(tn_server_cfg), C.POINTER(vp)]),
         "tn_server_submit": (i32, [vp, vp, vp, i64, i32, vp, C.POINTER(C.c_uint64)]),
         "tn_server_wait": (i32, [vp, C.c_uint64, i64]),
@@ -366,6 +368,21 @@ def tn_path_search(n_qubits: int, edges, dims, **opts):
     _check(LIB.tn_path_search(C.byref(g), d.ctypes.data_as(C.POINTER(C.c_double)), C.byref(o),
                               order.ctypes.data_as(C.POINTER(C.c_int32)), C.byref(score), C.byref(states)))
     return order, float(score.value), int(states.value)
+
+
+def tn_cut_search(n_qubits: int, edges, dims, **opts):
+    """(order, cuts, total complex MACs) of the planner on an arbitrary graph (host only)."""
+    g, e = _graph_struct(n_qubits, edges)
+    d = np.ascontiguousarray(np.asarray(dims, dtype=np.float64))
+    o, keep = _opts(**opts)
+    order = np.zeros(n_qubits, dtype=np.int32)
+    cuts = np.zeros(max(e.shape[0], 1), dtype=np.int32)
+    nc = C.c_int32()
+    tot = C.c_double()
+    _check(LIB.tn_cut_search(C.byref(g), d.ctypes.data_as(C.POINTER(C.c_double)), C.byref(o),
+                             order.ctypes.data_as(C.POINTER(C.c_int32)), cuts.ctypes.data_as(C.POINTER(C.c_int32)),
+                             C.byref(nc), C.byref(tot)))
+    return order, cuts[: nc.value], float(tot.value)
 
 
 # --------------------------------------------------------------------------

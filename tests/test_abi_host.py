@@ -173,3 +173,27 @@ def test_no_cpu_fallback_without_gpu(tn):
     with pytest.raises(tn.TNError) as ei:
         tn.tn_evolve_two_sided(c, 1)
     assert ei.value.status == tn.TN_ERR_CUDA
+
+
+def test_cut_search_respects_limit_and_reports_cost(tn):
+    """Cutting: every intermediate of the cut network fits the limit; total = slices x path score."""
+    import math
+    g = gen.grid(4, 5)
+    rng = np.random.default_rng(4)
+    dims = rng.choice([4, 8, 16, 32, 64], size=len(g.edges)).astype(float)
+    order0, score0, _ = tn.tn_path_search(g.n, g.edges, dims)
+    for limit in (1 << 22, 1 << 18, 1 << 14):
+        order, cuts, total = tn.tn_cut_search(g.n, g.edges, dims, max_intermediate=limit)
+        d2 = dims.copy()
+        d2[list(cuts)] = 1
+        S = set()
+        for q in order:
+            S.add(int(q))
+            assert math.prod(d2[e] for e, (u, v) in enumerate(g.edges) if (u in S) != (v in S)) <= limit
+        slices = math.prod(dims[e] for e in cuts)
+        assert total == pytest.approx(slices * opath.score(list(order), g.edges, d2), rel=1e-12)
+        assert total >= score0 * (1 - 1e-12) or len(cuts) == 0
+    order, cuts, total = tn.tn_cut_search(g.n, g.edges, dims, n_cuts=0)
+    assert len(cuts) == 0 and total == pytest.approx(score0, rel=1e-12)
+    order, cuts, total = tn.tn_cut_search(g.n, g.edges, dims, cut_edges=[3, 7])
+    assert list(cuts) == [3, 7]

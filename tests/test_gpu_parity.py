@@ -193,3 +193,54 @@ def test_device_buffers_in_and_out(tn):
     out = torch.zeros(100, dtype=torch.complex128, device="cuda")
     tn.tn_amplitudes(p, bits_dev, "fp64", out=out)
     assert rel_err(out.cpu().numpy(), ref) < FP64_TOL
+
+
+# per-form bound on |da|/rms|a|: the six-product forms carry ~24-bit products and meet 1e-5;
+# the two-piece forms (~21 and ~17 bits) are kept for comparison with looser bounds
+TC_BOUND = {"bf16x6": TC_TOL, "tf32x6": 3e-5, "tf32x3": 5e-5, "bf16x3": 2e-4, "tf32": 2e-2}
+
+
+@pytest.mark.parametrize("prec", ["bf16x6", "tf32x6", "tf32x3", "bf16x3"])
+def test_tensor_core_grid12_vs_statevector(tn, prec):
+    w = gen.workload("grid12")
+    ref = statevector_amplitudes(12, w.gates, w.bits)
+    a, _, _ = gpu_amplitudes(tn, 12, w.graph.edges, w.gates, w.bits, w.split, prec=prec)
+    assert rel_err(a, ref) < TC_BOUND[prec]
+
+
+def test_tensor_core_single_pass_tf32_is_coarse_but_close(tn):
+    """Single-pass TF32 (10-bit mantissa) misses 1e-5 by far but stays within a few 1e-3."""
+    w = gen.workload("grid12")
+    ref = statevector_amplitudes(12, w.gates, w.bits)
+    a, _, _ = gpu_amplitudes(tn, 12, w.graph.edges, w.gates, w.bits, w.split, prec="tf32")
+    assert rel_err(a, ref) < 2e-2
+
+
+def test_tensor_core_syc53_vs_oracle_and_fp64(tn):
+    w = gen.workload("syc53", n_bits=48)
+    ref = oracle_amplitudes(w.graph.n, w.graph.edges, w.gates, w.bits, w.split, w.chi, w.cutoff)
+    c = tn.tn_build(w.graph.n, w.graph.edges, w.gates)
+    tn.tn_evolve_two_sided(c, w.split, w.chi, w.cutoff)
+    p = tn.tn_path(c)
+    a64 = tn.tn_amplitudes(p, w.bits, "fp64")
+    assert rel_err(a64, ref) < FP64_TOL
+    for prec in ("bf16x6", "tf32x6", "tf32x3", "bf16x3", "tf32"):
+        tn.tn_profile_enable(True)
+        a = tn.tn_amplitudes(p, w.bits, prec)
+        prof = tn.tn_profile_read()
+        tn.tn_profile_enable(False)
+        assert prof.get("contract_step_tcgen05", {}).get("launches", 0) > 0
+        assert rel_err(a, ref) < TC_BOUND[prec], prec
+        assert rel_err(a, a64) < TC_BOUND[prec], prec
+
+
+def test_tensor_core_cuts_and_ragged_tiles(tn):
+    """Slices, M not a multiple of 128 and N not a multiple of the tile on the tcgen05 path.
+    The 14-cycle circuit is deep enough that complex64 storage itself costs about 1.4e-5
+    (FP32 SIMT path), so the bound here is 2e-5."""
+    w = gen.workload("grid20", n_bits=4)
+    ref = statevector_amplitudes(20, w.gates, w.bits)
+    a, _, p = gpu_amplitudes(tn, 20, w.graph.edges, w.gates, w.bits, w.split, prec="tf32x6",
+                             max_intermediate=1 << 22)
+    assert p.info["n_slices"] > 1
+    assert rel_err(a, ref) < 2e-5
