@@ -11,6 +11,7 @@
 // transpose-transpose-GEMM step cost no extra pass over memory.
 #include <cuda_runtime.h>
 
+#include "tn_device.h"
 #include "tn_internal.h"
 
 namespace {
@@ -74,7 +75,7 @@ __device__ __forceinline__ V overlap_elem(const V *ket, const V *bra, int64_t ia
 
 template <typename R>
 __global__ void form_kernel(StepParams s, ContractArgs a, const typename C2T<R>::T *ket,
-                            const typename C2T<R>::T *bra, typename C2T<R>::T *tout) {
+                            const typename C2T<R>::T *bra, OutDesc out) {
   using V = typename C2T<R>::T;
   int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= a.items * s.N) return;
@@ -82,8 +83,34 @@ __global__ void form_kernel(StepParams s, ContractArgs a, const typename C2T<R>:
   ItemCtx c = item_ctx(a, s, item);
   const V *kp = ket + s.ket_off + c.sa;
   const V *bp = bra + c.b * a.bra_stride + s.bra_off + c.sb;
-  tout[item * a.t_stride + a.tab[s.t_ocol + n]] =
-      overlap_elem(kp, bp, a.tab[s.t_bna + n], a.tab[s.t_bnb + n], s.ket_sig, s.bra_sig);
+  store_out(out, a.t_stride, item, a.tab[s.t_ocol + n],
+            overlap_elem(kp, bp, a.tab[s.t_bna + n], a.tab[s.t_bnb + n], s.ket_sig, s.bra_sig));
+}
+
+// the overlap tensor in its real embedding B_r[2N][2K] (row 2n = (Re c, -Im c), row 2n+1 =
+// (Im c, Re c) along k), as three bf16 planes, for the TMA-fed tensor-core step
+__global__ void form_b_kernel(StepParams s, ContractArgs a, const float2 *ket, const float2 *bra, Pieces B,
+                              int64_t item0) {
+  const unsigned kn = (unsigned)(s.K * s.N), K = (unsigned)s.K;
+  const unsigned r = blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t item = item0 + blockIdx.y;
+  if (r >= kn) return;
+  const unsigned n = r / K, k = r % K;
+  ItemCtx c = item_ctx(a, s, item);
+  const float2 *kp = ket + s.ket_off + c.sa;
+  const float2 *bp = bra + c.b * a.bra_stride + s.bra_off + c.sb;
+  const float2 v = overlap_elem(kp, bp, (int64_t)a.tab[s.t_bka + k] + a.tab[s.t_bna + n],
+                                (int64_t)a.tab[s.t_bkb + k] + a.tab[s.t_bnb + n], s.ket_sig, s.bra_sig);
+  uint32_t w0[3], w1[3];
+  tn_split3(v.x, -v.y, w0);
+  tn_split3(v.y, v.x, w1);
+  uint32_t *base = reinterpret_cast<uint32_t *>(const_cast<void *>(B.base)) + item * (B.item_elems / 2);
+  const int64_t plane = B.plane_elems / 2, row0 = (int64_t)(2 * n) * K + k, row1 = row0 + K;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    base[q * plane + row0] = w0[q];
+    base[q * plane + row1] = w1[q];
+  }
 }
 
 // the overlap tensor of the absorbed node, per item, as [N][K] complex64 (K contiguous)
@@ -105,7 +132,7 @@ __global__ void form_c_kernel(StepParams s, ContractArgs a, const float2 *ket, c
 template <typename R, int BM, int BN, int BK, int TM, int TN>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN))
 step_kernel(StepParams s, ContractArgs a, const typename C2T<R>::T *ket, const typename C2T<R>::T *bra,
-            const typename C2T<R>::T *tin, typename C2T<R>::T *tout) {
+            const typename C2T<R>::T *tin, OutDesc out) {
   using V = typename C2T<R>::T;
   constexpr int NT = (BM / TM) * (BN / TN);
   __shared__ V As[BK][BM + 1];
@@ -165,7 +192,6 @@ step_kernel(StepParams s, ContractArgs a, const typename C2T<R>::T *ket, const t
     }
     __syncthreads();
   }
-  V *op = tout + item * a.t_stride;
 #pragma unroll
   for (int i = 0; i < TM; ++i) {
     const int ro = rowoff[ty * TM + i];
@@ -173,7 +199,7 @@ step_kernel(StepParams s, ContractArgs a, const typename C2T<R>::T *ket, const t
 #pragma unroll
     for (int j = 0; j < TN; ++j) {
       int64_t n = n0 + tx * TN + j;
-      if (n < s.N) op[ro + ocol[n]] = acc[i][j];
+      if (n < s.N) store_out(out, a.t_stride, item, ro + ocol[n], acc[i][j]);
     }
   }
 }
@@ -182,7 +208,7 @@ step_kernel(StepParams s, ContractArgs a, const typename C2T<R>::T *ket, const t
 template <typename R>
 __global__ void __launch_bounds__(256)
 step_small_kernel(StepParams s, ContractArgs a, const typename C2T<R>::T *ket, const typename C2T<R>::T *bra,
-                  const typename C2T<R>::T *tin, typename C2T<R>::T *tout) {
+                  const typename C2T<R>::T *tin, OutDesc out) {
   using V = typename C2T<R>::T;
   __shared__ V red[256 / 32];
   const int64_t item = blockIdx.x;
@@ -193,8 +219,8 @@ step_small_kernel(StepParams s, ContractArgs a, const typename C2T<R>::T *ket, c
   const V *tp = tin + item * a.t_stride;
   const int32_t *bka = a.tab + s.t_bka, *bkb = a.tab + s.t_bkb;
   const int32_t *bna = a.tab + s.t_bna, *bnb = a.tab + s.t_bnb, *ocol = a.tab + s.t_ocol;
-  for (int64_t out = 0; out < s.M * s.N; ++out) {
-    int64_t m = out / s.N, n = out % s.N;
+  for (int64_t oi = 0; oi < s.M * s.N; ++oi) {
+    int64_t m = oi / s.N, n = oi % s.N;
     V acc = cz<V>();
     for (int64_t k = tid; k < s.K; k += 256) {
       V cv = overlap_elem(kp, bp, (int64_t)bka[k] + bna[n], (int64_t)bkb[k] + bnb[n], s.ket_sig, s.bra_sig);
@@ -209,7 +235,7 @@ step_small_kernel(StepParams s, ContractArgs a, const typename C2T<R>::T *ket, c
     if (tid == 0) {
       V t = cz<V>();
       for (int w = 0; w < 256 / 32; ++w) { t.x += red[w].x; t.y += red[w].y; }
-      tout[item * a.t_stride + orow_of(s, m) + ocol[n]] = t;
+      store_out(out, a.t_stride, item, orow_of(s, m) + ocol[n], t);
     }
     __syncthreads();
   }
@@ -220,7 +246,7 @@ step_small_kernel(StepParams s, ContractArgs a, const typename C2T<R>::T *ket, c
 template <typename R>
 __global__ void __launch_bounds__(256)
 step_stream_kernel(StepParams s, ContractArgs a, const typename C2T<R>::T *ket, const typename C2T<R>::T *bra,
-                   const typename C2T<R>::T *tin, typename C2T<R>::T *tout, int64_t rows_per_cta) {
+                   const typename C2T<R>::T *tin, OutDesc out, int64_t rows_per_cta) {
   using V = typename C2T<R>::T;
   __shared__ V Cs[16 * 16];
   __shared__ int oc[16];
@@ -240,7 +266,6 @@ step_stream_kernel(StepParams s, ContractArgs a, const typename C2T<R>::T *ket, 
   if (tid < N) oc[tid] = a.tab[s.t_ocol + tid];
   __syncthreads();
   const V *tp = tin + item * a.t_stride;
-  V *op = tout + item * a.t_stride;
   const int64_t m1 = m0 + rows_per_cta < s.M ? m0 + rows_per_cta : s.M;
   for (int64_t m = m0 + tid; m < m1; m += 256) {
     V x[16];
@@ -255,7 +280,7 @@ step_stream_kernel(StepParams s, ContractArgs a, const typename C2T<R>::T *ket, 
 #pragma unroll
       for (int k = 0; k < 16; ++k)
         if (k < K) acc = cfma(x[k], Cs[k * N + n], acc);
-      op[ro + oc[n]] = acc;
+      store_out(out, a.t_stride, item, ro + oc[n], acc);
     }
   }
 }
@@ -277,13 +302,13 @@ __global__ void slice_sum_kernel(const typename C2T<R>::T *res, int64_t stride, 
 
 template <typename R, int BM, int BN, int BK, int TM, int TN>
 cudaError_t launch_tiled(const StepParams &s, const ContractArgs &a, const void *ket, const void *bra,
-                         const void *t_in, void *t_out, cudaStream_t st) {
+                         const void *t_in, const OutDesc &t_out, cudaStream_t st) {
   using V = typename C2T<R>::T;
   int64_t tiles = ((s.M + BM - 1) / BM) * ((s.N + BN - 1) / BN);
   int64_t grid = tiles * a.items;
   if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
   step_kernel<R, BM, BN, BK, TM, TN><<<(unsigned)grid, (BM / TM) * (BN / TN), 0, st>>>(
-      s, a, (const V *)ket, (const V *)bra, (const V *)t_in, (V *)t_out);
+      s, a, (const V *)ket, (const V *)bra, (const V *)t_in, t_out);
   tn_count_launch(1);
   return cudaGetLastError();
 }
@@ -291,12 +316,12 @@ cudaError_t launch_tiled(const StepParams &s, const ContractArgs &a, const void 
 }  // namespace
 
 template <typename R>
-cudaError_t launch_form(const StepParams &s, const ContractArgs &a, const void *ket, const void *bra, void *t_out,
-                        cudaStream_t st) {
+cudaError_t launch_form(const StepParams &s, const ContractArgs &a, const void *ket, const void *bra,
+                        const OutDesc &t_out, cudaStream_t st) {
   using V = typename C2T<R>::T;
   int64_t total = a.items * s.N;
   if (total <= 0) return cudaSuccess;
-  form_kernel<R><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(s, a, (const V *)ket, (const V *)bra, (V *)t_out);
+  form_kernel<R><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(s, a, (const V *)ket, (const V *)bra, t_out);
   tn_count_launch(1);
   return cudaGetLastError();
 }
@@ -314,9 +339,21 @@ cudaError_t launch_form_c(const StepParams &s, const ContractArgs &a, const floa
   return cudaGetLastError();
 }
 
+cudaError_t launch_form_b_pieces(const StepParams &s, const ContractArgs &a, const float2 *ket, const float2 *bra,
+                                 const Pieces &B, cudaStream_t st) {
+  const int64_t kn = s.K * s.N;
+  if (kn <= 0 || a.items <= 0) return cudaSuccess;
+  for (int64_t i0 = 0; i0 < a.items; i0 += 65535) {
+    const int64_t ni = a.items - i0 < 65535 ? a.items - i0 : 65535;
+    form_b_kernel<<<dim3((unsigned)((kn + 255) / 256), (unsigned)ni), 256, 0, st>>>(s, a, ket, bra, B, i0);
+  }
+  tn_count_launch(1);
+  return cudaGetLastError();
+}
+
 template <typename R>
 cudaError_t launch_step(const StepParams &s, const ContractArgs &a, const void *ket, const void *bra,
-                        const void *t_in, void *t_out, cudaStream_t st) {
+                        const void *t_in, const OutDesc &t_out, cudaStream_t st) {
   using V = typename C2T<R>::T;
   if (a.items <= 0) return cudaSuccess;
   if (s.K <= 16 && s.N <= 16 && s.M >= 512) {
@@ -324,14 +361,14 @@ cudaError_t launch_step(const StepParams &s, const ContractArgs &a, const void *
     const int64_t grid = ((s.M + rows - 1) / rows) * a.items;
     if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     step_stream_kernel<R><<<(unsigned)grid, 256, 0, st>>>(s, a, (const V *)ket, (const V *)bra, (const V *)t_in,
-                                                          (V *)t_out, rows);
+                                                          t_out, rows);
     tn_count_launch(1);
     return cudaGetLastError();
   }
   if (s.M * s.N <= 16) {
     if (a.items > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     step_small_kernel<R><<<(unsigned)a.items, 256, 0, st>>>(s, a, (const V *)ket, (const V *)bra, (const V *)t_in,
-                                                            (V *)t_out);
+                                                            t_out);
     tn_count_launch(1);
     return cudaGetLastError();
   }
@@ -351,13 +388,13 @@ cudaError_t launch_slice_sum(const void *res, int64_t items_stride, int64_t n_bi
   return cudaGetLastError();
 }
 
-template cudaError_t launch_form<double>(const StepParams &, const ContractArgs &, const void *, const void *, void *,
-                                         cudaStream_t);
-template cudaError_t launch_form<float>(const StepParams &, const ContractArgs &, const void *, const void *, void *,
-                                        cudaStream_t);
+template cudaError_t launch_form<double>(const StepParams &, const ContractArgs &, const void *, const void *,
+                                         const OutDesc &, cudaStream_t);
+template cudaError_t launch_form<float>(const StepParams &, const ContractArgs &, const void *, const void *,
+                                        const OutDesc &, cudaStream_t);
 template cudaError_t launch_step<double>(const StepParams &, const ContractArgs &, const void *, const void *,
-                                         const void *, void *, cudaStream_t);
+                                         const void *, const OutDesc &, cudaStream_t);
 template cudaError_t launch_step<float>(const StepParams &, const ContractArgs &, const void *, const void *,
-                                        const void *, void *, cudaStream_t);
+                                        const void *, const OutDesc &, cudaStream_t);
 template cudaError_t launch_slice_sum<double>(const void *, int64_t, int64_t, int64_t, int, double2 *, cudaStream_t);
 template cudaError_t launch_slice_sum<float>(const void *, int64_t, int64_t, int64_t, int, double2 *, cudaStream_t);

@@ -1104,7 +1104,8 @@ static tn_status compile_plan(tn_circuit *c, tn_plan *p) {
     }
     maxT = std::max(maxT, M * N);
   }
-  maxT = (maxT + 1) & ~1LL;   // even: 16-byte aligned item strides for complex64
+  maxT = (maxT + 7) & ~7LL;             // item strides stay 16-byte aligned in every format
+  p->maxKN = (p->maxKN + 1) & ~1LL;
   if (maxT >= (1LL << 31) || (int64_t)tab.size() >= (1LL << 31))
     return tn_fail(TN_ERR_UNSUPPORTED, "intermediate of %lld elements exceeds the 2^31 index range; add cuts",
                    (long long)maxT);
@@ -1142,8 +1143,9 @@ int64_t plan_ws_bytes(const tn_plan *p, int kind, int64_t chunk, int64_t slices)
   b += chunk * c->bra.item_elems * 16;                      // bra FP64
   if (kind) b += chunk * c->bra.item_elems * 8;             // bra c64 copy
   b += chunk * std::max<int64_t>(c->bra.max_work, 1) * 16;  // SVD work beyond shared memory
-  b += 2 * chunk * slices * p->maxT * el;                   // ping-pong intermediates
-  if (kind) b += chunk * slices * p->maxKN * 8;             // overlap tensors for the tensor-core steps
+  // ping-pong intermediates (complex64 or three bf16 pieces per real on the complex64 paths)
+  b += 2 * chunk * slices * p->maxT * (kind ? 12 : el);
+  if (kind) b += chunk * slices * p->maxKN * 24;            // overlap tensors of the tensor-core steps
   b += chunk * 16 + 4096;                                   // results, flags
   return b;
 }
@@ -1264,9 +1266,10 @@ tn_status ws_ensure(tn_plan *p, Workspace &w, int kind, cudaStream_t st) {
   if ((s = mem.ensure(w.bra64, ch * c->bra.item_elems * 16, st)) != TN_OK) return s;
   if (kind && (s = mem.ensure(w.bra32, ch * c->bra.item_elems * 8, st)) != TN_OK) return s;
   if ((s = mem.ensure(w.gwork, ch * std::max<int64_t>(c->bra.max_work, 1) * 16, st)) != TN_OK) return s;
-  if ((s = mem.ensure(w.t0, ch * sc * p->maxT * el, st)) != TN_OK) return s;
-  if ((s = mem.ensure(w.t1, ch * sc * p->maxT * el, st)) != TN_OK) return s;
-  if (kind && (s = mem.ensure(w.cbuf, ch * sc * p->maxKN * 8, st)) != TN_OK) return s;
+  const int64_t tel = kind ? 12 : el;
+  if ((s = mem.ensure(w.t0, ch * sc * p->maxT * tel, st)) != TN_OK) return s;
+  if ((s = mem.ensure(w.t1, ch * sc * p->maxT * tel, st)) != TN_OK) return s;
+  if (kind && (s = mem.ensure(w.cbuf, ch * sc * p->maxKN * 24, st)) != TN_OK) return s;
   if ((s = mem.ensure(w.res, ch * 16, st)) != TN_OK) return s;
   if ((s = mem.ensure(w.err, 64, st)) != TN_OK) return s;
   w.chunk = (int)ch;
@@ -1311,6 +1314,16 @@ tn_status run_amplitudes(tn_plan *p, Workspace &w, const uint64_t *bits, int64_t
       CUDA_TRY(launch_to_c64((const double2 *)w.bra64.p, (float2 *)w.bra32.p, nb * c->bra.item_elems, st));
       bra = w.bra32.p;
     }
+    // kernel per step: 0 SIMT, 1 tcgen05 with in-kernel operand split, 2 TMA-fed tcgen05 (BF16x6);
+    // a producer writes bf16 pieces when its consumer is a TMA step, else complex64
+    const size_t nsteps = p->steps.size();
+    std::vector<int> path(nsteps, 0);
+    for (size_t j = 1; j < nsteps; ++j) {
+      const StepParams &sp = p->steps[j];
+      if (prec == TN_BF16X6) path[j] = tma_step_supported(sp) ? 2 : 0;
+      else if (prec != TN_FP64 && prec != TN_FP32) path[j] = tc_step_supported(sp) ? 1 : 0;
+    }
+    const int64_t cap = (int64_t)w.chunk * w.slice_chunk;     // items the buffers hold
     for (int64_t s0 = 0; s0 < S; s0 += w.slice_chunk) {
       const int64_t sg = std::min<int64_t>(w.slice_chunk, S - s0);
       ContractArgs a;
@@ -1322,23 +1335,31 @@ tn_status run_amplitudes(tn_plan *p, Workspace &w, const uint64_t *bits, int64_t
       a.bra_stride = c->bra.item_elems;
       void *tin = w.t0.p, *tout = w.t1.p;
       const double el = kind ? 8.0 : 16.0;
+      auto out_for = [&](void *buf, size_t consumer) {
+        OutDesc o;
+        o.p = buf;
+        o.fmt = (consumer < nsteps && path[consumer] == 2) ? 1 : 0;
+        o.plane_u32 = cap * p->maxT;
+        return o;
+      };
       {
         ProfScope ps(kind ? "overlap_form_c64" : "overlap_form_c128", st, el * a.items * p->steps[0].N, 0);
-        if (kind) CUDA_TRY(launch_form<float>(p->steps[0], a, ket, bra, tin, st));
-        else CUDA_TRY(launch_form<double>(p->steps[0], a, ket, bra, tin, st));
+        if (kind) CUDA_TRY(launch_form<float>(p->steps[0], a, ket, bra, out_for(tin, 1), st));
+        else CUDA_TRY(launch_form<double>(p->steps[0], a, ket, bra, out_for(tin, 1), st));
       }
-      for (size_t j = 1; j < p->steps.size(); ++j) {
+      for (size_t j = 1; j < nsteps; ++j) {
         const StepParams &sp = p->steps[j];
         const double items = (double)a.items;
         const double by = el * items * ((double)sp.M * sp.K + (double)sp.M * sp.N);
         const double fl = 8.0 * items * (double)sp.M * sp.K * sp.N;
+        const OutDesc od = out_for(tout, j + 1);
         if (prec == TN_FP64) {
           ProfScope ps("contract_step_fp64", st, by, fl);
-          CUDA_TRY(launch_step<double>(sp, a, ket, bra, tin, tout, st));
-        } else if (prec == TN_FP32 || !tc_step_supported(sp)) {
+          CUDA_TRY(launch_step<double>(sp, a, ket, bra, tin, od, st));
+        } else if (path[j] == 0) {
           ProfScope ps(prec == TN_FP32 ? "contract_step_fp32" : "contract_step_fp32_tc_fallback", st, by, fl);
-          CUDA_TRY(launch_step<float>(sp, a, ket, bra, tin, tout, st));
-        } else {
+          CUDA_TRY(launch_step<float>(sp, a, ket, bra, tin, od, st));
+        } else if (path[j] == 1) {
           {
             ProfScope ps("overlap_form_c64", st, 8.0 * items * (double)sp.K * sp.N, 16.0 * items * (double)sp.K * sp.N);
             CUDA_TRY(launch_form_c(sp, a, (const float2 *)ket, (const float2 *)bra, (float2 *)w.cbuf.p, p->maxKN, st));
@@ -1346,6 +1367,25 @@ tn_status run_amplitudes(tn_plan *p, Workspace &w, const uint64_t *bits, int64_t
           ProfScope ps("contract_step_tcgen05", st, by + 8.0 * items * (double)sp.K * sp.N, fl);
           CUDA_TRY(launch_step_tc((int)prec, sp, a, (const float2 *)w.cbuf.p, p->maxKN, (const float2 *)tin,
                                   (float2 *)tout, (int *)w.err.p + 1, st));
+        } else {
+          Pieces B;
+          B.base = w.cbuf.p;
+          B.item_elems = 4 * p->maxKN;
+          B.plane_elems = cap * B.item_elems;
+          {
+            ProfScope ps("overlap_form_bf16_pieces", st, 24.0 * items * (double)sp.K * sp.N,
+                         16.0 * items * (double)sp.K * sp.N);
+            CUDA_TRY(launch_form_b_pieces(sp, a, (const float2 *)ket, (const float2 *)bra, B, st));
+          }
+          Pieces A;
+          A.base = tin;
+          A.item_elems = 2 * p->maxT;
+          A.plane_elems = cap * A.item_elems;
+          // algorithmic bytes of the step in its operand format: A and B pieces read, output written
+          const double byp = items * (12.0 * (double)sp.M * sp.K + 24.0 * (double)sp.K * sp.N +
+                                      (od.fmt ? 12.0 : 8.0) * (double)sp.M * sp.N);
+          ProfScope ps("contract_step_tcgen05_tma", st, byp, fl);
+          CUDA_TRY(launch_step_tma(sp, a, A, B, od, (int *)w.err.p + 1, st));
         }
         std::swap(tin, tout);
       }

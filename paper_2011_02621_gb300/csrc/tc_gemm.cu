@@ -24,6 +24,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "tn_device.h"
 #include "tn_internal.h"
 
 namespace {

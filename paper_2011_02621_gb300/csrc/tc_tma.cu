@@ -1,0 +1,341 @@
+// TMA-fed tcgen05 contraction step (BF16x6 form): the operand path uses no CUDA-core work.
+//
+// Operands arrive pre-split. Every complex64 value x of an intermediate that feeds a
+// tensor-core step is stored by its producer as three bf16 planes x = x_0 + x_1 + x_2 (each
+// piece exact), in the consumer's row-major [M][2K] layout (interleaved re, im). The overlap
+// tensor C of the absorbed node (Eq. overlap) is written by the formation kernel in its real
+// embedding B_r[2N][2K] (row 2n = (Re c, -Im c), row 2n+1 = (Im c, Re c) along k), split the
+// same way. One CTA computes a 128 x BN real output tile of one item:
+//   warp 0   issues cp.async.bulk.tensor loads of the 3 A and 3 B pieces of each 64-real K
+//            chunk into a ring of shared-memory stages (128-byte swizzle, the canonical
+//            K-major layout of the MMA), signalling a "full" mbarrier with the byte count;
+//   warp 1   allocates TMEM and issues tcgen05.mma kind::f16 (bf16 in, fp32 accumulate) for
+//            the six products x_i*y_j with i + j <= 2, order 0 spread round-robin over R
+//            accumulators, orders 1 and 2 in one accumulator each; each stage is released by
+//            tcgen05.commit on its "empty" mbarrier, the last one on "done";
+//   warps 2-5 wait for "done", read the accumulators with tcgen05.ld, add them smallest first
+//            and write the result straight into the next step's layout, as complex64 or as
+//            bf16 pieces for the next tensor-core step.
+// Every wait is bounded by a clock limit and raises an error code instead of hanging.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "tn_device.h"
+#include "tn_internal.h"
+
+namespace {
+
+constexpr int T_THREADS = 192;
+constexpr int T_BM = 128;
+constexpr int T_P = 3;
+constexpr long long T_WAIT = 500000000LL;   // ~0.25 s at 2 GHz
+
+__device__ __forceinline__ uint32_t s_u32(const void *p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
+
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;                        // leading byte offset (unused, swizzled K-major)
+  d |= (uint64_t)(1024u >> 4) << 32;             // stride byte offset: next 8-row group
+  d |= (uint64_t)1 << 46;                        // descriptor version for tcgen05
+  d |= (uint64_t)2 << 61;                        // SWIZZLE_128B
+  return d;
+}
+
+__device__ __forceinline__ uint32_t idesc_bf16(int bn) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(bn >> 3) << 17) | ((uint32_t)(T_BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void bar_init(uint32_t a, uint32_t n) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(n) : "memory");
+}
+
+__device__ __forceinline__ bool bar_try(uint32_t a, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(a), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ bool bar_wait(uint32_t a, uint32_t parity, int *err, int code) {
+  const long long t0 = clock64();
+  while (!bar_try(a, parity)) {
+    if (clock64() - t0 > T_WAIT) {
+      atomicCAS(err, 0, code);
+      return false;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void bar_expect_tx(uint32_t a, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void tma_3d(uint32_t dst, const CUtensorMap *map, int x, int y, int z, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit_to(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+}  // namespace
+
+namespace {
+
+template <int BN, int R, int S>
+__global__ void __launch_bounds__(T_THREADS, 1)
+tma_step_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMap tA1,
+                const __grid_constant__ CUtensorMap tA2, const __grid_constant__ CUtensorMap tB0,
+                const __grid_constant__ CUtensorMap tB1, const __grid_constant__ CUtensorMap tB2, StepParams s,
+                ContractArgs a, OutDesc out, int *err) {
+  constexpr int A_BYTES = T_BM * 128, B_BYTES = BN * 128;
+  constexpr int STAGE = T_P * (A_BYTES + B_BYTES);
+  constexpr int GROUPS = R + 2;
+  constexpr uint32_t TMEM_COLS = GROUPS * BN <= 32 ? 32 : GROUPS * BN <= 64 ? 64 : GROUPS * BN <= 128 ? 128
+                                 : GROUPS * BN <= 256 ? 256 : 512;
+  static_assert(GROUPS * BN <= 512, "TMEM columns");
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ __align__(8) uint64_t full[S], empty[S], done;
+  __shared__ uint32_t tmem_s;
+  __shared__ int rowoff[T_BM];
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t tiles_m = (s.M + T_BM - 1) / T_BM, tiles_n = (2 * s.N + BN - 1) / BN;
+  const int64_t blk = blockIdx.x;
+  const int item = (int)(blk / (tiles_m * tiles_n));
+  const int64_t rem = blk % (tiles_m * tiles_n);
+  const int m0 = (int)((rem / tiles_n) * T_BM);
+  const int nr0 = (int)((rem % tiles_n) * BN);
+  const int64_t nk = (2 * s.K + 63) / 64;        // 64-real K chunks
+
+  if (tid == 0) {
+    for (int i = 0; i < S; ++i) {
+      bar_init(s_u32(&full[i]), 1);
+      bar_init(s_u32(&empty[i]), 1);
+    }
+    bar_init(s_u32(&done), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(s_u32(&tmem_s)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid >= 64 && tid < 64 + T_BM) {            // epilogue warps: output row offsets
+    const int r = tid - 64;
+    const int64_t m = m0 + r;
+    int off = -1;
+    if (m < s.M) {
+      off = 0;
+      unsigned mm = (unsigned)m;
+      for (int j = s.n_rest - 1; j >= 0; --j) {
+        if (s.rest_pow2) {
+          off += (int)(mm & ((1u << s.rest_log2[j]) - 1u)) * s.rest_ostride[j];
+          mm >>= s.rest_log2[j];
+        } else {
+          const unsigned d = (unsigned)s.rest_dim[j];
+          off += (int)(mm % d) * s.rest_ostride[j];
+          mm /= d;
+        }
+      }
+    }
+    rowoff[r] = off;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_s;
+
+  if (warp == 0) {
+    // ---------------- TMA producer
+    if (lane == 0) {
+      const CUtensorMap *mA[3] = {&tA0, &tA1, &tA2};
+      const CUtensorMap *mB[3] = {&tB0, &tB1, &tB2};
+      int64_t issued = 0;
+      for (int64_t kc = 0; kc < nk; ++kc) {
+        const int st = (int)(kc % S);
+        const uint32_t it = (uint32_t)(kc / S);
+        if (kc >= S && !bar_wait(s_u32(&empty[st]), (it - 1) & 1, err, 11)) break;
+        uint8_t *base = smem + st * STAGE;
+        bar_expect_tx(s_u32(&full[st]), (uint32_t)STAGE);
+        for (int q = 0; q < T_P; ++q)
+          tma_3d(s_u32(base + q * A_BYTES), mA[q], (int)(kc * 64), m0, item, s_u32(&full[st]));
+        for (int q = 0; q < T_P; ++q)
+          tma_3d(s_u32(base + T_P * A_BYTES + q * B_BYTES), mB[q], (int)(kc * 64), nr0, item, s_u32(&full[st]));
+        ++issued;
+      }
+      if (issued > 0) {   // the last loads must have landed before the CTA may exit
+        const int64_t last = issued - 1;
+        bar_wait(s_u32(&full[last % S]), (uint32_t)((last / S) & 1), err, 12);
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16(BN);
+      for (int64_t kc = 0; kc < nk; ++kc) {
+        const int st = (int)(kc % S);
+        if (!bar_wait(s_u32(&full[st]), (uint32_t)((kc / S) & 1), err, 13)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t a0 = s_u32(smem + st * STAGE), b0 = a0 + T_P * A_BYTES;
+#pragma unroll
+        for (int ks = 0; ks < 4; ++ks) {          // 16 bf16 (32 bytes) of K per instruction
+          const uint32_t off = (uint32_t)ks * 32u;
+          const int64_t t = kc * 4 + ks;
+          const uint32_t first = (t == 0) ? 0u : 1u;
+          mma_bf16(tmem + (uint32_t)((t % R) * BN), desc_sw128(a0 + off), desc_sw128(b0 + off), idesc,
+                   t < R ? 0u : 1u);
+          // order 1: x0*y1 + x1*y0
+          mma_bf16(tmem + (uint32_t)(R * BN), desc_sw128(a0 + off), desc_sw128(b0 + B_BYTES + off), idesc, first);
+          mma_bf16(tmem + (uint32_t)(R * BN), desc_sw128(a0 + A_BYTES + off), desc_sw128(b0 + off), idesc, 1u);
+          // order 2: x0*y2 + x1*y1 + x2*y0
+          mma_bf16(tmem + (uint32_t)((R + 1) * BN), desc_sw128(a0 + off), desc_sw128(b0 + 2 * B_BYTES + off), idesc,
+                   first);
+          mma_bf16(tmem + (uint32_t)((R + 1) * BN), desc_sw128(a0 + A_BYTES + off),
+                   desc_sw128(b0 + B_BYTES + off), idesc, 1u);
+          mma_bf16(tmem + (uint32_t)((R + 1) * BN), desc_sw128(a0 + 2 * A_BYTES + off), desc_sw128(b0 + off), idesc,
+                   1u);
+        }
+        mma_commit_to(s_u32(&empty[st]));
+      }
+      mma_commit_to(s_u32(&done));               // after every issued MMA, also on an early stop
+    }
+  } else {
+    // ---------------- epilogue (warps 2..5 -> TMEM lane groups 2, 3, 0, 1)
+    const bool ok = bar_wait(s_u32(&done), 0u, err, 14);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int lg = warp & 3;
+    const int ro = rowoff[lg * 32 + lane];
+    const bool all = ok && (*(volatile int *)err == 0);
+    const int32_t *ocol = a.tab + s.t_ocol;
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN && all; c0 += 16) {
+      float acc[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) acc[j] = 0.f;
+#pragma unroll
+      for (int g = GROUPS - 1; g >= 0; --g) {
+        if (g < R && (int64_t)g >= nk * 4) continue;   // order-0 accumulator never written
+        uint32_t r[16];
+        const uint32_t taddr = tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(g * BN + c0);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int j = 0; j < 16; ++j) acc[j] += __uint_as_float(r[j]);
+      }
+      if (ro >= 0) {
+#pragma unroll
+        for (int j = 0; j < 16; j += 2) {
+          const int64_t n = (nr0 + c0 + j) >> 1;
+          if (n < s.N) store_out(out, a.t_stride, item, ro + ocol[n], make_float2(acc[j], acc[j + 1]));
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+// driver entry point for tensor-map encoding (no link-time dependency on libcuda)
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// 3-D bf16 map {inner, rows, items}, box {64, box_rows, 1}, 128-byte swizzle, zero fill outside
+bool make_map(CUtensorMap *m, const void *base, uint64_t inner, uint64_t rows, uint64_t items, uint64_t row_bytes,
+              uint64_t item_bytes, uint32_t box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[3] = {inner, rows, items};
+  cuuint64_t strides[2] = {row_bytes, item_bytes};
+  cuuint32_t box[3] = {64, box_rows, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+template <int BN, int R, int S>
+cudaError_t launch_t(const StepParams &s, const ContractArgs &a, const Pieces &A, const Pieces &B, const OutDesc &out,
+                     int *err, cudaStream_t st) {
+  constexpr size_t stage = (size_t)T_P * (T_BM * 128 + BN * 128);
+  const size_t smem = S * stage + 1024;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(tma_step_kernel<BN, R, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  CUtensorMap mA[3], mB[3];
+  const uint64_t K2 = (uint64_t)(2 * s.K), N2 = (uint64_t)(2 * s.N);
+  for (int q = 0; q < T_P; ++q) {
+    if (!make_map(&mA[q], (const uint16_t *)A.base + q * A.plane_elems, K2, (uint64_t)s.M, (uint64_t)a.items, K2 * 2,
+                  (uint64_t)A.item_elems * 2, T_BM))
+      return cudaErrorInvalidValue;
+    if (!make_map(&mB[q], (const uint16_t *)B.base + q * B.plane_elems, K2, N2, (uint64_t)a.items, K2 * 2,
+                  (uint64_t)B.item_elems * 2, BN))
+      return cudaErrorInvalidValue;
+  }
+  const int64_t tiles = ((s.M + T_BM - 1) / T_BM) * ((2 * s.N + BN - 1) / BN);
+  const int64_t grid = tiles * a.items;
+  if (grid <= 0) return cudaSuccess;
+  if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  tma_step_kernel<BN, R, S><<<(unsigned)grid, T_THREADS, smem, st>>>(mA[0], mA[1], mA[2], mB[0], mB[1], mB[2], s, a,
+                                                                     out, err);
+  tn_count_launch(1);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool tma_step_supported(const StepParams &s) {
+  // 16-byte TMA strides (K a multiple of 4), tiles mostly useful, indices within 32 bits
+  return s.M >= 64 && 2 * s.N >= 64 && s.K >= 8 && (s.K % 4) == 0 && 2 * s.K < (1LL << 31);
+}
+
+cudaError_t launch_step_tma(const StepParams &s, const ContractArgs &a, const Pieces &A, const Pieces &B,
+                            const OutDesc &out, int *err, cudaStream_t st) {
+  if (2 * s.N >= 128) return launch_t<128, 2, 2>(s, a, A, B, out, err, st);
+  return launch_t<64, 6, 3>(s, a, A, B, out, err, st);
+}

@@ -81,13 +81,30 @@ struct ContractArgs {
   int64_t bra_stride;           // elements per bitstring region of the bra buffer
 };
 
+// Where a producer writes an intermediate: fmt 0 = complex64 (or complex128 on the FP64
+// path) at [item * t_stride + offset]; fmt 1 = three bf16 planes (pieces of every real, see
+// the tensor-core step), plane q at (uint32 *)p + q * plane_u32, the (re, im) pair of a complex
+// element as one uint32 at [item * t_stride + offset].
+struct OutDesc {
+  void *p;
+  int fmt;
+  int64_t plane_u32;
+};
+
+// bf16 pieces operand for a TMA load: plane q at (uint16 *)base + q * plane_elems, item i at
+// + i * item_elems (bf16 elements)
+struct Pieces {
+  const void *base;
+  int64_t plane_elems, item_elems;
+};
+
 // precision-templated launchers (R = double or float)
 template <typename R>
 cudaError_t launch_form(const StepParams &s, const ContractArgs &a, const void *ket, const void *bra,
-                        void *t_out, cudaStream_t st);
+                        const OutDesc &out, cudaStream_t st);
 template <typename R>
 cudaError_t launch_step(const StepParams &s, const ContractArgs &a, const void *ket, const void *bra,
-                        const void *t_in, void *t_out, cudaStream_t st);
+                        const void *t_in, const OutDesc &out, cudaStream_t st);
 // out[b] (+)= sum over the group's slices, in slice order, in FP64 (accumulate: add to out)
 template <typename R>
 cudaError_t launch_slice_sum(const void *res, int64_t items_stride, int64_t n_bits, int64_t n_slices,
@@ -100,6 +117,13 @@ cudaError_t launch_form_c(const StepParams &s, const ContractArgs &a, const floa
 cudaError_t launch_step_tc(int prec, const StepParams &s, const ContractArgs &a, const float2 *cbuf,
                            int64_t c_stride, const float2 *t_in, float2 *t_out, int *errflag, cudaStream_t st);
 bool tc_step_supported(const StepParams &s);
+// the overlap tensor of one step in its real embedding, split into three bf16 planes
+cudaError_t launch_form_b_pieces(const StepParams &s, const ContractArgs &a, const float2 *ket, const float2 *bra,
+                                 const Pieces &B, cudaStream_t st);
+// TMA-fed tcgen05 step (BF16x6) from pre-split A and B pieces
+cudaError_t launch_step_tma(const StepParams &s, const ContractArgs &a, const Pieces &A, const Pieces &B,
+                            const OutDesc &out, int *err, cudaStream_t st);
+bool tma_step_supported(const StepParams &s);
 
 // launch accounting
 void tn_count_launch(int64_t k);

@@ -229,7 +229,8 @@ def test_tensor_core_syc53_vs_oracle_and_fp64(tn):
         a = tn.tn_amplitudes(p, w.bits, prec)
         prof = tn.tn_profile_read()
         tn.tn_profile_enable(False)
-        assert prof.get("contract_step_tcgen05", {}).get("launches", 0) > 0
+        tc = sum(v["launches"] for k, v in prof.items() if k.startswith("contract_step_tcgen05"))
+        assert tc > 0, prec
         assert rel_err(a, ref) < TC_BOUND[prec], prec
         assert rel_err(a, a64) < TC_BOUND[prec], prec
 
