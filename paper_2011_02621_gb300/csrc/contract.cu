@@ -267,12 +267,27 @@ step_stream_kernel(StepParams s, ContractArgs a, const typename C2T<R>::T *ket, 
   __syncthreads();
   const V *tp = tin + item * a.t_stride;
   const int64_t m1 = m0 + rows_per_cta < s.M ? m0 + rows_per_cta : s.M;
+  const bool four = (N == 4 && oc[3] - oc[0] == 3);   // the four outputs of a row are contiguous
   for (int64_t m = m0 + tid; m < m1; m += 256) {
     V x[16];
 #pragma unroll
     for (int k = 0; k < 16; ++k)
       if (k < K) x[k] = tp[m * K + k];
     const int ro = orow_of(s, m);
+    if (four) {
+      R v[8];
+#pragma unroll
+      for (int n = 0; n < 4; ++n) {
+        V acc = cz<V>();
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+          if (k < K) acc = cfma(x[k], Cs[k * 4 + n], acc);
+        v[2 * n] = acc.x;
+        v[2 * n + 1] = acc.y;
+      }
+      store_out4(out, a.t_stride, item, ro + oc[0], v);
+      continue;
+    }
 #pragma unroll
     for (int n = 0; n < 16; ++n) {
       if (n >= N) break;

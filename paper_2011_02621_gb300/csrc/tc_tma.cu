@@ -234,28 +234,38 @@ tma_step_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__
     const int32_t *ocol = a.tab + s.t_ocol;
 #pragma unroll 1
     for (int c0 = 0; c0 < BN && all; c0 += 16) {
-      float acc[16];
+      // all accumulators of this 16-column block, one wait, summed smallest first
+      uint32_t r[GROUPS][16];
 #pragma unroll
-      for (int j = 0; j < 16; ++j) acc[j] = 0.f;
-#pragma unroll
-      for (int g = GROUPS - 1; g >= 0; --g) {
-        if (g < R && (int64_t)g >= nk * 4) continue;   // order-0 accumulator never written
-        uint32_t r[16];
+      for (int g = 0; g < GROUPS; ++g) {
         const uint32_t taddr = tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(g * BN + c0);
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "=r"(r[g][0]), "=r"(r[g][1]), "=r"(r[g][2]), "=r"(r[g][3]), "=r"(r[g][4]), "=r"(r[g][5]),
+              "=r"(r[g][6]), "=r"(r[g][7]), "=r"(r[g][8]), "=r"(r[g][9]), "=r"(r[g][10]), "=r"(r[g][11]),
+              "=r"(r[g][12]), "=r"(r[g][13]), "=r"(r[g][14]), "=r"(r[g][15])
             : "r"(taddr));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      }
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      float acc[16];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) acc[j] += __uint_as_float(r[j]);
+      for (int j = 0; j < 16; ++j) {
+        float v = 0.f;
+#pragma unroll
+        for (int g = GROUPS - 1; g >= 0; --g)
+          if (g >= R || (int64_t)g < nk * 4) v += __uint_as_float(r[g][j]);   // unwritten order-0 slots skipped
+        acc[j] = v;
       }
       if (ro >= 0) {
+        const int64_t n0 = (nr0 + c0) >> 1;    // eight complex columns n0 .. n0 + 7
+        if (n0 + 7 < s.N && ocol[n0 + 7] - ocol[n0] == 7) {
+          store_out8(out, a.t_stride, item, ro + ocol[n0], acc);
+        } else {
 #pragma unroll
-        for (int j = 0; j < 16; j += 2) {
-          const int64_t n = (nr0 + c0 + j) >> 1;
-          if (n < s.N) store_out(out, a.t_stride, item, ro + ocol[n], make_float2(acc[j], acc[j + 1]));
+          for (int j = 0; j < 16; j += 2) {
+            const int64_t n = n0 + (j >> 1);
+            if (n < s.N) store_out(out, a.t_stride, item, ro + ocol[n], make_float2(acc[j], acc[j + 1]));
+          }
         }
       }
     }

@@ -41,3 +41,86 @@ __device__ __forceinline__ void store_out(const OutDesc &o, int64_t t_stride, in
 __device__ __forceinline__ void store_out(const OutDesc &o, int64_t t_stride, int64_t item, int64_t off, double2 v) {
   reinterpret_cast<double2 *>(o.p)[item * t_stride + off] = v;
 }
+
+// Eight consecutive complex outputs (v[0..15] = re, im pairs) at offsets off .. off + 7 of one
+// item: 16-byte vector stores when off is aligned for them, scalar stores otherwise.
+__device__ __forceinline__ void store_out8(const OutDesc &o, int64_t t_stride, int64_t item, int64_t off,
+                                           const float v[16]) {
+  if (o.fmt == 0) {
+    float2 *b = reinterpret_cast<float2 *>(o.p) + item * t_stride + off;
+    if ((off & 1) == 0) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        reinterpret_cast<float4 *>(b)[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) b[j] = make_float2(v[2 * j], v[2 * j + 1]);
+    }
+  } else {
+    uint32_t w[3][8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      uint32_t t[3];
+      tn_split3(v[2 * j], v[2 * j + 1], t);
+      w[0][j] = t[0];
+      w[1][j] = t[1];
+      w[2][j] = t[2];
+    }
+    uint32_t *b = reinterpret_cast<uint32_t *>(o.p) + item * t_stride + off;
+    if ((off & 3) == 0) {
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        uint4 *d = reinterpret_cast<uint4 *>(b + q * o.plane_u32);
+        d[0] = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
+        d[1] = make_uint4(w[q][4], w[q][5], w[q][6], w[q][7]);
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < 3; ++q)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) b[q * o.plane_u32 + j] = w[q][j];
+    }
+  }
+}
+
+// Four consecutive complex outputs (v[0..7]) at offsets off .. off + 3 of one item.
+__device__ __forceinline__ void store_out4(const OutDesc &o, int64_t t_stride, int64_t item, int64_t off,
+                                           const float v[8]) {
+  if (o.fmt == 0) {
+    float2 *b = reinterpret_cast<float2 *>(o.p) + item * t_stride + off;
+    if ((off & 1) == 0) {
+      reinterpret_cast<float4 *>(b)[0] = make_float4(v[0], v[1], v[2], v[3]);
+      reinterpret_cast<float4 *>(b)[1] = make_float4(v[4], v[5], v[6], v[7]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = make_float2(v[2 * j], v[2 * j + 1]);
+    }
+  } else {
+    uint32_t w[3][4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      uint32_t t[3];
+      tn_split3(v[2 * j], v[2 * j + 1], t);
+      w[0][j] = t[0];
+      w[1][j] = t[1];
+      w[2][j] = t[2];
+    }
+    uint32_t *b = reinterpret_cast<uint32_t *>(o.p) + item * t_stride + off;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      if ((off & 3) == 0) {
+        *reinterpret_cast<uint4 *>(b + q * o.plane_u32) = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) b[q * o.plane_u32 + j] = w[q][j];
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void store_out4(const OutDesc &o, int64_t t_stride, int64_t item, int64_t off,
+                                           const double v[8]) {
+  double2 *b = reinterpret_cast<double2 *>(o.p) + item * t_stride + off;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) b[j] = make_double2(v[2 * j], v[2 * j + 1]);
+}
