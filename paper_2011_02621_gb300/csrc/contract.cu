@@ -300,6 +300,72 @@ step_stream_kernel(StepParams s, ContractArgs a, const typename C2T<R>::T *ket, 
   }
 }
 
+// The same streaming step with K and N fixed at compile time (small register footprint).
+template <typename R, int KK, int NN>
+__global__ void __launch_bounds__(256)
+step_stream_fixed(StepParams s, ContractArgs a, const typename C2T<R>::T *ket, const typename C2T<R>::T *bra,
+                  const typename C2T<R>::T *tin, OutDesc out, int64_t rows_per_cta) {
+  using V = typename C2T<R>::T;
+  __shared__ V Cs[KK * NN];
+  __shared__ int oc[NN];
+  const int tid = threadIdx.x;
+  const int64_t ctas_m = (s.M + rows_per_cta - 1) / rows_per_cta;
+  const int64_t item = blockIdx.x / ctas_m;
+  const int64_t m0 = (blockIdx.x % ctas_m) * rows_per_cta;
+  ItemCtx c = item_ctx(a, s, item);
+  if (tid < KK * NN) {
+    const V *kp = ket + s.ket_off + c.sa;
+    const V *bp = bra + c.b * a.bra_stride + s.bra_off + c.sb;
+    const int k = tid / NN, n = tid % NN;
+    Cs[tid] = overlap_elem(kp, bp, (int64_t)a.tab[s.t_bka + k] + a.tab[s.t_bna + n],
+                           (int64_t)a.tab[s.t_bkb + k] + a.tab[s.t_bnb + n], s.ket_sig, s.bra_sig);
+  }
+  if (tid < NN) oc[tid] = a.tab[s.t_ocol + tid];
+  __syncthreads();
+  const V *tp = tin + item * a.t_stride;
+  const int64_t m1 = m0 + rows_per_cta < s.M ? m0 + rows_per_cta : s.M;
+  const bool four = (NN == 4 && oc[3] - oc[0] == 3);
+  for (int64_t m = m0 + tid; m < m1; m += 256) {
+    V x[KK];
+#pragma unroll
+    for (int k = 0; k < KK; ++k) x[k] = tp[m * KK + k];
+    const int ro = orow_of(s, m);
+    R v[2 * NN];
+#pragma unroll
+    for (int n = 0; n < NN; ++n) {
+      V acc = cz<V>();
+#pragma unroll
+      for (int k = 0; k < KK; ++k) acc = cfma(x[k], Cs[k * NN + n], acc);
+      v[2 * n] = acc.x;
+      v[2 * n + 1] = acc.y;
+    }
+    if (NN == 4 && four) {
+      store_out4(out, a.t_stride, item, ro + oc[0], v);
+    } else {
+#pragma unroll
+      for (int n = 0; n < NN; ++n) {
+        V t;
+        t.x = v[2 * n];
+        t.y = v[2 * n + 1];
+        store_out(out, a.t_stride, item, ro + oc[n], t);
+      }
+    }
+  }
+}
+
+template <typename R, int KK, int NN>
+cudaError_t launch_stream_fixed(const StepParams &s, const ContractArgs &a, const void *ket, const void *bra,
+                                const void *t_in, const OutDesc &t_out, cudaStream_t st) {
+  using V = typename C2T<R>::T;
+  const int64_t rows = 1024;
+  const int64_t grid = ((s.M + rows - 1) / rows) * a.items;
+  if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  step_stream_fixed<R, KK, NN><<<(unsigned)grid, 256, 0, st>>>(s, a, (const V *)ket, (const V *)bra,
+                                                                (const V *)t_in, t_out, rows);
+  tn_count_launch(1);
+  return cudaGetLastError();
+}
+
 template <typename R>
 __global__ void slice_sum_kernel(const typename C2T<R>::T *res, int64_t stride, int64_t n_bits, int64_t n_slices,
                                  int accumulate, double2 *out) {
@@ -371,6 +437,13 @@ cudaError_t launch_step(const StepParams &s, const ContractArgs &a, const void *
                         const void *t_in, const OutDesc &t_out, cudaStream_t st) {
   using V = typename C2T<R>::T;
   if (a.items <= 0) return cudaSuccess;
+  if (s.M >= 512) {
+#define TN_FIXED(k, n) \
+  if (s.K == k && s.N == n) return launch_stream_fixed<R, k, n>(s, a, ket, bra, t_in, t_out, st);
+    TN_FIXED(4, 4) TN_FIXED(1, 4) TN_FIXED(4, 1) TN_FIXED(2, 2) TN_FIXED(2, 4) TN_FIXED(4, 2)
+    TN_FIXED(1, 2) TN_FIXED(2, 1) TN_FIXED(4, 16) TN_FIXED(16, 4) TN_FIXED(16, 1) TN_FIXED(1, 16)
+#undef TN_FIXED
+  }
   if (s.K <= 16 && s.N <= 16 && s.M >= 512) {
     const int64_t rows = 1024;
     const int64_t grid = ((s.M + rows - 1) / rows) * a.items;

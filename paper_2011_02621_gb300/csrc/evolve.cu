@@ -74,19 +74,28 @@ __host__ __device__ inline int C_of(const WorkLayout &L) { return L.C; }
 constexpr int GATE_THREADS = 128;
 constexpr int MAX_SWEEPS = 60;
 
-// One CTA per item: X_k = P A^k, X_l = Q A^l (Eqs. result1/result2), SVD of
-// the smaller-row endpoint by parallel one-sided (Hestenes) Jacobi, keep
-// s_j > cutoff*s_0 (at most dout, zero-padded to dout), A^sv <- U,
-// A^other <- X_other (S V)^T (Eqs. svd/svd2).
+// TPI threads per item (128: one item per CTA; 32: one warp per item, four items per CTA
+// for small matrices): X_k = P A^k, X_l = Q A^l (Eqs. result1/result2), SVD of the
+// smaller-row endpoint by parallel one-sided (Hestenes) Jacobi, keep s_j > cutoff*s_0 (at
+// most dout, zero-padded to dout), A^sv <- U, A^other <- X_other (S V)^T (Eqs. svd/svd2).
+template <int TPI>
+__device__ __forceinline__ void item_sync() {
+  if (TPI == 32) __syncwarp(); else __syncthreads();
+}
+
+template <int TPI>
 __global__ void __launch_bounds__(GATE_THREADS) gate_kernel(GateParams g, double2 *base, int64_t item_stride,
-                                                            double2 *gwork, int *errflag) {
+                                                            double2 *gwork, int *errflag, int items) {
   extern __shared__ double2 smem[];
-  const int item = blockIdx.x;
-  const int tid = threadIdx.x;
-  const int lane = tid & 31, warp = tid >> 5, nwarp = GATE_THREADS / 32;
+  constexpr int GPB = GATE_THREADS / TPI;         // items per block
+  const int grp = threadIdx.x / TPI;
+  const int item = blockIdx.x * GPB + grp;
+  const int tid = threadIdx.x % TPI;
+  const int lane = tid & 31, warp = tid >> 5, nwarp = TPI / 32;
+  if (TPI == 32 && item >= items) return;         // whole warps only: no block-wide barrier below
   double2 *A = base + (int64_t)item * item_stride;
-  double2 *work = g.use_smem ? smem : gwork + (int64_t)item * g.work_stride;
   const WorkLayout L = work_layout(g);
+  double2 *work = g.use_smem ? smem + (int64_t)grp * L.total : gwork + (int64_t)item * g.work_stride;
   double2 *Y = work + L.y, *Xo = work + L.xo, *W = work + L.w, *Vp = work + L.vp;
   double *sig = reinterpret_cast<double *>(work + L.sig);
   int *rank = reinterpret_cast<int *>(work + L.rank);
@@ -108,7 +117,7 @@ __global__ void __launch_bounds__(GATE_THREADS) gate_kernel(GateParams g, double
     const bool is_sv = (is_k == (g.sv_is_k != 0));
     const int64_t O = m / 2;
     const int64_t total = (int64_t)m * n;
-    for (int64_t idx = tid; idx < total; idx += GATE_THREADS) {
+    for (int64_t idx = tid; idx < total; idx += TPI) {
       int r = (int)(idx / n), c = (int)(idx % n);
       int sp = (int)(r / O);
       int64_t o = r % O;
@@ -125,31 +134,34 @@ __global__ void __launch_bounds__(GATE_THREADS) gate_kernel(GateParams g, double
     }
   }
   const int R = L.R, C = L.C;
-  for (int64_t idx = tid; idx < (int64_t)C * C; idx += GATE_THREADS) {
+  for (int64_t idx = tid; idx < (int64_t)C * C; idx += TPI) {
     int i = (int)(idx % C), j = (int)(idx / C);
     W[idx] = make_double2(i == j ? 1.0 : 0.0, 0.0);
   }
-  __syncthreads();
+  item_sync<TPI>();
 
   // ---- parallel one-sided Jacobi (round-robin pairing)
   // rotation threshold: |<y_p, y_q>| > tol * |y_p| |y_q| with tol = 2 sqrt(R) eps (the rounding
   // level of the column dot products), and pairs whose columns are negligible against the
   // whole matrix (|y_p| |y_q| <= 1e-30 ||Y||_F^2) are left alone.
-  __shared__ int s_rot;
-  __shared__ double s_fro;
-  __shared__ double s_part[GATE_THREADS / 32];
+  __shared__ int s_rot_a[GPB];
+  __shared__ double s_fro_a[GPB];
+  __shared__ double s_part_a[GPB][TPI / 32];
+  int &s_rot = s_rot_a[grp];
+  double &s_fro = s_fro_a[grp];
+  double *s_part = s_part_a[grp];
   {
     double f = 0;
-    for (int64_t idx = tid; idx < (int64_t)L.R * L.C; idx += GATE_THREADS) f = fma(Y[idx].x, Y[idx].x, fma(Y[idx].y, Y[idx].y, f));
+    for (int64_t idx = tid; idx < (int64_t)L.R * L.C; idx += TPI) f = fma(Y[idx].x, Y[idx].x, fma(Y[idx].y, Y[idx].y, f));
     for (int o = 16; o; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
     if (lane == 0) s_part[warp] = f;
-    __syncthreads();
+    item_sync<TPI>();
     if (tid == 0) {
       double t = 0;
-      for (int w = 0; w < GATE_THREADS / 32; ++w) t += s_part[w];
+      for (int w = 0; w < TPI / 32; ++w) t += s_part[w];
       s_fro = t;
     }
-    __syncthreads();
+    item_sync<TPI>();
   }
   const double tol = 2.0 * sqrt((double)L.R) * 2.220446049250313e-16;
   const double floor_ab = 1e-30 * s_fro;
@@ -158,7 +170,7 @@ __global__ void __launch_bounds__(GATE_THREADS) gate_kernel(GateParams g, double
   bool converged = (C <= 1);
   for (int sweep = 0; sweep < MAX_SWEEPS && !converged; ++sweep) {
     if (tid == 0) s_rot = 0;
-    __syncthreads();
+    item_sync<TPI>();
     for (int rd = 0; rd < rounds; ++rd) {
       for (int pi = warp; pi < Cp / 2; pi += nwarp) {
         int p, q;
@@ -200,10 +212,10 @@ __global__ void __launch_bounds__(GATE_THREADS) gate_kernel(GateParams g, double
         }
         if (lane == 0) s_rot = 1;
       }
-      __syncthreads();
+      item_sync<TPI>();
     }
     converged = (s_rot == 0);
-    __syncthreads();
+    item_sync<TPI>();
   }
   if (!converged && tid == 0) atomicOr(errflag, 1);
 
@@ -215,9 +227,11 @@ __global__ void __launch_bounds__(GATE_THREADS) gate_kernel(GateParams g, double
     for (int o = 16; o; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
     if (lane == 0) sig[j] = sqrt(s2);
   }
-  __syncthreads();
-  __shared__ double s_max;
-  __shared__ int s_keep;
+  item_sync<TPI>();
+  __shared__ double s_max_a[GPB];
+  __shared__ int s_keep_a[GPB];
+  double &s_max = s_max_a[grp];
+  int &s_keep = s_keep_a[grp];
   if (tid == 0) {
     double mx = 0;
     for (int j = 0; j < C; ++j) mx = fmax(mx, sig[j]);
@@ -226,23 +240,23 @@ __global__ void __launch_bounds__(GATE_THREADS) gate_kernel(GateParams g, double
     s_max = mx;
     s_keep = kc < g.dout ? kc : g.dout;
   }
-  for (int j = tid; j < C; j += GATE_THREADS) {
+  for (int j = tid; j < C; j += TPI) {
     int rk = 0;
     for (int i = 0; i < C; ++i) rk += (sig[i] > sig[j] || (sig[i] == sig[j] && i < j)) ? 1 : 0;
     rank[j] = rk;
     colof[rk] = j;
   }
-  __syncthreads();
+  item_sync<TPI>();
   const int keep = s_keep;
   const int dout = g.dout;
 
   // ---- V' = S V^H rows (dout x n), zero beyond keep
-  for (int64_t idx = tid; idx < (int64_t)dout * n; idx += GATE_THREADS) Vp[idx] = make_double2(0, 0);
-  __syncthreads();
+  for (int64_t idx = tid; idx < (int64_t)dout * n; idx += TPI) Vp[idx] = make_double2(0, 0);
+  item_sync<TPI>();
   for (int j = 0; j < C; ++j) {
     int t = rank[j];
     if (t >= keep) continue;
-    for (int c = tid; c < n; c += GATE_THREADS) {
+    for (int c = tid; c < n; c += TPI) {
       double2 v;
       if (!ytrans) { double2 w = W[(int64_t)j * C + c]; v = make_double2(sig[j] * w.x, -sig[j] * w.y); }
       else { v = cconj(Y[(int64_t)j * R + c]); }
@@ -259,7 +273,7 @@ __global__ void __launch_bounds__(GATE_THREADS) gate_kernel(GateParams g, double
     const int m = svk ? g.m_k : g.m_l;
     const int64_t O = m / 2;
     const int64_t total = (int64_t)m * dout;
-    for (int64_t idx = tid; idx < total; idx += GATE_THREADS) {
+    for (int64_t idx = tid; idx < total; idx += TPI) {
       int r = (int)(idx / dout), t = (int)(idx % dout);
       double2 u = make_double2(0, 0);
       if (t < keep) {
@@ -277,7 +291,7 @@ __global__ void __launch_bounds__(GATE_THREADS) gate_kernel(GateParams g, double
       An[sp * nv.sig + other_offset(nv, o) + (int64_t)t * nv.stride[nv.pos]] = u;
     }
   }
-  __syncthreads();
+  item_sync<TPI>();
 
   // ---- A^other <- X_other V'^T
   {
@@ -288,7 +302,7 @@ __global__ void __launch_bounds__(GATE_THREADS) gate_kernel(GateParams g, double
     const int m = svk ? g.m_l : g.m_k;
     const int64_t O = m / 2;
     const int64_t total = (int64_t)m * dout;
-    for (int64_t idx = tid; idx < total; idx += GATE_THREADS) {
+    for (int64_t idx = tid; idx < total; idx += TPI) {
       int r = (int)(idx / dout), t = (int)(idx % dout);
       double2 acc = make_double2(0, 0);
       const double2 *xr = Xo + (int64_t)r * n, *vt = Vp + (int64_t)t * n;
@@ -339,12 +353,24 @@ int64_t gate_work_elems(const GateParams &g) { return work_layout(g).total; }
 cudaError_t launch_gate(const GateParams &g, double2 *base, int64_t item_stride, int items, double2 *gwork,
                         int *errflag, cudaStream_t st) {
   if (items <= 0) return cudaSuccess;
-  size_t smem = g.use_smem ? (size_t)work_layout(g).total * sizeof(double2) : 0;
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(gate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+  const WorkLayout L = work_layout(g);
+  // small matrices: one warp per item, four items per CTA
+  const bool warp_per_item = g.use_smem && L.C <= 16 && L.R <= 256 && 4 * L.total * sizeof(double2) <= 96 * 1024;
+  if (warp_per_item) {
+    const size_t smem = 4 * (size_t)L.total * sizeof(double2);
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(gate_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    gate_kernel<32><<<(items + 3) / 4, GATE_THREADS, smem, st>>>(g, base, item_stride, gwork, errflag, items);
+  } else {
+    const size_t smem = g.use_smem ? (size_t)L.total * sizeof(double2) : 0;
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(gate_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    gate_kernel<128><<<items, GATE_THREADS, smem, st>>>(g, base, item_stride, gwork, errflag, items);
   }
-  gate_kernel<<<items, GATE_THREADS, smem, st>>>(g, base, item_stride, gwork, errflag);
   tn_count_launch(1);
   return cudaGetLastError();
 }
