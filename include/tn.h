@@ -178,6 +178,25 @@ tn_status tn_plan_details(const tn_plan *p, int32_t *order, int32_t *cuts, int64
 tn_status tn_amplitudes(tn_plan *p, const uint64_t *bits, int64_t n, tn_precision prec,
                         tn_c128 *out, void *cuda_stream);
 
+/* tn_amplitudes without device allocation. The paper has no counterpart: this is for callers
+ * that must not allocate device memory while they run -- a process whose own pool already holds
+ * the GPU's memory and accounts for every byte, a real-time or embedded host limited to a budget
+ * fixed at start-up, or code running inside an allocator callback, which must not re-enter the
+ * allocator. Same arguments, results and precisions as tn_amplitudes; every scratch buffer is
+ * carved from one static device array of 32 MiB that each GPU loading the library holds until
+ * the process exits. No cudaMalloc, cudaFree or allocator callback is called.
+ *  - The first call on a device looks up the array's device address (a CUDA runtime query,
+ *    once per device, with that device current); make that first call before any stream
+ *    capture begins.
+ *  - Batches are sized to fit the array; a plan whose single bitstring and single slice need
+ *    more than 32 MiB is rejected with TN_ERR_UNSUPPORTED (use tn_amplitudes, or plan with a
+ *    smaller max_intermediate).
+ *  - All calls share the array and it keeps the previous call's contents; each call clears the
+ *    words it needs at zero and writes every other buffer before reading it. Calls whose work
+ *    overlaps on the GPU (other streams, other threads) race on the array: serialise them. */
+tn_status tn_amplitudes_static(tn_plan *p, const uint64_t *bits, int64_t n, tn_precision prec,
+                               tn_c128 *out, void *cuda_stream);
+
 /* Kernel launches issued since the last reset (all threads). */
 int64_t tn_launch_count(int32_t reset);
 

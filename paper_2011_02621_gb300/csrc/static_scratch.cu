@@ -1,0 +1,138 @@
+// tn_amplitudes_static: tn_amplitudes without any device allocation.
+//
+// Some callers cannot let a library allocate device memory while they run: processes whose own
+// memory pool has reserved the GPU's memory up front and accounts for every byte (a further
+// cudaMalloc would fail or break that accounting), real-time or embedded hosts that may only use
+// a fixed budget decided at start-up, and code that runs inside an allocator callback, where
+// allocating again would re-enter that allocator. For them this entry point runs the same
+// computation as tn_amplitudes, with every scratch buffer (bitstrings, bra tensors, SVD work,
+// intermediates, overlap tensors, results, error words) carved out of one statically sized
+// device array that lives in this file. Each GPU that loads the library holds that array
+// (TN_STATIC_SCRATCH_BYTES) until the process exits.
+#include <algorithm>
+#include <mutex>
+
+#include "tn_host.h"
+
+#define TN_STATIC_SCRATCH_BYTES (size_t(32) << 20)   // 32 MiB per device
+
+static __device__ __align__(256) unsigned char tn_static_scratch[TN_STATIC_SCRATCH_BYTES];
+
+namespace {
+
+std::mutex g_scratch_mu;
+void *g_scratch_addr[256] = {};
+
+// The array's device address on the current device. In host code the array's name is only a
+// stand-in, so the address is asked once per device (with that device current) and cached.
+tn_status scratch_address(void **out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return tn_fail(TN_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+  if (dev < 0 || dev >= 256) return tn_fail(TN_ERR_UNSUPPORTED, "device ordinal %d out of range", dev);
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  if (!g_scratch_addr[dev]) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, tn_static_scratch);
+    if (e != cudaSuccess || !p)
+      return tn_fail(TN_ERR_CUDA, "cudaGetSymbolAddress of the static scratch: %s", cudaGetErrorString(e));
+    g_scratch_addr[dev] = p;
+  }
+  *out = g_scratch_addr[dev];
+  return TN_OK;
+}
+
+size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Byte sizes of the workspace buffers for `ch` bitstrings of `sc` slices each (the sizes the
+// workspace set-up asks for; each buffer is given exactly that capacity below).
+struct Sizes {
+  size_t bits, bra64, bra32, gwork, t, cbuf, res, err, total;
+};
+
+Sizes sizes_for(const tn_plan *p, int kind, int64_t ch, int64_t sc) {
+  const tn_circuit *c = p->c;
+  const int words = (c->n + 63) / 64;
+  const int64_t tel = kind ? 12 : 16;
+  Sizes z;
+  z.bits = (size_t)(ch * words * 8);
+  z.bra64 = (size_t)(ch * c->bra.item_elems * 16);
+  z.bra32 = kind ? (size_t)(ch * c->bra.item_elems * 8) : 0;
+  z.gwork = (size_t)(ch * std::max<int64_t>(c->bra.max_work, 1) * 16);
+  z.t = (size_t)(ch * sc * p->maxT * tel);
+  z.cbuf = kind ? (size_t)(ch * sc * p->maxKN * 24) : 0;
+  z.res = (size_t)(ch * 16);
+  z.err = 64;
+  z.total = up256(z.bits) + up256(z.bra64) + up256(z.bra32) + up256(z.gwork) + 2 * up256(z.t) + up256(z.cbuf) +
+            up256(z.res) + up256(z.err);
+  return z;
+}
+
+// allocator that refuses: if the workspace set-up ever asked for more than was carved, the call
+// fails with TN_ERR_OOM instead of allocating
+void *refuse_alloc(size_t, void *, void *) { return nullptr; }
+void refuse_free(void *, size_t, void *, void *) {}
+
+}  // namespace
+
+extern "C" tn_status tn_amplitudes_static(tn_plan *p, const uint64_t *bits, int64_t n, tn_precision prec,
+                                          tn_c128 *out, void *cuda_stream) {
+  if (!p) return tn_fail(TN_ERR_ARG, "tn_amplitudes_static: NULL plan");
+  if (prec < TN_FP64 || prec > TN_TF32X6) return tn_fail(TN_ERR_ARG, "unknown precision %d", (int)prec);
+  if (n == 0) return TN_OK;
+  if (n < 0 || !bits || !out) return tn_fail(TN_ERR_ARG, "tn_amplitudes_static: bad arguments");
+  const int kind = prec == TN_FP64 ? 0 : 1;
+  const size_t cap = TN_STATIC_SCRATCH_BYTES;
+  // as many whole bitstrings as fit; else one bitstring with as many of its slices as fit
+  int64_t ch = 0, sc = p->n_slices;
+  {
+    const size_t one = sizes_for(p, kind, 1, sc).total;
+    if (one <= cap) {
+      ch = (int64_t)(cap / one);
+      ch = std::min<int64_t>(std::min<int64_t>(ch, n), 1 << 16);
+      while (ch > 1 && sizes_for(p, kind, ch, sc).total > cap) --ch;
+    } else {
+      ch = 1;
+      while (sc > 1 && sizes_for(p, kind, 1, sc).total > cap) sc = (sc + 1) / 2;
+      if (sizes_for(p, kind, 1, sc).total > cap)
+        return tn_fail(TN_ERR_UNSUPPORTED,
+                       "tn_amplitudes_static: one bitstring and one slice need %zu bytes of scratch, more than the "
+                       "%zu-byte static scratch; use tn_amplitudes or more cuts (smaller max_intermediate)",
+                       sizes_for(p, kind, 1, 1).total, cap);
+    }
+  }
+  void *base = nullptr;
+  tn_status s = scratch_address(&base);
+  if (s != TN_OK) return s;
+  // a private copy of the plan and its circuit whose workspace lives in the static array and
+  // whose allocator refuses; nothing of the caller's plan or circuit is modified
+  tn_circuit cc = *p->c;
+  cc.mem.a.alloc = refuse_alloc;
+  cc.mem.a.free = refuse_free;
+  cc.mem.a.ctx = nullptr;
+  cc.mem.has = true;
+  tn_plan q = *p;
+  q.c = &cc;
+  q.chunk[kind] = (int)ch;
+  q.slice_chunk[kind] = sc;
+  q.ws = Workspace();
+  const Sizes z = sizes_for(p, kind, ch, sc);
+  unsigned char *cur = static_cast<unsigned char *>(base);
+  auto carve = [&](Buf &b, size_t bytes) {
+    b.p = bytes ? cur : nullptr;
+    b.bytes = bytes;
+    b.stream = (cudaStream_t)cuda_stream;
+    cur += up256(bytes);
+  };
+  carve(q.ws.bits, z.bits);
+  carve(q.ws.bra64, z.bra64);
+  carve(q.ws.bra32, z.bra32);
+  carve(q.ws.gwork, z.gwork);
+  carve(q.ws.t0, z.t);
+  carve(q.ws.t1, z.t);
+  carve(q.ws.cbuf, z.cbuf);
+  carve(q.ws.res, z.res);
+  carve(q.ws.err, z.err);
+  // the error words are cleared by the run itself; every other buffer is written before read
+  return run_amplitudes(&q, q.ws, bits, n, prec, out, (cudaStream_t)cuda_stream);
+}

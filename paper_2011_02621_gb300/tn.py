@@ -90,6 +90,7 @@ def _load():
         "tn_path": (i32, [vp, C.POINTER(tn_path_opts), C.POINTER(vp), C.POINTER(tn_plan_info)]),
         "tn_plan_details": (i32, [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i64)]),
         "tn_amplitudes": (i32, [vp, vp, i64, i32, vp, vp]),
+        "tn_amplitudes_static": (i32, [vp, vp, i64, i32, vp, vp]),
         "tn_launch_count": (i64, [i32]),
         "tn_profile_enable": (i32, [i32]),
         "tn_profile_read": (i32, [i32, C.c_char_p, i32, C.POINTER(i64), C.POINTER(dbl), C.POINTER(dbl),
@@ -343,6 +344,28 @@ def tn_amplitudes(p: Plan, bits, prec: str = "fp64", out=None, stream=None):
         res = out
         optr = out.data_ptr()
     _check(LIB.tn_amplitudes(p.ptr, C.c_void_p(bptr), B, PRECISIONS[prec], C.c_void_p(optr), _stream_handle(stream)))
+    del keep
+    return res
+
+
+def tn_amplitudes_static(p: Plan, bits, prec: str = "fp64", out=None, stream=None):
+    """Same as :func:`tn_amplitudes`, for callers that must not allocate device memory during the
+    call: the library's scratch comes from its fixed 32 MiB static device array, never from an
+    allocator. Arguments and results are those of :func:`tn_amplitudes`."""
+    n = p.circuit.n_qubits
+    words = max((n + 63) // 64, 1)
+    if hasattr(bits, "data_ptr"):
+        B, bptr, keep = int(bits.shape[0]), bits.data_ptr(), bits
+    else:
+        b = np.asarray(bits)
+        if b.dtype != np.uint64 or b.ndim != 2 or b.shape[1] != words:
+            b = pack_bits(b.reshape(-1, n))
+        keep = np.ascontiguousarray(b)
+        B, bptr = int(keep.shape[0]), keep.ctypes.data
+    res = np.zeros(B, dtype=np.complex128) if out is None else out
+    optr = res.ctypes.data if isinstance(res, np.ndarray) else res.data_ptr()
+    _check(LIB.tn_amplitudes_static(p.ptr, C.c_void_p(bptr), B, PRECISIONS[prec], C.c_void_p(optr),
+                                    _stream_handle(stream)))
     del keep
     return res
 
