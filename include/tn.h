@@ -255,8 +255,11 @@ typedef struct {
   double peak_admitted_bytes;
 } tn_server_stats;
 
-/* Create a server; its worker threads run tn_amplitudes-equivalent work for
- * admitted requests on their own streams. Errors: TN_ERR_ARG, TN_ERR_CUDA. */
+/* Create a server; its worker threads (min(max_inflight, n_streams) of them), each with its
+ * own stream and workspaces, take the oldest request whose device memory fits the budget next
+ * to the batches in flight, merge into it the queued requests of the same plan and precision
+ * (continuous batching, up to the plan's batch size), and run them as one device batch of the
+ * tn_amplitudes path. Free the server before the plans it served. Errors: TN_ERR_ARG, TN_ERR_CUDA. */
 tn_status tn_server_create(const tn_server_cfg *cfg, tn_server **out);
 
 /* Queue a request (the bits are copied; out must stay valid until the ticket

@@ -412,9 +412,12 @@ def tn_cut_search(n_qubits: int, edges, dims, **opts):
 # serving loop
 # --------------------------------------------------------------------------
 class Server:
+    """Owns a tn_server*; keeps every plan it served alive until it is freed."""
+
     def __init__(self, ptr):
         self.ptr = ptr
         self._pending = {}
+        self._plans = []
 
     def __del__(self):
         if getattr(self, "ptr", None):
@@ -442,6 +445,8 @@ def tn_server_submit(s: Server, p: Plan, bits, prec: str = "fp64", out=None) -> 
     _check(LIB.tn_server_submit(s.ptr, p.ptr, C.c_void_p(b.ctypes.data), int(b.shape[0]), PRECISIONS[prec],
                                 C.c_void_p(optr), C.byref(t)))
     s._pending[int(t.value)] = (res, p)
+    if not any(q is p for q in s._plans):
+        s._plans.append(p)
     return int(t.value)
 
 
@@ -452,6 +457,12 @@ def tn_server_wait(s: Server, ticket: int, timeout_ms: int = -1):
     res, _ = s._pending.pop(ticket)
     _check(st)
     return res
+
+
+def tn_server_free(s: Server):
+    if s.ptr:
+        LIB.tn_server_free(s.ptr)
+        s.ptr = None
 
 
 def tn_server_stats_get(s: Server) -> dict:
