@@ -14,9 +14,16 @@ Conventions (readings where the paper is silent):
   the high bit. After the gate the auxiliary index of the shared edge becomes
   the pair (a, s) with combined index a * chi_o + s on both endpoints
   (Eqs. result1/result2).
-* Compression SVDs the endpoint whose row dimension 2 * prod(other legs) is
-  smaller (ties: q[0]); keeps singular values > cutoff * s_0, at most chi
-  (chi = 0: no cap), and never renormalises (Eqs. svd/svd2).
+* Compression SVDs one endpoint (Eqs. svd/svd2 leave the choice open: "say
+  A^k"). The endpoint is fixed by the circuit structure alone, never by the
+  data: in the structural shapes (every bond starts at 1; a gate with chi_o
+  terms multiplies its bond by chi_o; the compression bounds it by the row
+  count of the SVD'd matrix and by chi) it is the endpoint whose matrix has
+  fewer rows 2 * prod(other legs), ties to q[0]. With truncation, which
+  endpoint is compressed changes the result, so a data-independent rule is
+  what makes the result well defined for every bitstring. The compression keeps
+  singular values > cutoff * s_0, at most chi (chi = 0: no cap), and never
+  renormalises.
 * The bra half starts from the product vector |s> and applies the transposes
   of the second group of gates from the last one back to the first; the
   amplitude is then sum_sigma psi_bar[sigma] phi[sigma] with no complex
@@ -99,7 +106,8 @@ class TNS:
         shape[pos] *= P.shape[2]
         return out.reshape(shape)
 
-    def apply_2q(self, q0: int, q1: int, m: np.ndarray, chi: int = 0, cutoff: float = 1e-12) -> None:
+    def apply_2q(self, q0: int, q1: int, m: np.ndarray, chi: int = 0, cutoff: float = 1e-12,
+                 svd_node: Optional[int] = None) -> None:
         k, l = q0, q1
         e = self.edge_id.get(tuple(sorted((k, l))))
         if e is None:
@@ -112,7 +120,7 @@ class TNS:
         # Eqs. svd / svd2: SVD one endpoint, absorb S V into the other
         rows_k = Ak.size // Ak.shape[pk]
         rows_l = Al.size // Al.shape[pl]
-        if rows_k <= rows_l:
+        if (rows_k <= rows_l) if svd_node is None else (svd_node == k):
             Asv, psv, Aot, pot, sv = Ak, pk, Al, pl, k
         else:
             Asv, psv, Aot, pot, sv = Al, pl, Ak, pk, l
@@ -133,12 +141,44 @@ class TNS:
             self.A[k], self.A[l] = Aot, Asv
         self.log.append(dict(edge=e, svd_node=sv, m=X.shape[0], n=X.shape[1], s=S, keep=keep))
 
-    def apply(self, gate, chi: int = 0, cutoff: float = 1e-12, transpose: bool = False) -> None:
+    def apply(self, gate, chi: int = 0, cutoff: float = 1e-12, transpose: bool = False,
+              svd_node: Optional[int] = None) -> None:
         m = gate.m.T if transpose else gate.m
         if len(gate.qubits) == 1:
             self.apply_1q(gate.qubits[0], m)
         else:
-            self.apply_2q(gate.qubits[0], gate.qubits[1], m, chi, cutoff)
+            self.apply_2q(gate.qubits[0], gate.qubits[1], m, chi, cutoff, svd_node)
+
+
+def structural_svd_nodes(n, edges, gates, chi=0, return_dims: bool = False):
+    """The endpoint each two-qubit gate of ``gates`` (in application order) compresses: the one
+    whose matrix has fewer rows 2 * prod(other legs) in the structural shapes, ties to the gate's
+    first qubit. Structural shapes: bonds start at 1; a gate multiplies its bond by its chi_o
+    (Eq. gatesplit); the compression bounds it by the rows of the compressed matrix and by chi
+    (Eqs. svd, shouwei). Independent of the state."""
+    es = [tuple(sorted(e)) for e in edges]
+    eid = {e: i for i, e in enumerate(es)}
+    legs: List[List[int]] = [[] for _ in range(n)]
+    for i, (u, v) in enumerate(es):
+        legs[u].append(i)
+        legs[v].append(i)
+    d = [1] * len(es)
+    out = []
+    for g in gates:
+        if len(g.qubits) == 1:
+            continue
+        k, l = g.qubits
+        e = eid[tuple(sorted((k, l)))]
+        chi_o = gate_split(g.m)[2]
+        rows_k = 2 * math.prod(d[f] for f in legs[k] if f != e)
+        rows_l = 2 * math.prod(d[f] for f in legs[l] if f != e)
+        node, rows = (k, rows_k) if rows_k <= rows_l else (l, rows_l)
+        nd = min(d[e] * chi_o, rows)
+        if chi and chi > 0:
+            nd = min(nd, chi)
+        d[e] = nd
+        out.append(node)
+    return (out, d) if return_dims else out
 
 
 # --------------------------------------------------------------------------
@@ -150,20 +190,21 @@ def split_gates(gates, split_cycle: int):
     return g1, g2
 
 
+def _evolve(t: TNS, seq, chi, cutoff, transpose) -> TNS:
+    nodes = iter(structural_svd_nodes(t.n, t.edges, seq, chi))
+    for g in seq:
+        t.apply(g, chi, cutoff, transpose=transpose, svd_node=None if len(g.qubits) == 1 else next(nodes))
+    return t
+
+
 def evolve_ket(n, edges, gates1, chi=0, cutoff=1e-12) -> TNS:
     """|phi> = (group 1) |0...0>."""
-    t = TNS(n, edges)
-    for g in gates1:
-        t.apply(g, chi, cutoff)
-    return t
+    return _evolve(TNS(n, edges), list(gates1), chi, cutoff, False)
 
 
 def evolve_bra(n, edges, gates2, bits, chi=0, cutoff=1e-12) -> TNS:
     """Coefficients of <psi| = <s| (group 2): the transposed gates, last to first, on |s>."""
-    t = TNS(n, edges, bits)
-    for g in reversed(list(gates2)):
-        t.apply(g, chi, cutoff, transpose=True)
-    return t
+    return _evolve(TNS(n, edges, bits), list(reversed(list(gates2))), chi, cutoff, True)
 
 
 # --------------------------------------------------------------------------
@@ -223,16 +264,24 @@ def contract_network(tensors: List[np.ndarray], labels: List[List[int]]) -> comp
     return complex(ts[0].reshape(()) if ts[0].ndim == 0 else ts[0].sum())
 
 
-def overlap_amplitude(ket: TNS, bra: TNS, cuts: Sequence[int] = ()) -> complex:
-    """<psi|phi> by Eq. overlap; with ``cuts`` the sum over all slices of the cut edges."""
+def overlap_amplitude(ket: TNS, bra: TNS, cuts: Sequence[int] = (), slices=None) -> complex:
+    """<psi|phi> by Eq. overlap; with ``cuts`` the sum over all slices of the cut edges.
+
+    ``slices``: if given, only the slices with these indices enter the sum (index = position in
+    the enumeration of the cut edges' values, first cut edge most significant; with no cuts the
+    one slice is index 0)."""
     C = [overlap_node(ket.A[q], bra.A[q]) for q in range(ket.n)]
     labels = [list(ket.legs[q]) for q in range(ket.n)]
     cuts = list(cuts)
     if not cuts:
+        if slices is not None and 0 not in slices:
+            return 0j
         return contract_network(C, labels)
     dims = [C[ket.edges[e][0]].shape[labels[ket.edges[e][0]].index(e)] for e in cuts]
     total = 0j
-    for vals in itertools.product(*[range(d) for d in dims]):
+    for k, vals in enumerate(itertools.product(*[range(d) for d in dims])):
+        if slices is not None and k not in slices:
+            continue
         sub, sl = [], []
         for q in range(ket.n):
             t, lab = C[q], labels[q]
@@ -264,13 +313,14 @@ def to_dense(t: TNS) -> np.ndarray:
     return np.transpose(out, [lab.index(("p", q)) for q in range(t.n)])
 
 
-def amplitudes(n, edges, gates, bits_batch, split_cycle, chi=0, cutoff=1e-12, cuts=(), ket=None):
-    """The full method for each row of ``bits_batch``; returns (amplitudes, ket)."""
+def amplitudes(n, edges, gates, bits_batch, split_cycle, chi=0, cutoff=1e-12, cuts=(), ket=None, slices=None):
+    """The full method for each row of ``bits_batch``; returns (amplitudes, ket). ``slices``: only
+    these slices of the cut network enter each sum (see overlap_amplitude)."""
     g1, g2 = split_gates(gates, split_cycle)
     if ket is None:
         ket = evolve_ket(n, edges, g1, chi, cutoff)
     out = np.empty(len(bits_batch), dtype=np.complex128)
     for i, bits in enumerate(bits_batch):
         bra = evolve_bra(n, edges, g2, bits, chi, cutoff)
-        out[i] = overlap_amplitude(ket, bra, cuts)
+        out[i] = overlap_amplitude(ket, bra, cuts, slices)
     return out, ket

@@ -213,6 +213,49 @@ def test_bond_bounds_every_compression():
         assert rec["keep"] <= rec["n"]
 
 
+def test_structural_endpoints_by_hand_and_as_bounds():
+    """The structural recursion that fixes which endpoint each compression SVDs (the endpoint with
+    fewer rows 2 prod(other legs), ties to q[0]; bond <- min(dim chi_o, those rows, chi)), worked
+    by hand on the chain 0-1-2 with fSim on (0,1), (1,2), (0,1), (1,2):
+    (0,1): rows 2 vs 2, tie -> 0, bond min(4, 2) = 2;  (1,2): rows 4 vs 2 -> 2, bond min(4, 2) = 2;
+    (0,1): rows 2 vs 4 -> 0, bond min(8, 2) = 2;       (1,2): rows 4 vs 2 -> 2, bond min(8, 2) = 2.
+    A gate written (1,0) ties to its first qubit, 1. With chi = 1 every bond stays 1, so (1,2) sees
+    rows 2 vs 2 and ties to 1: endpoints 0, 1, 0, 1. The recursion bounds every bond the evolution
+    reaches, and the oracle compresses the endpoints it names."""
+    from gen import Gate
+    f = gen.fsim(np.pi / 2, np.pi / 6)
+    chain = [(0, 1), (1, 2)]
+    seq = [Gate(1, (0, 1), f), Gate(1, (1, 2), f), Gate(2, (0, 1), f), Gate(2, (1, 2), f)]
+    assert tns.structural_svd_nodes(3, chain, seq, return_dims=True) == ([0, 2, 0, 2], [2, 2])
+    assert tns.structural_svd_nodes(3, chain, [Gate(1, (1, 0), f)]) == [1]
+    assert tns.structural_svd_nodes(3, chain, seq, chi=1, return_dims=True) == ([0, 1, 0, 1], [1, 1])
+    g = gen.grid(3, 4)
+    gates = gen.rqc(g, 6, gen.rng(41, 1), twoq="haar", oneq="haar")
+    nodes, dims = tns.structural_svd_nodes(g.n, g.edges, gates, return_dims=True)
+    ket = tns.evolve_ket(g.n, g.edges, gates)
+    assert all(b <= d for b, d in zip(ket.bonds(), dims))
+    assert [rec["svd_node"] for rec in ket.log] == nodes
+
+
+def test_capped_fsim_compressions_meet_degenerate_spectra():
+    """fSim(pi/2, phi) has a flat operator-Schmidt spectrum, so after a compression the SVD'd
+    endpoint stays an isometry: later compressions of it see equal singular values, and a chi cap
+    below them keeps an arbitrary half of a degenerate subspace. Truncated amplitudes of such
+    circuits are therefore not unique (any SVD routine may pick another half); exact comparisons
+    need untruncated runs or cuts inside a gap."""
+    w = gen.regular3_family(count=32, n_bits=1)[7]
+    g1, _ = tns.split_gates(w.gates, w.split)
+    ket = tns.evolve_ket(w.graph.n, w.graph.edges, g1, chi=2)
+    degenerate = [rec for rec in ket.log
+                  if rec["keep"] < len(rec["s"]) and rec["s"][rec["keep"]] > 1e-12 * rec["s"][0]
+                  and rec["s"][rec["keep"] - 1] / rec["s"][rec["keep"]] < 1 + 1e-9]
+    assert len(degenerate) > 0
+    _, _, chi_o = tns.gate_split(gen.fsim(np.pi / 2, np.pi / 6))
+    s = np.linalg.svd(gen.fsim(np.pi / 2, np.pi / 6).reshape(2, 2, 2, 2).transpose(0, 2, 1, 3).reshape(4, 4),
+                      compute_uv=False)
+    assert chi_o == 4 and np.allclose(s, s[0])
+
+
 def test_graph_state_closed_form_at_scale():
     """H on every qubit, then CZ on every edge: a(s) = 2^{-n/2} (-1)^{sum_edges s_i s_j}, at 53 and 104 qubits."""
     for g in (gen.staggered(6, 9, remove_seed=gen.BASE_SEED + 3), gen.staggered(8, 13)):
