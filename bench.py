@@ -202,6 +202,148 @@ def source_sha():
     return h.hexdigest()[:16]
 
 
+# ---------------------------------------------------------------------------
+# serving: a seeded Poisson request stream over three circuit classes
+# ---------------------------------------------------------------------------
+SERVE_CLASSES = (("syc104", 4096), ("syc53", 65536), ("grid20", 16))   # (workload, size cap)
+
+
+def batch_run(tn, np, torch, prec, steps, warmup, flush):
+    """32 circuits on random 3-regular graphs (24..40 qubits, 12 cycles, largest chi with no cut at
+    2^24 elements), 1024 bitstrings each, as one graph launch; beside it the same work as 32
+    sequential tn_amplitudes calls, and end to end with host copies."""
+    import gen
+    fam = gen.regular3_family(count=32, n_bits=1024)
+    stream = torch.cuda.current_stream()
+    plans, chis, cmacs = [], [], 0.0
+    for w in fam:
+        c, p, chi = tn.tn_build_largest_chi(w.graph.n, w.graph.edges, w.gates, w.split)
+        tn.tn_autotune(p, prec, len(w.bits), stream=stream)
+        plans.append(p)
+        chis.append(chi)
+        cmacs += p.info["cmacs"] * len(w.bits)
+    bits = [w.bits for w in fam]
+    b = tn.tn_batch_create(plans, bits, prec, stream=stream)
+    b64 = tn.tn_batch_create(plans, bits, "fp64", stream=stream)
+    total = b.total
+
+    def timed(fn):
+        for _ in range(warmup):
+            fn()
+        t = 0.0
+        for _ in range(steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t += e0.elapsed_time(e1) / 1000.0
+        return t / steps
+
+    t_graph = timed(lambda: tn.tn_batch_run(b, stream=stream))
+    a_tc = tn.tn_batch_read(b, stream=stream)
+    tn.tn_batch_run(b64, stream=stream)
+    a64 = tn.tn_batch_read(b64, stream=stream)
+    ok = 0
+    for g, r in zip(b.split(a_tc), b64.split(a64)):
+        ok += int(np.sum(np.abs(g - r) / np.sqrt(np.mean(np.abs(r) ** 2)) <= TOL))
+    dev_bits = [torch.from_numpy(tn.pack_bits(x).view(np.int64).copy()).cuda() for x in bits]
+    dev_out = [torch.empty(len(x), dtype=torch.complex128, device="cuda") for x in bits]
+
+    def sequential():
+        for p, x, o in zip(plans, dev_bits, dev_out):
+            tn.tn_amplitudes(p, x, prec, out=o, stream=stream)
+
+    t_seq = timed(sequential)
+    flat, _ = tn._packed_concat(plans, bits)
+    pin_bits = torch.from_numpy(flat.view(np.int64).copy()).pin_memory()
+    pin_out = torch.empty(total, dtype=torch.complex128).pin_memory()
+
+    def e2e():
+        tn.tn_batch_set_bits(b, pin_bits, stream=stream)
+        tn.tn_batch_run(b, stream=stream)
+        tn.tn_batch_read(b, out=pin_out, stream=stream)
+
+    t_e2e = timed(e2e)
+    info = tn.tn_batch_info(b)
+    frac = ok / total
+    res = {"workload": "32 circuits on seeded random 3-regular graphs, 24-40 qubits, 12 cycles "
+                       "(Haar SU(2) + fSim(pi/2, pi/6) per edge colour), 1024 bitstrings each",
+           "precision": prec, "amplitudes": total, "value": total / t_graph * frac, "unit": UNIT,
+           "ms_per_launch": 1000 * t_graph, "graph_kernels": info["graph_kernels"],
+           "device_bytes": info["device_bytes"], "within_1e-5_of_fp64": frac,
+           "chi_per_circuit": chis, "contraction_tflops": 8 * cmacs / t_graph / 1e12,
+           "sequential_calls": {"value": total / t_seq * frac, "ms": 1000 * t_seq},
+           "e2e": {"value": total / t_e2e * frac, "unit": UNIT, "h2d_bytes_per_step": int(flat.nbytes),
+                   "d2h_bytes_per_step": int(total * 16)}}
+    tn.tn_batch_free(b)
+    tn.tn_batch_free(b64)
+    return res
+
+
+def serving_run(tn, np, prec, seconds, load=0.8, seed=2011_02621 + 5, plans=None):
+    """Replay a Poisson stream of amplitude requests against tn_server_* at `load` times the form's
+    measured capacity; sizes log-uniform in [1, cap] per class, classes in equal proportion."""
+    import gen
+    import time as _t
+    if plans is None:
+        plans = {}
+        for name, cap in SERVE_CLASSES:
+            w = gen.workload(name, n_bits=1)
+            c = tn.tn_build(w.graph.n, w.graph.edges, w.gates)
+            tn.tn_evolve_two_sided(c, w.split, w.chi, w.cutoff)
+            opts = {"max_intermediate": 1 << 22} if name == "grid20" else {}
+            plans[name] = (tn.tn_path(c, mem_budget_bytes=4.0 * 2 ** 30, **opts), w.graph.n, cap)
+    # capacity (amplitudes/s) per class in this form, from one batch each
+    capacity = {}
+    for name, (p, nq, cap) in plans.items():
+        nb = max(4, min(cap, 1024 if name != "grid20" else 8))
+        bits = gen.bitstrings(nq, nb, gen.rng(seed, 9))
+        tn.tn_amplitudes(p, bits, prec)
+        t0 = _t.perf_counter()
+        tn.tn_amplitudes(p, bits, prec)
+        capacity[name] = nb / (_t.perf_counter() - t0)
+    rng = np.random.default_rng(seed)
+    names = [n for n, _ in SERVE_CLASSES]
+    # expected service seconds per request, mixed over classes; arrival rate for the target load
+    mean_size = {n: (cap - 1) / np.log(cap) if cap > 1 else 1.0 for n, cap in SERVE_CLASSES}
+    e_service = np.mean([mean_size[n] / capacity[n] for n in names])
+    lam = load / e_service
+    arrivals, t = [], 0.0
+    while True:
+        t += rng.exponential(1.0 / lam)
+        if t > seconds:
+            break
+        name = names[int(rng.integers(len(names)))]
+        cap = dict(SERVE_CLASSES)[name]
+        size = int(np.clip(np.exp(rng.uniform(0, np.log(cap))), 1, cap))
+        arrivals.append((t, name, size))
+    srv = tn.tn_server_create(hbm_budget_bytes=48.0 * 2 ** 30, max_inflight=4)
+    tickets = []
+    start = _t.perf_counter()
+    for (ta, name, size) in arrivals:
+        now = _t.perf_counter() - start
+        if ta > now:
+            _t.sleep(ta - now)
+        p, nq, _ = plans[name]
+        bits = gen.bitstrings(nq, size, gen.rng(seed + len(tickets), 2))
+        tickets.append((name, size, tn.tn_server_submit(srv, p, bits, prec)))
+    for name, size, tk in tickets:
+        tn.tn_server_wait(srv, tk)
+    wall = _t.perf_counter() - start
+    st = tn.tn_server_stats_get(srv)
+    tn.tn_server_free(srv)
+    return plans, {"precision": prec, "requests": len(tickets), "offered_load": load,
+                   "arrival_rate_per_s": lam, "seconds": seconds,
+                   "amplitudes": st["amplitudes"], "amplitudes_per_s": st["amplitudes"] / wall,
+                   "p50_latency_s": st["p50_latency_s"], "p99_latency_s": st["p99_latency_s"],
+                   "max_inflight_seen": st["max_inflight_seen"],
+                   "capacity_amplitudes_per_s": {k: round(v, 1) for k, v in capacity.items()},
+                   "size_caps": dict(SERVE_CLASSES)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -216,6 +358,11 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=64, help="reference arm: oracle bitstrings per step")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--profile-only", action="store_true", help="short run for ncu captures")
+    ap.add_argument("--serve-seconds", type=float, default=10.0, help="serving stream length (0: skip)")
+    ap.add_argument("--serve", action="store_true", help="serving comparison only: BF16x6 vs FP64 (one line)")
+    ap.add_argument("--no-tune", action="store_true", help="keep the shape heuristic's step kernels")
+    ap.add_argument("--mem-gib", type=float, default=32.0, help="device memory budget of the plan's batches")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 32-circuit batched-graph measurement")
     args = ap.parse_args()
     rank, world, local = env_int("RANK", 0), env_int("WORLD_SIZE", 1), env_int("LOCAL_RANK", 0)
     if args.impl == "reference":
@@ -237,15 +384,24 @@ def main():
         dist.barrier()
     from paper_2011_02621_gb300 import tn
 
+    if args.serve:
+        if rank == 0:
+            plans, a = serving_run(tn, np, "bf16x6", max(args.serve_seconds, 1.0))
+            _, b = serving_run(tn, np, "fp64", max(args.serve_seconds, 1.0), plans=plans)
+            print(json.dumps({"metric": "serving p50/p99 latency and amplitudes/s, 104q d8 / 53q d10 / 20q d14 mix",
+                              "unit": "s", "n_gpus": 1, "data": "synthetic", "tensor_core": a, "fp64": b}))
+        return 0
+
     w = gen.workload("syc53", n_bits=args.bits)
     bits_np = _rank_bits(w, rank)                 # weak scaling: each rank its own bitstrings
     B = len(bits_np)
     packed = tn.pack_bits(bits_np)
     c = tn.tn_build(w.graph.n, w.graph.edges, w.gates)
     tn.tn_evolve_two_sided(c, w.split, w.chi, w.cutoff)
-    plan = tn.tn_path(c, mem_budget_bytes=32.0 * 2 ** 30)
+    plan = tn.tn_path(c, mem_budget_bytes=args.mem_gib * 2 ** 30)
     info = plan.info
     stream = torch.cuda.current_stream()
+    tuned = None if args.no_tune else tn.tn_autotune(plan, args.prec, B, stream=stream)
     bits_dev = torch.from_numpy(packed.view(np.int64).copy()).cuda()
     out_dev = torch.empty(B, dtype=torch.complex128, device="cuda")
     bits_pin = torch.from_numpy(packed.view(np.int64).copy()).pin_memory()
@@ -275,8 +431,12 @@ def main():
         step(bits_dev, out_dev)
     torch.cuda.synchronize()
     if args.profile_only:
+        # one step inside a profiler range (ncu --profile-from-start off captures just this step)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
         step(bits_dev, out_dev)
         torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
         if rank == 0:
             print(json.dumps({"profile_only": True, "info": info}))
         return 0
@@ -369,6 +529,15 @@ def main():
                 "d2h_bytes_per_step": int(B * 16)},
         "clocks": clk,
     }
+    if tuned is not None:
+        line["config"]["step_kernels"] = {k: tuned.count(k) for k in sorted(set(tuned))}
+    if not args.no_batch and world == 1:
+        del plan                       # its workspace goes back to the allocator first
+        torch.cuda.synchronize()
+        line["batch"] = batch_run(tn, np, torch, args.prec, args.steps, args.warmup, flush)
+    if args.serve_seconds > 0 and world == 1:
+        _, sv = serving_run(tn, np, args.prec, args.serve_seconds)
+        line["serving"] = sv
     if not args.no_cpu and world == 1:
         cs = min(args.cpu_sample, B)
         r = cpu_oracle("syc53", args.bits, cs)

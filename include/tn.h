@@ -114,12 +114,14 @@ typedef struct {
   int64_t max_intermediate; /* automatic cuts keep every intermediate <= this many elements
                                per (bitstring, slice); 0 = 2^24 */
   double mem_budget_bytes;  /* workspace budget of tn_amplitudes; 0 = 8 GiB */
+  int32_t no_merge;         /* 1 = one network node per qubit; 0 = merge boundary nodes of degree
+                               <= 2 into a neighbour first (exact; see tn_path) */
 } tn_path_opts;
 
 /* Summary of a plan. All counts are per amplitude unless stated. */
 typedef struct {
   int32_t n_qubits;
-  int32_t n_steps;            /* pairwise contraction steps (n_qubits - 1) */
+  int32_t n_steps;            /* pairwise contraction steps (n_nodes - 1) */
   int32_t n_cuts;
   int64_t n_slices;           /* product of the cut edges' dimensions */
   double score;               /* Algorithm 1 score of the path (complex MACs per slice) */
@@ -131,6 +133,7 @@ typedef struct {
   int32_t max_rank_used;      /* M that Algorithm 1 ran with */
   int32_t chunk_bitstrings;   /* bitstrings per device batch */
   int64_t workspace_bytes;    /* device workspace for the widest precision */
+  int32_t n_nodes;            /* nodes of the contracted network (n_qubits minus merged nodes) */
 } tn_plan_info;
 
 /* Build a circuit: validates the graph (connected, simple, endpoints in
@@ -161,11 +164,19 @@ tn_status tn_circuit_bond_dims(const tn_circuit *c, int32_t side, int32_t *out);
 /* Cuts and contraction path (supplement, Algorithm 1 with Assumptions 1-3;
  * cutting as in the overlap paragraph), compiled into static per-step
  * shapes and uploaded. `opts` may be NULL (defaults). `info` may be NULL.
+ * Unless opts->no_merge, boundary nodes are first merged into a neighbour: a
+ * node v of degree <= 2 whose other legs are no wider than its edge a to u is
+ * contracted with u over a, separately and exactly (FP64) on the ket and on
+ * every bitstring's bra, giving one node with a physical index of 4 (or 8)
+ * values; the overlap network and the amplitudes are unchanged, the path
+ * search and the contraction see fewer, no larger nodes.
  * Errors: TN_ERR_STATE, TN_ERR_NO_PATH, TN_ERR_ARG, TN_ERR_CUDA, TN_ERR_OOM. */
 tn_status tn_path(tn_circuit *c, const tn_path_opts *opts, tn_plan **out, tn_plan_info *info);
 
-/* Plan details: order[n_qubits] (contraction order), cuts[n_cuts] (edge
- * ids), steps[3*n_steps] = (M, K, N) per step per slice. Any pointer may be NULL. */
+/* Plan details: order[n_qubits] (contraction order of the network's nodes,
+ * each named by its representative qubit, then -1 for the merged qubits),
+ * cuts[n_cuts] (edge ids), steps[3*n_steps] = (M, K, N) per step per slice.
+ * Any pointer may be NULL. */
 tn_status tn_plan_details(const tn_plan *p, int32_t *order, int32_t *cuts, int64_t *steps);
 
 /* Amplitudes of n bitstrings. bits: n rows of ceil(n_qubits/64) uint64 words,
@@ -177,6 +188,15 @@ tn_status tn_plan_details(const tn_plan *p, int32_t *order, int32_t *cuts, int64
  * Errors: TN_ERR_ARG, TN_ERR_CUDA, TN_ERR_OOM, TN_ERR_UNSUPPORTED. */
 tn_status tn_amplitudes(tn_plan *p, const uint64_t *bits, int64_t n, tn_precision prec,
                         tn_c128 *out, void *cuda_stream);
+
+/* Partial amplitudes: for each bitstring the FP64 sum over the slices [slice_begin, slice_end)
+ * of the plan's cut network only (0 <= slice_begin <= slice_end <= info.n_slices; an empty range
+ * gives zeros). Summing the results over a partition of [0, n_slices) gives tn_amplitudes up to
+ * the order of the FP64 additions. This is how slices are sharded over ranks when a job has fewer
+ * bitstrings than ranks (cutting, overlap paragraph: the amplitude is the sum over the cut
+ * indices). Same arguments, memory rules and errors as tn_amplitudes. */
+tn_status tn_amplitudes_slices(tn_plan *p, const uint64_t *bits, int64_t n, tn_precision prec,
+                               int64_t slice_begin, int64_t slice_end, tn_c128 *out, void *cuda_stream);
 
 /* tn_amplitudes without device allocation. The paper has no counterpart: this is for callers
  * that must not allocate device memory while they run -- a process whose own pool already holds
@@ -196,6 +216,66 @@ tn_status tn_amplitudes(tn_plan *p, const uint64_t *bits, int64_t n, tn_precisio
  *    overlaps on the GPU (other streams, other threads) race on the array: serialise them. */
 tn_status tn_amplitudes_static(tn_plan *p, const uint64_t *bits, int64_t n, tn_precision prec,
                                tn_c128 *out, void *cuda_stream);
+
+/* ---- kernel autotuning and batched circuits ------------------------------- */
+
+/* Step kernels (values written by tn_autotune / tn_plan_kernels, one per contraction step):
+ * 0 shape heuristic (SIMT), 1-3 SIMT tiles 64x64 / 128x16 / 256x4 (rows x columns),
+ * 4 SIMT streaming (K, N <= 16), 5 SIMT streaming with K and N fixed at compile time,
+ * 6 SIMT one-CTA-per-item reduction (tiny outputs), 16 tcgen05 with the operand split in the
+ * kernel (TF32, TF32x3, BF16x3, TF32x6), 32 TMA-fed tcgen05 building the overlap operand in
+ * shared memory with the tile picked by shape, 33 / 34 the same with 128- / 64-column tiles,
+ * 40 / 41 / 42 the same three loading the operand after a formation pass (BF16x6). The paper has
+ * no counterpart: which
+ * kernel runs a pairwise contraction is an implementation choice that changes no result beyond
+ * rounding. */
+enum { TN_KERNEL_SIMT = 0, TN_KERNEL_TC = 16, TN_KERNEL_TMA = 32, TN_KERNEL_TMA128 = 33, TN_KERNEL_TMA64 = 34,
+       TN_KERNEL_TMA_LOADB = 40, TN_KERNEL_TMA_LOADB128 = 41, TN_KERNEL_TMA_LOADB64 = 42 };
+
+/* Time every kernel that supports each contraction step of the plan in precision `prec`, on the
+ * plan's workspace with a batch of min(n_bits, chunk) bitstrings (n_bits = 0: the full chunk),
+ * and keep the fastest per step (the shape heuristic's kernel unless another is >= 3% faster).
+ * The choice is stored in the plan for `prec` and used by every later amplitude, server and batch
+ * call on it. kernels (may be NULL): info.n_steps entries, the chosen kernel per step.
+ * Synchronises the stream. Errors: TN_ERR_ARG, TN_ERR_STATE, TN_ERR_CUDA, TN_ERR_OOM, TN_ERR_TIMEOUT. */
+tn_status tn_autotune(tn_plan *p, tn_precision prec, int64_t n_bits, void *cuda_stream, int32_t *kernels);
+
+/* The kernels the plan runs in `prec` (tuned, else the shape heuristic), info.n_steps entries. */
+tn_status tn_plan_kernels(const tn_plan *p, tn_precision prec, int32_t *kernels);
+
+/* Set the plan's kernels for `prec`: info.n_steps TN_KERNEL_* values, each supporting its step
+ * (TN_ERR_ARG otherwise, and nothing changes); NULL returns to the shape heuristic. */
+tn_status tn_plan_set_kernels(tn_plan *p, tn_precision prec, const int32_t *kernels);
+
+typedef struct tn_batch tn_batch;
+
+/* Several circuits (their plans, each with its own batch of bitstrings; shapes may differ) as one
+ * CUDA graph. bits: every circuit's bitstrings concatenated in plan order, circuit i taking
+ * n_bits[i] rows of ceil(n_qubits_i/64) words; host or device memory, copied. The batch owns
+ * device buffers for the bitstrings, the results and one workspace per circuit (allocated through
+ * each circuit's allocator), runs every circuit once on `cuda_stream` to validate it, and
+ * captures the whole batch (one independent branch per circuit: bra evolution, overlap,
+ * contraction with the plan's kernels, FP64 slice sum) into one graph. Plans and circuits must
+ * outlive the batch; re-evolving a circuit invalidates it. The paper has no counterpart: this is
+ * the batching of many circuits into one launch.
+ * Errors: TN_ERR_ARG, TN_ERR_STATE, TN_ERR_CUDA, TN_ERR_OOM, TN_ERR_TIMEOUT. */
+tn_status tn_batch_create(tn_plan *const *plans, int32_t n_plans, const uint64_t *bits, const int64_t *n_bits,
+                          tn_precision prec, void *cuda_stream, tn_batch **out);
+
+/* Replace every circuit's bitstrings (same layout and counts as at creation); stream-ordered. */
+tn_status tn_batch_set_bits(tn_batch *b, const uint64_t *bits, void *cuda_stream);
+
+/* One launch of the batch's graph on `cuda_stream`; asynchronous. Errors: TN_ERR_STATE, TN_ERR_CUDA. */
+tn_status tn_batch_run(tn_batch *b, void *cuda_stream);
+
+/* All amplitudes of the last run, concatenated in plan order, into out (host or device); reads
+ * the circuits' error words and synchronises the stream. Errors: TN_ERR_CUDA, TN_ERR_TIMEOUT. */
+tn_status tn_batch_read(tn_batch *b, tn_c128 *out, void *cuda_stream);
+
+/* Kernel nodes in the graph and device bytes the batch holds. Either pointer may be NULL. */
+tn_status tn_batch_info(const tn_batch *b, int64_t *graph_kernels, int64_t *device_bytes);
+
+void tn_batch_free(tn_batch *b);
 
 /* Kernel launches issued since the last reset (all threads). */
 int64_t tn_launch_count(int32_t reset);

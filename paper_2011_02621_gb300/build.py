@@ -20,7 +20,7 @@ LIB = os.path.join(HERE, "libtn.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 CU = ["evolve.cu", "contract.cu", "tc_gemm.cu", "tc_tma.cu", "static_scratch.cu"]
-CPP = ["host.cpp", "server.cpp"]
+CPP = ["host.cpp", "server.cpp", "tune.cpp", "batch.cpp"]
 
 
 def cuda_home() -> str:

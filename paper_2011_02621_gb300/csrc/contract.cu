@@ -20,59 +20,6 @@ template <typename R> struct C2T;
 template <> struct C2T<double> { using T = double2; };
 template <> struct C2T<float> { using T = float2; };
 
-template <typename V> __device__ __forceinline__ V cz() { V v; v.x = 0; v.y = 0; return v; }
-template <typename V> __device__ __forceinline__ V cfma(V a, V b, V c) {
-  c.x = fma(a.x, b.x, fma(-a.y, b.y, c.x));
-  c.y = fma(a.x, b.y, fma(a.y, b.x, c.y));
-  return c;
-}
-
-struct ItemCtx {
-  int64_t b, sl;
-  int32_t sa, sb;
-};
-
-__device__ __forceinline__ ItemCtx item_ctx(const ContractArgs &a, const StepParams &s, int64_t item) {
-  ItemCtx c;
-  if (a.n_slices == 1) {
-    c.b = item;
-    c.sl = a.slice0;
-  } else {
-    c.b = (unsigned)item / (unsigned)a.n_slices;
-    c.sl = a.slice0 + (unsigned)item % (unsigned)a.n_slices;
-  }
-  c.sa = a.tab[s.t_sa + c.sl];
-  c.sb = a.tab[s.t_sb + c.sl];
-  return c;
-}
-
-// output offset of row m: m decomposed over the rest legs, weighted by their output strides
-__device__ __forceinline__ int orow_of(const StepParams &s, int64_t m64) {
-  unsigned m = (unsigned)m64;   // rows < 2^31 (checked when the plan is compiled)
-  int off = 0;
-  if (s.rest_pow2) {
-    for (int j = s.n_rest - 1; j >= 0; --j) {
-      const int lg = s.rest_log2[j];
-      off += (int)(m & ((1u << lg) - 1u)) * s.rest_ostride[j];
-      m >>= lg;
-    }
-  } else {
-    for (int j = s.n_rest - 1; j >= 0; --j) {
-      const unsigned d = (unsigned)s.rest_dim[j];
-      off += (int)(m % d) * s.rest_ostride[j];
-      m /= d;
-    }
-  }
-  return off;
-}
-
-// C element (Eq. overlap) at table offsets
-template <typename V>
-__device__ __forceinline__ V overlap_elem(const V *ket, const V *bra, int64_t ia, int64_t ib, int64_t ksig,
-                                          int64_t bsig) {
-  return cfma(ket[ia + ksig], bra[ib + bsig], cfma(ket[ia], bra[ib], cz<V>()));
-}
-
 template <typename R>
 __global__ void form_kernel(StepParams s, ContractArgs a, const typename C2T<R>::T *ket,
                             const typename C2T<R>::T *bra, OutDesc out) {
@@ -84,7 +31,7 @@ __global__ void form_kernel(StepParams s, ContractArgs a, const typename C2T<R>:
   const V *kp = ket + s.ket_off + c.sa;
   const V *bp = bra + c.b * a.bra_stride + s.bra_off + c.sb;
   store_out(out, a.t_stride, item, a.tab[s.t_ocol + n],
-            overlap_elem(kp, bp, a.tab[s.t_bna + n], a.tab[s.t_bnb + n], s.ket_sig, s.bra_sig));
+            overlap_elem(kp, bp, a.tab[s.t_bna + n], a.tab[s.t_bnb + n], s.ket_sig, s.bra_sig, s.phys));
 }
 
 // the overlap tensor in its real embedding B_r[2N][2K] (row 2n = (Re c, -Im c), row 2n+1 =
@@ -100,7 +47,7 @@ __global__ void form_b_kernel(StepParams s, ContractArgs a, const float2 *ket, c
   const float2 *kp = ket + s.ket_off + c.sa;
   const float2 *bp = bra + c.b * a.bra_stride + s.bra_off + c.sb;
   const float2 v = overlap_elem(kp, bp, (int64_t)a.tab[s.t_bka + k] + a.tab[s.t_bna + n],
-                                (int64_t)a.tab[s.t_bkb + k] + a.tab[s.t_bnb + n], s.ket_sig, s.bra_sig);
+                                (int64_t)a.tab[s.t_bkb + k] + a.tab[s.t_bnb + n], s.ket_sig, s.bra_sig, s.phys);
   uint32_t w0[3], w1[3];
   tn_split3(v.x, -v.y, w0);
   tn_split3(v.y, v.x, w1);
@@ -125,7 +72,7 @@ __global__ void form_c_kernel(StepParams s, ContractArgs a, const float2 *ket, c
   const float2 *kp = ket + s.ket_off + c.sa;
   const float2 *bp = bra + c.b * a.bra_stride + s.bra_off + c.sb;
   cbuf[item * c_stride + r] = overlap_elem(kp, bp, (int64_t)a.tab[s.t_bka + k] + a.tab[s.t_bna + n],
-                                           (int64_t)a.tab[s.t_bkb + k] + a.tab[s.t_bnb + n], s.ket_sig, s.bra_sig);
+                                           (int64_t)a.tab[s.t_bkb + k] + a.tab[s.t_bnb + n], s.ket_sig, s.bra_sig, s.phys);
 }
 
 // Tiled SIMT complex GEMM: one CTA per (item, BM x BN output tile).
@@ -174,7 +121,7 @@ step_kernel(StepParams s, ContractArgs a, const typename C2T<R>::T *ket, const t
       int64_t k = k0 + kk, n = n0 + nn;
       V v = cz<V>();
       if (k < s.K && n < s.N)
-        v = overlap_elem(kp, bp, (int64_t)bka[k] + bna[n], (int64_t)bkb[k] + bnb[n], s.ket_sig, s.bra_sig);
+        v = overlap_elem(kp, bp, (int64_t)bka[k] + bna[n], (int64_t)bkb[k] + bnb[n], s.ket_sig, s.bra_sig, s.phys);
       Bs[kk][nn] = v;
     }
     __syncthreads();
@@ -223,7 +170,7 @@ step_small_kernel(StepParams s, ContractArgs a, const typename C2T<R>::T *ket, c
     int64_t m = oi / s.N, n = oi % s.N;
     V acc = cz<V>();
     for (int64_t k = tid; k < s.K; k += 256) {
-      V cv = overlap_elem(kp, bp, (int64_t)bka[k] + bna[n], (int64_t)bkb[k] + bnb[n], s.ket_sig, s.bra_sig);
+      V cv = overlap_elem(kp, bp, (int64_t)bka[k] + bna[n], (int64_t)bkb[k] + bnb[n], s.ket_sig, s.bra_sig, s.phys);
       acc = cfma(tp[m * s.K + k], cv, acc);
     }
     for (int o = 16; o; o >>= 1) {
@@ -261,7 +208,7 @@ step_stream_kernel(StepParams s, ContractArgs a, const typename C2T<R>::T *ket, 
   if (tid < K * N) {
     const int k = tid / N, n = tid % N;
     Cs[tid] = overlap_elem(kp, bp, (int64_t)a.tab[s.t_bka + k] + a.tab[s.t_bna + n],
-                           (int64_t)a.tab[s.t_bkb + k] + a.tab[s.t_bnb + n], s.ket_sig, s.bra_sig);
+                           (int64_t)a.tab[s.t_bkb + k] + a.tab[s.t_bnb + n], s.ket_sig, s.bra_sig, s.phys);
   }
   if (tid < N) oc[tid] = a.tab[s.t_ocol + tid];
   __syncthreads();
@@ -318,7 +265,7 @@ step_stream_fixed(StepParams s, ContractArgs a, const typename C2T<R>::T *ket, c
     const V *bp = bra + c.b * a.bra_stride + s.bra_off + c.sb;
     const int k = tid / NN, n = tid % NN;
     Cs[tid] = overlap_elem(kp, bp, (int64_t)a.tab[s.t_bka + k] + a.tab[s.t_bna + n],
-                           (int64_t)a.tab[s.t_bkb + k] + a.tab[s.t_bnb + n], s.ket_sig, s.bra_sig);
+                           (int64_t)a.tab[s.t_bkb + k] + a.tab[s.t_bnb + n], s.ket_sig, s.bra_sig, s.phys);
   }
   if (tid < NN) oc[tid] = a.tab[s.t_ocol + tid];
   __syncthreads();
@@ -432,37 +379,65 @@ cudaError_t launch_form_b_pieces(const StepParams &s, const ContractArgs &a, con
   return cudaGetLastError();
 }
 
+// (K, N) pairs with a compile-time streaming kernel
+#define TN_FIXED_LIST(X) \
+  X(4, 4) X(1, 4) X(4, 1) X(2, 2) X(2, 4) X(4, 2) X(1, 2) X(2, 1) X(4, 16) X(16, 4) X(16, 1) X(1, 16)
+
+static bool has_fixed(int64_t K, int64_t N) {
+#define TN_HAS(k, n) if (K == k && N == n) return true;
+  TN_FIXED_LIST(TN_HAS)
+#undef TN_HAS
+  return false;
+}
+
+bool simt_variant_ok(const StepParams &s, int v) {
+  switch (v) {
+    case SIMT_AUTO: case SIMT_T64: case SIMT_T128: case SIMT_T256: return true;
+    case SIMT_STREAM: return s.K <= 16 && s.N <= 16;
+    case SIMT_FIXED: return has_fixed(s.K, s.N);
+    case SIMT_SMALL: return s.M * s.N <= 256;
+    default: return false;
+  }
+}
+
 template <typename R>
 cudaError_t launch_step(const StepParams &s, const ContractArgs &a, const void *ket, const void *bra,
-                        const void *t_in, const OutDesc &t_out, cudaStream_t st) {
+                        const void *t_in, const OutDesc &t_out, cudaStream_t st, int variant) {
   using V = typename C2T<R>::T;
   if (a.items <= 0) return cudaSuccess;
-  if (s.M >= 512) {
+  if (!simt_variant_ok(s, variant)) return cudaErrorInvalidValue;
+  if (variant == SIMT_AUTO) {   // the shape heuristic
+    if (s.M >= 512 && has_fixed(s.K, s.N)) variant = SIMT_FIXED;
+    else if (s.K <= 16 && s.N <= 16 && s.M >= 512) variant = SIMT_STREAM;
+    else if (s.M * s.N <= 16) variant = SIMT_SMALL;
+    else variant = s.N >= 48 ? SIMT_T64 : s.N >= 12 ? SIMT_T128 : SIMT_T256;
+  }
+  switch (variant) {
+    case SIMT_FIXED:
 #define TN_FIXED(k, n) \
   if (s.K == k && s.N == n) return launch_stream_fixed<R, k, n>(s, a, ket, bra, t_in, t_out, st);
-    TN_FIXED(4, 4) TN_FIXED(1, 4) TN_FIXED(4, 1) TN_FIXED(2, 2) TN_FIXED(2, 4) TN_FIXED(4, 2)
-    TN_FIXED(1, 2) TN_FIXED(2, 1) TN_FIXED(4, 16) TN_FIXED(16, 4) TN_FIXED(16, 1) TN_FIXED(1, 16)
+      TN_FIXED_LIST(TN_FIXED)
 #undef TN_FIXED
+      return cudaErrorInvalidValue;
+    case SIMT_STREAM: {
+      const int64_t rows = 1024;
+      const int64_t grid = ((s.M + rows - 1) / rows) * a.items;
+      if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+      step_stream_kernel<R><<<(unsigned)grid, 256, 0, st>>>(s, a, (const V *)ket, (const V *)bra, (const V *)t_in,
+                                                            t_out, rows);
+      tn_count_launch(1);
+      return cudaGetLastError();
+    }
+    case SIMT_SMALL:
+      if (a.items > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+      step_small_kernel<R><<<(unsigned)a.items, 256, 0, st>>>(s, a, (const V *)ket, (const V *)bra,
+                                                              (const V *)t_in, t_out);
+      tn_count_launch(1);
+      return cudaGetLastError();
+    case SIMT_T64: return launch_tiled<R, 64, 64, 8, 4, 4>(s, a, ket, bra, t_in, t_out, st);
+    case SIMT_T128: return launch_tiled<R, 128, 16, 8, 8, 2>(s, a, ket, bra, t_in, t_out, st);
+    default: return launch_tiled<R, 256, 4, 8, 8, 1>(s, a, ket, bra, t_in, t_out, st);
   }
-  if (s.K <= 16 && s.N <= 16 && s.M >= 512) {
-    const int64_t rows = 1024;
-    const int64_t grid = ((s.M + rows - 1) / rows) * a.items;
-    if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    step_stream_kernel<R><<<(unsigned)grid, 256, 0, st>>>(s, a, (const V *)ket, (const V *)bra, (const V *)t_in,
-                                                          t_out, rows);
-    tn_count_launch(1);
-    return cudaGetLastError();
-  }
-  if (s.M * s.N <= 16) {
-    if (a.items > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    step_small_kernel<R><<<(unsigned)a.items, 256, 0, st>>>(s, a, (const V *)ket, (const V *)bra, (const V *)t_in,
-                                                            t_out);
-    tn_count_launch(1);
-    return cudaGetLastError();
-  }
-  if (s.N >= 48) return launch_tiled<R, 64, 64, 8, 4, 4>(s, a, ket, bra, t_in, t_out, st);
-  if (s.N >= 12) return launch_tiled<R, 128, 16, 8, 8, 2>(s, a, ket, bra, t_in, t_out, st);
-  return launch_tiled<R, 256, 4, 8, 8, 1>(s, a, ket, bra, t_in, t_out, st);
 }
 
 template <typename R>
@@ -481,8 +456,8 @@ template cudaError_t launch_form<double>(const StepParams &, const ContractArgs 
 template cudaError_t launch_form<float>(const StepParams &, const ContractArgs &, const void *, const void *,
                                         const OutDesc &, cudaStream_t);
 template cudaError_t launch_step<double>(const StepParams &, const ContractArgs &, const void *, const void *,
-                                         const void *, const OutDesc &, cudaStream_t);
+                                         const void *, const OutDesc &, cudaStream_t, int);
 template cudaError_t launch_step<float>(const StepParams &, const ContractArgs &, const void *, const void *,
-                                        const void *, const OutDesc &, cudaStream_t);
+                                        const void *, const OutDesc &, cudaStream_t, int);
 template cudaError_t launch_slice_sum<double>(const void *, int64_t, int64_t, int64_t, int, double2 *, cudaStream_t);
 template cudaError_t launch_slice_sum<float>(const void *, int64_t, int64_t, int64_t, int, double2 *, cudaStream_t);

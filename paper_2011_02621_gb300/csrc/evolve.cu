@@ -85,7 +85,7 @@ __device__ __forceinline__ void item_sync() {
 
 template <int TPI>
 __global__ void __launch_bounds__(GATE_THREADS) gate_kernel(GateParams g, double2 *base, int64_t item_stride,
-                                                            double2 *gwork, int *errflag, int items) {
+                                                            double2 *gwork, int *errflag, int items, int *rank_out) {
   extern __shared__ double2 smem[];
   constexpr int GPB = GATE_THREADS / TPI;         // items per block
   const int grp = threadIdx.x / TPI;
@@ -239,6 +239,13 @@ __global__ void __launch_bounds__(GATE_THREADS) gate_kernel(GateParams g, double
     for (int j = 0; j < C; ++j) kc += (sig[j] > g.cutoff * mx) ? 1 : 0;
     s_max = mx;
     s_keep = kc < g.dout ? kc : g.dout;
+    if (rank_out && item == 0) {
+      // numerical rank: singular values above the rounding level of the column norms
+      const double thr = 4.0 * sqrt((double)R) * 2.220446049250313e-16 * mx;
+      int nr = 0;
+      for (int j = 0; j < C; ++j) nr += (sig[j] > thr) ? 1 : 0;
+      *rank_out = nr;
+    }
   }
   for (int j = tid; j < C; j += TPI) {
     int rk = 0;
@@ -314,14 +321,20 @@ __global__ void __launch_bounds__(GATE_THREADS) gate_kernel(GateParams g, double
   }
 }
 
+// product state: basis states from `bits` (|0> without bits), or the given per-qubit 2-vectors
 __global__ void init_product_kernel(double2 *base, int64_t item_stride, int items, const int64_t *node_off,
-                                    int nq, const uint64_t *bits, int words) {
+                                    int nq, const uint64_t *bits, int words, const double2 *init_vec) {
   int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (int64_t)items * nq) return;
   int item = (int)(idx / nq), q = (int)(idx % nq);
+  double2 *A = base + (int64_t)item * item_stride + node_off[q];
+  if (init_vec) {
+    A[0] = init_vec[2 * q];
+    A[1] = init_vec[2 * q + 1];
+    return;
+  }
   int b = 0;
   if (bits) b = (int)((bits[(int64_t)item * words + (q >> 6)] >> (q & 63)) & 1ull);
-  double2 *A = base + (int64_t)item * item_stride + node_off[q];
   A[0] = make_double2(b == 0 ? 1.0 : 0.0, 0.0);
   A[1] = make_double2(b == 1 ? 1.0 : 0.0, 0.0);
 }
@@ -350,8 +363,23 @@ __global__ void copy_words_kernel(const uint64_t *src, uint64_t *dst, int64_t n)
 
 int64_t gate_work_elems(const GateParams &g) { return work_layout(g).total; }
 
+// Raise a kernel's dynamic shared memory limit to the most the device allows next to the kernel's
+// static shared memory, once (every later launch asks for at most that, so concurrent host
+// threads never lower it under one another).
+template <typename F>
+static cudaError_t allow_max_smem(F *kernel) {
+  int dev = 0, optin = 0;
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kernel);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+  return e;
+}
+
 cudaError_t launch_gate(const GateParams &g, double2 *base, int64_t item_stride, int items, double2 *gwork,
-                        int *errflag, cudaStream_t st) {
+                        int *errflag, int *rank_out, cudaStream_t st) {
   if (items <= 0) return cudaSuccess;
   const WorkLayout L = work_layout(g);
   // small matrices: one warp per item, four items per CTA
@@ -359,28 +387,30 @@ cudaError_t launch_gate(const GateParams &g, double2 *base, int64_t item_stride,
   if (warp_per_item) {
     const size_t smem = 4 * (size_t)L.total * sizeof(double2);
     if (smem > 48 * 1024) {
-      cudaError_t e = cudaFuncSetAttribute(gate_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      static const cudaError_t e = allow_max_smem(gate_kernel<32>);
       if (e != cudaSuccess) return e;
     }
-    gate_kernel<32><<<(items + 3) / 4, GATE_THREADS, smem, st>>>(g, base, item_stride, gwork, errflag, items);
+    gate_kernel<32><<<(items + 3) / 4, GATE_THREADS, smem, st>>>(g, base, item_stride, gwork, errflag, items,
+                                                                 rank_out);
   } else {
     const size_t smem = g.use_smem ? (size_t)L.total * sizeof(double2) : 0;
     if (smem > 48 * 1024) {
-      cudaError_t e = cudaFuncSetAttribute(gate_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      static const cudaError_t e = allow_max_smem(gate_kernel<128>);
       if (e != cudaSuccess) return e;
     }
-    gate_kernel<128><<<items, GATE_THREADS, smem, st>>>(g, base, item_stride, gwork, errflag, items);
+    gate_kernel<128><<<items, GATE_THREADS, smem, st>>>(g, base, item_stride, gwork, errflag, items, rank_out);
   }
   tn_count_launch(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_init_product(double2 *base, int64_t item_stride, int items, const int64_t *node_off_dev,
-                                int n_qubits, const uint64_t *bits, int words, cudaStream_t st) {
+                                int n_qubits, const uint64_t *bits, int words, const double2 *init_vec,
+                                cudaStream_t st) {
   int64_t total = (int64_t)items * n_qubits;
   if (total <= 0) return cudaSuccess;
   init_product_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(base, item_stride, items, node_off_dev,
-                                                                       n_qubits, bits, words);
+                                                                       n_qubits, bits, words, init_vec);
   tn_count_launch(1);
   return cudaGetLastError();
 }
@@ -389,6 +419,45 @@ cudaError_t launch_apply1(const Apply1Params &a, double2 *base, int64_t item_str
   int64_t total = (int64_t)items * a.size_rest;
   if (total <= 0) return cudaSuccess;
   apply1_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(a, base, item_stride, items);
+  tn_count_launch(1);
+  return cudaGetLastError();
+}
+
+// One merged node tensor per item (grid.y strides over items): each thread one output element,
+// the sum over the shared leg in index order, in FP64.
+__global__ void merge_kernel(MergeParams m, double2 *base, int64_t item_stride, int64_t items) {
+  const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= m.out_size) return;
+  int64_t r = o, iu = 0, iv = 0;
+  for (int j = m.nv - 1; j >= 0; --j) {
+    iv += (r % m.dv[j]) * m.sv[j];
+    r /= m.dv[j];
+  }
+  for (int j = m.nu - 1; j >= 0; --j) {
+    iu += (r % m.du[j]) * m.su[j];
+    r /= m.du[j];
+  }
+  iv += (r % m.pv) * m.sv_p;
+  iu += (r / m.pv) * m.su_p;
+  for (int64_t item = blockIdx.y; item < items; item += gridDim.y) {
+    const double2 *U = base + item * item_stride + m.u_off + iu;
+    const double2 *V = base + item * item_stride + m.v_off + iv;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int x = 0; x < m.da; ++x) {
+      const double2 u = U[x * m.su_a], v = V[x * m.sv_a];
+      acc.x = fma(u.x, v.x, fma(-u.y, v.y, acc.x));
+      acc.y = fma(u.x, v.y, fma(u.y, v.x, acc.y));
+    }
+    base[item * item_stride + m.out_off + o] = acc;
+  }
+}
+
+cudaError_t launch_merge(const MergeParams &m, double2 *base, int64_t item_stride, int64_t items, cudaStream_t st) {
+  if (items <= 0 || m.out_size <= 0) return cudaSuccess;
+  const int64_t gx = (m.out_size + 255) / 256;
+  if (gx > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  merge_kernel<<<dim3((unsigned)gx, (unsigned)(items < 65535 ? items : 65535)), 256, 0, st>>>(m, base, item_stride,
+                                                                                             items);
   tn_count_launch(1);
   return cudaGetLastError();
 }

@@ -46,12 +46,6 @@ extern "C" int64_t tn_launch_count(int32_t reset) {
 
 extern "C" const char *tn_last_error(void) { return g_err.c_str(); }
 
-#define CUDA_TRY(x)                                                                        \
-  do {                                                                                     \
-    cudaError_t e_ = (x);                                                                  \
-    if (e_ != cudaSuccess) return tn_fail(TN_ERR_CUDA, "%s: %s", #x, cudaGetErrorString(e_)); \
-  } while (0)
-
 // ---------------------------------------------------------------------------
 // tracing
 // ---------------------------------------------------------------------------
@@ -97,6 +91,12 @@ void prof_drain() {   // caller holds the mutex
 
 ProfScope::ProfScope(const char *kind, cudaStream_t stream, double bytes, double flops) {
   if (!g_prof_on) return;
+  // no events inside a stream capture (work captured into a graph is timed by its launch)
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return;
+  }
   std::lock_guard<std::mutex> lk(g_prof_mu);
   if (!g_prof_on) return;
   int k = -1;
@@ -378,8 +378,16 @@ static M2 mul2(const M2 &a, const M2 &b) {
 // Build one half: `seq` in processing order, matrices transposed for the bra.
 // Single-qubit gates accumulate per qubit and fuse into the next two-qubit
 // gate on that qubit (its input side); leftovers become tail applications.
+// caps / cap_sv (optional): probed rank per two-qubit step and the endpoint it was probed on;
+// a cap applies only where this program SVDs the same endpoint.
+// The half's gate program with static shapes. Without `force_sv` every compression SVDs the
+// endpoint with fewer rows 2 * prod(other legs) (ties: q[0]) and the bond becomes
+// min(dim * chi_o, those rows, chi): the structural program, independent of the state. With
+// `force_sv` (the structural program's endpoints) and `caps` (probed ranks), the same endpoints
+// are kept and each bond is also capped by its probed rank.
 static void build_half(const tn_circuit *c, const std::vector<const tn_gate *> &seq, bool transpose, int chi,
-                       double cutoff, Half &h) {
+                       double cutoff, Half &h, const std::vector<int> *caps = nullptr,
+                       const std::vector<int> *force_sv = nullptr) {
   const int n = c->n;
   h = Half();
   h.dims.assign(c->ne, 1);
@@ -443,9 +451,12 @@ static void build_half(const tn_circuit *c, const std::vector<const tn_gate *> &
     gp.n = gp.din * chi_o;
     gp.m_k = (int)(2 * ok);
     gp.m_l = (int)(2 * ol);
+    const size_t gi = h.gp.size();
     gp.sv_is_k = gp.m_k <= gp.m_l ? 1 : 0;     // SVD the endpoint with fewer rows (ties: q[0])
-    int dout = std::min(gp.n, std::min(gp.m_k, gp.m_l));
+    if (force_sv && gi < force_sv->size()) gp.sv_is_k = (*force_sv)[gi];
+    int dout = std::min(gp.n, gp.sv_is_k ? gp.m_k : gp.m_l);
     if (chi > 0) dout = std::min(dout, chi);
+    if (caps && gi < caps->size() && (*caps)[gi] > 0) dout = std::min(dout, (*caps)[gi]);   // probed rank
     gp.dout = dout;
     gp.cutoff = cutoff;
     for (int i = 0; i < 16; ++i) {
@@ -507,20 +518,23 @@ static double gate_flops(const GateParams &g) {
 }
 
 tn_status run_half(const Half &h, int n_qubits, double2 *base, int items, const int64_t *node_off_dev,
-                   const uint64_t *bits_dev, int words, double2 *gwork, int *errflag, cudaStream_t st) {
+                   const uint64_t *bits_dev, int words, double2 *gwork, int *errflag, cudaStream_t st,
+                   int *rank_out_dev, const double2 *init_vec_dev, int64_t item_stride) {
+  const int64_t stride = item_stride > 0 ? item_stride : h.item_elems;
   {
     ProfScope ps("init_product", st, 32.0 * items * n_qubits, 0);
-    CUDA_TRY(launch_init_product(base, h.item_elems, items, node_off_dev, n_qubits, bits_dev, words, st));
+    CUDA_TRY(launch_init_product(base, stride, items, node_off_dev, n_qubits, bits_dev, words, init_vec_dev, st));
   }
   for (const auto &op : h.seq) {
     if (op.first == 2) {
       const GateParams &g = h.gp[op.second];
       ProfScope ps("gate_svd_fp64", st, gate_bytes(g) * items, gate_flops(g) * items);
-      CUDA_TRY(launch_gate(g, base, h.item_elems, items, gwork, errflag, st));
+      CUDA_TRY(launch_gate(g, base, stride, items, gwork, errflag, rank_out_dev ? rank_out_dev + op.second : nullptr,
+                           st));
     } else {
       const Apply1Params &a = h.ap[op.second];
       ProfScope ps("apply_1q_fp64", st, 64.0 * a.size_rest * items, 16.0 * a.size_rest * items);
-      CUDA_TRY(launch_apply1(a, base, h.item_elems, items, st));
+      CUDA_TRY(launch_apply1(a, base, stride, items, st));
     }
   }
   return TN_OK;
@@ -537,6 +551,58 @@ static tn_status init_device(int &dev) {
   return TN_OK;
 }
 
+// Run one half once (one item) and read back the numerical rank of every compression.
+// `init` = per-qubit 2-vectors of a product initial state (NULL: |0...0>).
+static tn_status probe_ranks(tn_circuit *c, const Half &h, const std::vector<double2> *init, std::vector<int> &caps,
+                             cudaStream_t st) {
+  DevMem &mem = c->mem;
+  Buf region, offs, work, ranks, ivec, err;
+  auto cleanup = [&]() {
+    cudaStreamSynchronize(st);
+    mem.release(region);
+    mem.release(offs);
+    mem.release(work);
+    mem.release(ranks);
+    mem.release(ivec);
+    mem.release(err);
+  };
+  const size_t ng = std::max<size_t>(h.gp.size(), 1);
+  tn_status s;
+  if ((s = mem.ensure(region, h.item_elems * sizeof(double2), st)) != TN_OK ||
+      (s = mem.ensure(offs, c->n * sizeof(int64_t), st)) != TN_OK ||
+      (s = mem.ensure(work, std::max<int64_t>(h.max_work, 1) * sizeof(double2), st)) != TN_OK ||
+      (s = mem.ensure(ranks, ng * sizeof(int), st)) != TN_OK ||
+      (s = mem.ensure(ivec, 2 * c->n * sizeof(double2), st)) != TN_OK || (s = mem.ensure(err, 16, st)) != TN_OK) {
+    cleanup();
+    return s;
+  }
+  cudaError_t e = cudaMemcpyAsync(offs.p, h.node_off.data(), c->n * sizeof(int64_t), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && init)
+    e = cudaMemcpyAsync(ivec.p, init->data(), 2 * c->n * sizeof(double2), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ranks.p, 0, ng * sizeof(int), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(err.p, 0, 16, st);
+  if (e != cudaSuccess) {
+    cleanup();
+    return tn_fail(TN_ERR_CUDA, "rank probe set-up: %s", cudaGetErrorString(e));
+  }
+  s = run_half(h, c->n, (double2 *)region.p, 1, (const int64_t *)offs.p, nullptr, 1, (double2 *)work.p,
+               (int *)err.p, st, (int *)ranks.p, init ? (const double2 *)ivec.p : nullptr);
+  if (s != TN_OK) {
+    cleanup();
+    return s;
+  }
+  caps.assign(h.gp.size(), 0);
+  int errv = 0;
+  e = cudaMemcpyAsync(caps.data(), ranks.p, h.gp.size() * sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&errv, err.p, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cleanup();
+  if (e != cudaSuccess) return tn_fail(TN_ERR_CUDA, "rank probe: %s", cudaGetErrorString(e));
+  if (errv) return tn_fail(TN_ERR_TIMEOUT, "Jacobi SVD did not converge within its sweep limit (rank probe)");
+  for (int &x : caps) x = std::max(x, 1);
+  return TN_OK;
+}
+
 extern "C" tn_status tn_evolve_two_sided(tn_circuit *c, int32_t split_cycle, int32_t chi_max, double cutoff_rel,
                                          void *cuda_stream) {
   if (!c) return tn_fail(TN_ERR_ARG, "tn_evolve_two_sided: NULL circuit");
@@ -547,6 +613,7 @@ extern "C" tn_status tn_evolve_two_sided(tn_circuit *c, int32_t split_cycle, int
   cudaStream_t st = (cudaStream_t)cuda_stream;
   // the same program again keeps plans valid (same static shapes); anything else rebuilds it
   const bool same = c->evolved && c->split == split_cycle && c->chi == chi_max && c->cutoff == cutoff_rel;
+  DevMem &mem = c->mem;
   if (!same) {
     std::vector<const tn_gate *> g1, g2;
     for (const auto &g : c->gates) (g.cycle <= split_cycle ? g1 : g2).push_back(&g);
@@ -556,10 +623,46 @@ extern "C" tn_status tn_evolve_two_sided(tn_circuit *c, int32_t split_cycle, int
     c->split = split_cycle;
     c->chi = chi_max;
     c->cutoff = cutoff_rel;
+    // Rank probe. The static bounds can exceed the true bond ranks. The ket is a single state:
+    // its ranks are exact. For the bra, the ranks reached from one random (generic) product state
+    // bound those reached from every basis state (a rank can only drop on special inputs), so
+    // they are safe static shapes; rank deficits stay zero-padded. Every rebuilt program SVDs the
+    // structural program's endpoints (which endpoint is compressed changes a truncated result, so
+    // it must not depend on the data), capped by the probed ranks, and is probed again until the
+    // shapes stop shrinking (at most four rounds).
+    c->evolved = false;
+    std::vector<double2> gen_init(2 * c->n);
+    {
+      uint64_t x = 0x9E3779B97F4A7C15ull;   // fixed splitmix64 stream: deterministic shapes
+      auto u = [&x]() {
+        x += 0x9E3779B97F4A7C15ull;
+        uint64_t z = x;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        return (double)(z >> 11) * (1.0 / 9007199254740992.0) - 0.5;
+      };
+      for (auto &v : gen_init) v = make_double2(u(), u());
+    }
+    for (int side = 0; side < 2; ++side) {
+      const std::vector<const tn_gate *> &seq = side == 0 ? g1 : g2;
+      Half &h = side == 0 ? c->ket : c->bra;
+      std::vector<int> sv(h.gp.size());     // the structural program's endpoints, kept throughout
+      for (size_t i = 0; i < h.gp.size(); ++i) sv[i] = h.gp[i].sv_is_k;
+      for (int round = 0; round < 4; ++round) {
+        std::vector<int> caps;
+        tn_status ps = probe_ranks(c, h, side == 0 ? nullptr : &gen_init, caps, st);
+        if (ps != TN_OK) return ps;
+        Half next;
+        build_half(c, seq, side == 1, chi_max, cutoff_rel, next, &caps, &sv);
+        const bool changed = next.dims != h.dims || next.item_elems != h.item_elems;
+        h = next;
+        if (!changed) break;
+      }
+    }
   }
   c->evolved = false;
   // upload node offsets, run the ket half (one item)
-  DevMem &mem = c->mem;
   if ((s = mem.ensure(c->ket_dev, c->ket.item_elems * sizeof(double2), st)) != TN_OK) return s;
   if ((s = mem.ensure(c->ket_c64, c->ket.item_elems * sizeof(float2), st)) != TN_OK) return s;
   if ((s = mem.ensure(c->ket_off_dev, c->n * sizeof(int64_t), st)) != TN_OK) return s;
@@ -571,7 +674,7 @@ extern "C" tn_status tn_evolve_two_sided(tn_circuit *c, int32_t split_cycle, int
   CUDA_TRY(cudaMemsetAsync(c->ket_dev.p, 0, c->ket.item_elems * sizeof(double2), st));
   CUDA_TRY(cudaMemsetAsync(c->err_dev.p, 0, sizeof(int), st));
   s = run_half(c->ket, c->n, (double2 *)c->ket_dev.p, 1, (const int64_t *)c->ket_off_dev.p, nullptr, 1,
-               (double2 *)c->ket_work.p, (int *)c->err_dev.p, st);
+               (double2 *)c->ket_work.p, (int *)c->err_dev.p, st, nullptr, nullptr);
   if (s != TN_OK) return s;
   CUDA_TRY(launch_to_c64((const double2 *)c->ket_dev.p, (float2 *)c->ket_c64.p, c->ket.item_elems, st));
   int err = 0;
@@ -764,15 +867,37 @@ static tn_status path_auto(const PathGraph &pg, const tn_path_opts &o, std::vect
   }
   int maxdeg = 0;
   for (int q = 0; q < pg.n; ++q) maxdeg = std::max(maxdeg, (int)pg.adj[q].size());
+  // smallest feasible M, then up to three larger ones (a looser rank bound can only lower the
+  // score); the lowest score wins
   int64_t total = 0;
   tn_status s = TN_ERR_NO_PATH;
+  int first = -1;
+  double best = 0;
+  std::vector<int> best_order;
   for (int M = std::max(maxdeg, 1); M <= pg.n + 1; ++M) {
+    if (first >= 0 && M > first + 3) break;
     int64_t p = 0;
-    s = alg1(pg, M, o.boundary_only != 0, true, cap, order, score, p);
+    std::vector<int> ord;
+    double sc = 0;
+    tn_status r = alg1(pg, M, o.boundary_only != 0, true, cap, ord, sc, p);
     total += p;
-    if (s == TN_OK) { rank_used = M; break; }
+    if (r != TN_OK) {
+      if (first >= 0) break;   // a larger M ran out of states: keep what was found
+      continue;
+    }
+    if (first < 0) first = M;
+    if (best_order.empty() || sc < best) {
+      best = sc;
+      best_order = ord;
+      rank_used = M;
+    }
+    s = TN_OK;
   }
   pops = total;
+  if (s == TN_OK) {
+    order = best_order;
+    score = best;
+  }
   return s;
 }
 
@@ -818,18 +943,18 @@ tn_path_opts tn_default_opts() {
 // cuts and the plan compiler
 // ---------------------------------------------------------------------------
 // sizes of the intermediates along `order` (elements), with per-edge dims
-static std::vector<double> frontier_sizes(const tn_circuit *c, const std::vector<int> &order,
+static std::vector<double> frontier_sizes(const Net &c, const std::vector<int> &order,
                                           const std::vector<double> &dims, std::vector<std::vector<int>> *open_out) {
-  std::vector<char> in(c->n, 0);
+  std::vector<char> in(c.n, 0);
   std::vector<double> sizes;
-  std::vector<char> open(c->ne, 0);
+  std::vector<char> open(c.ne, 0);
   for (size_t j = 0; j < order.size(); ++j) {
     int i = order[j];
     in[i] = 1;
-    for (int e : c->legs[i]) open[e] = !open[e] ? 1 : 0;   // toggles: opened by first endpoint, closed by second
+    for (int e : c.legs[i]) open[e] = !open[e] ? 1 : 0;   // toggles: opened by first endpoint, closed by second
     double s = 1;
     std::vector<int> op;
-    for (int e = 0; e < c->ne; ++e)
+    for (int e = 0; e < c.ne; ++e)
       if (open[e]) { s *= dims[e]; op.push_back(e); }
     sizes.push_back(s);
     if (open_out) open_out->push_back(op);
@@ -842,12 +967,12 @@ static std::vector<double> frontier_sizes(const tn_circuit *c, const std::vector
 // whose cut network has the smallest total cost (slices x Algorithm 1 score of the cut
 // network), until every intermediate fits `limit` (or `want` cuts are made). Returns the
 // final path of the cut network.
-static tn_status choose_cuts(const tn_circuit *c, const tn_path_opts &o, std::vector<double> dims, int want,
+static tn_status choose_cuts(const Net &c, const tn_path_opts &o, std::vector<double> dims, int want,
                              double limit, std::vector<int> &cuts, std::vector<int> &order, double &score,
                              int64_t &pops, int &rank_used) {
   cuts.clear();
   double slices = 1;
-  for (int it = 0; it < c->ne; ++it) {
+  for (int it = 0; it < c.ne; ++it) {
     std::vector<std::vector<int>> open;
     std::vector<double> sz = frontier_sizes(c, order, dims, &open);
     const double mx = *std::max_element(sz.begin(), sz.end());
@@ -861,7 +986,7 @@ static tn_status choose_cuts(const tn_circuit *c, const tn_path_opts &o, std::ve
       if (dims[e] <= 1) continue;
       std::vector<double> d2 = dims;
       d2[e] = 1;
-      PathGraph pg = make_pg(c->n, c->eu, c->ev, d2);
+      PathGraph pg = make_pg(c.n, c.eu, c.ev, d2);
       std::vector<int> ord;
       double sc = 0;
       int64_t pp = 0;
@@ -889,7 +1014,7 @@ static tn_status choose_cuts(const tn_circuit *c, const tn_path_opts &o, std::ve
 extern "C" tn_status tn_cut_search(const tn_graph *g, const double *dims, const tn_path_opts *opts, int32_t *order,
                                    int32_t *cuts, int32_t *n_cuts, double *total_cmacs) {
   if (!g || !dims || !order || !n_cuts) return tn_fail(TN_ERR_ARG, "tn_cut_search: NULL argument");
-  tn_circuit tmp;
+  Net tmp;
   tn_status s = check_graph(g, tmp.eu, tmp.ev, tmp.legs);
   if (s != TN_OK) return s;
   tmp.n = g->n_qubits;
@@ -915,7 +1040,7 @@ extern "C" tn_status tn_cut_search(const tn_graph *g, const double *dims, const 
     }
     PathGraph pg2 = make_pg(tmp.n, tmp.eu, tmp.ev, d2);
     if ((s = path_auto(pg2, o, ord, score, pops, ru)) != TN_OK) return s;
-  } else if ((s = choose_cuts(&tmp, o, d, o.n_cuts, limit, cut, ord, score, pops, ru)) != TN_OK) {
+  } else if ((s = choose_cuts(tmp, o, d, o.n_cuts, limit, cut, ord, score, pops, ru)) != TN_OK) {
     return s;
   }
   double slices = 1;
@@ -930,16 +1055,173 @@ extern "C" tn_status tn_cut_search(const tn_graph *g, const double *dims, const 
 
 static int64_t dc_of(const tn_circuit *c, int e) { return (int64_t)c->ket.dims[e] * c->bra.dims[e]; }
 
-static tn_status compile_plan(tn_circuit *c, tn_plan *p) {
-  const int n = c->n;
+// ---------------------------------------------------------------------------
+// the overlap network: one node per qubit, then boundary nodes merged into neighbours
+// ---------------------------------------------------------------------------
+static Net identity_net(const tn_circuit *c) {
+  Net g;
+  g.n = c->n;
+  g.ne = c->ne;
+  g.eu = c->eu;
+  g.ev = c->ev;
+  g.legs = c->legs;
+  g.eid.resize(c->ne);
+  g.dk.resize(c->ne);
+  g.db.resize(c->ne);
+  for (int e = 0; e < c->ne; ++e) {
+    g.eid[e] = e;
+    g.dk[e] = c->ket.dims[e];
+    g.db[e] = c->bra.dims[e];
+  }
+  g.rep.resize(c->n);
+  g.phys.assign(c->n, 2);
+  for (int q = 0; q < c->n; ++q) g.rep[q] = q;
+  g.ket_off = c->ket.node_off;
+  g.bra_off = c->bra.node_off;
+  g.ket_elems = c->ket.item_elems;
+  g.bra_elems = c->bra.item_elems;
+  return g;
+}
+
+// Merge node v into u through edge a on both halves: U's tensor becomes
+// [p_u, p_v, legs_u \ a, legs_v \ a] = sum_a U V, a new slot past the items' current ends.
+static void apply_merge(Net &g, int v, int a) {
+  const int u = g.eu[a] == v ? g.ev[a] : g.eu[a];
+  for (int half = 0; half < 2; ++half) {
+    const std::vector<int64_t> &d = half ? g.db : g.dk;
+    auto strides = [&](int node, std::vector<int64_t> &st) -> int64_t {
+      const auto &L = g.legs[node];
+      st.assign(L.size(), 1);
+      int64_t x = 1;
+      for (int j = (int)L.size() - 1; j >= 0; --j) { st[j] = x; x *= d[L[j]]; }
+      return x;
+    };
+    MergeParams m;
+    std::memset(&m, 0, sizeof m);
+    std::vector<int64_t> su, sv;
+    m.su_p = strides(u, su);
+    m.sv_p = strides(v, sv);
+    m.pu = g.phys[u];
+    m.pv = g.phys[v];
+    m.da = (int)d[a];
+    m.u_off = half ? g.bra_off[u] : g.ket_off[u];
+    m.v_off = half ? g.bra_off[v] : g.ket_off[v];
+    int64_t size = (int64_t)m.pu * m.pv;
+    for (size_t j = 0; j < g.legs[u].size(); ++j) {
+      const int e = g.legs[u][j];
+      if (e == a) { m.su_a = su[j]; continue; }
+      m.du[m.nu] = (int)d[e];
+      m.su[m.nu++] = su[j];
+      size *= d[e];
+    }
+    for (size_t j = 0; j < g.legs[v].size(); ++j) {
+      const int e = g.legs[v][j];
+      if (e == a) { m.sv_a = sv[j]; continue; }
+      m.dv[m.nv] = (int)d[e];
+      m.sv[m.nv++] = sv[j];
+      size *= d[e];
+    }
+    m.out_size = size;
+    int64_t &ext = half ? g.bra_elems : g.ket_elems;
+    m.out_off = ext;
+    ext += (size + 1) & ~1LL;
+    (half ? g.mb : g.mk).push_back(m);
+    (half ? g.bra_off : g.ket_off)[u] = m.out_off;
+  }
+  std::vector<int> L;
+  for (int e : g.legs[u])
+    if (e != a) L.push_back(e);
+  for (int e : g.legs[v]) {
+    if (e == a) continue;
+    L.push_back(e);
+    (g.eu[e] == v ? g.eu[e] : g.ev[e]) = u;
+  }
+  g.legs[u] = L;
+  g.legs[v].clear();
+  g.phys[u] *= g.phys[v];
+  g.eu[a] = g.ev[a] = -1;
+}
+
+// Repeatedly merge a not-yet-merged node v of degree <= 2 into the neighbour u across its widest
+// edge a when v's other legs are no wider than a (the merged tensor is no larger than u's), the
+// physical dimension stays <= 8, no parallel edge appears, no kept edge (an explicit cut) is
+// merged away, and at least two nodes remain. Then renumber nodes and edges compactly.
+static void merge_nodes(Net &g, const std::vector<char> &keep_edge) {
+  std::vector<char> alive(g.n, 1);
+  int n_alive = g.n;
+  auto other = [&](int e, int x) { return g.eu[e] == x ? g.ev[e] : g.eu[e]; };
+  for (bool did = true; did && n_alive > 2;) {
+    did = false;
+    for (int v = 0; v < g.n && !did; ++v) {
+      if (!alive[v] || g.phys[v] != 2 || g.legs[v].empty() || g.legs[v].size() > 2) continue;
+      int best = -1;
+      for (int a : g.legs[v]) {
+        if (keep_edge[g.eid[a]]) continue;
+        const int u = other(a, v);
+        if (g.phys[u] * g.phys[v] > 8) continue;
+        if (g.legs[u].size() + g.legs[v].size() - 2 > TN_MAXMLEGS) continue;
+        int64_t rest = 1;
+        bool parallel = false;
+        for (int e : g.legs[v]) {
+          if (e == a) continue;
+          rest *= g.dc(e);
+          const int x = other(e, v);
+          if (x == u) parallel = true;
+          for (int f : g.legs[u])
+            if (other(f, u) == x) parallel = true;
+        }
+        if (parallel || rest > g.dc(a)) continue;
+        if (best < 0 || g.dc(a) > g.dc(best)) best = a;
+      }
+      if (best < 0) continue;
+      apply_merge(g, v, best);
+      alive[v] = 0;
+      --n_alive;
+      did = true;
+    }
+  }
+  // compact: surviving nodes and edges in increasing order
+  std::vector<int> nid(g.n, -1), eidx(g.ne, -1);
+  Net h;
+  for (int v = 0; v < g.n; ++v)
+    if (alive[v]) {
+      nid[v] = h.n++;
+      h.rep.push_back(g.rep[v]);
+      h.phys.push_back(g.phys[v]);
+      h.ket_off.push_back(g.ket_off[v]);
+      h.bra_off.push_back(g.bra_off[v]);
+    }
+  for (int e = 0; e < g.ne; ++e)
+    if (g.eu[e] >= 0) {
+      eidx[e] = h.ne++;
+      h.eu.push_back(nid[g.eu[e]]);
+      h.ev.push_back(nid[g.ev[e]]);
+      h.eid.push_back(g.eid[e]);
+      h.dk.push_back(g.dk[e]);
+      h.db.push_back(g.db[e]);
+    }
+  h.legs.resize(h.n);
+  for (int v = 0; v < g.n; ++v)
+    if (alive[v])
+      for (int e : g.legs[v]) h.legs[nid[v]].push_back(eidx[e]);
+  h.ket_elems = g.ket_elems;
+  h.bra_elems = g.bra_elems;
+  h.mk = g.mk;
+  h.mb = g.mb;
+  g = h;
+}
+
+static tn_status compile_plan(tn_plan *p) {
+  const Net &c = p->net;
+  const int n = c.n;
   std::vector<int> pos(n);
   for (int j = 0; j < n; ++j) pos[p->order[j]] = j;
-  std::vector<char> is_cut(c->ne, 0);
+  std::vector<char> is_cut(c.ne, 0);
   for (int e : p->cuts) is_cut[e] = 1;
   std::vector<int64_t> cut_stride(p->cuts.size());
   {
     int64_t s = 1;
-    for (int j = (int)p->cuts.size() - 1; j >= 0; --j) { cut_stride[j] = s; s *= dc_of(c, p->cuts[j]); }
+    for (int j = (int)p->cuts.size() - 1; j >= 0; --j) { cut_stride[j] = s; s *= c.dc(p->cuts[j]); }
     p->n_slices = s;
   }
   auto &tab = p->tab_host;
@@ -950,30 +1232,30 @@ static tn_status compile_plan(tn_circuit *c, tn_plan *p) {
     return off;
   };
   // per-node ket/bra strides of each leg
-  auto leg_strides = [&](int i, const Half &h, std::vector<int64_t> &st) -> int64_t {
-    const auto &L = c->legs[i];
+  auto leg_strides = [&](int i, const std::vector<int64_t> &dims, std::vector<int64_t> &st) -> int64_t {
+    const auto &L = c.legs[i];
     st.assign(L.size(), 1);
     int64_t s = 1;
-    for (int j = (int)L.size() - 1; j >= 0; --j) { st[j] = s; s *= h.dims[L[j]]; }
+    for (int j = (int)L.size() - 1; j >= 0; --j) { st[j] = s; s *= dims[L[j]]; }
     return s;
   };
   // tables over a list of legs of node i: offsets into ket / bra for each multi-index
   auto leg_tables = [&](int i, const std::vector<int> &legs, std::vector<int64_t> &ta, std::vector<int64_t> &tb) {
     std::vector<int64_t> sk, sb;
-    leg_strides(i, c->ket, sk);
-    leg_strides(i, c->bra, sb);
+    leg_strides(i, c.dk, sk);
+    leg_strides(i, c.db, sb);
     int64_t total = 1;
-    for (int e : legs) total *= dc_of(c, e);
+    for (int e : legs) total *= c.dc(e);
     ta.assign(total, 0);
     tb.assign(total, 0);
     for (int64_t idx = 0; idx < total; ++idx) {
       int64_t r = idx, oa = 0, ob = 0;
       for (int j = (int)legs.size() - 1; j >= 0; --j) {
         int e = legs[j];
-        int64_t d = dc_of(c, e), cval = r % d;
+        int64_t d = c.dc(e), cval = r % d;
         r /= d;
-        int li = (int)(std::find(c->legs[i].begin(), c->legs[i].end(), e) - c->legs[i].begin());
-        int64_t db = c->bra.dims[e];
+        int li = (int)(std::find(c.legs[i].begin(), c.legs[i].end(), e) - c.legs[i].begin());
+        int64_t db = c.db[e];
         oa += (cval / db) * sk[li];
         ob += (cval % db) * sb[li];
       }
@@ -983,18 +1265,18 @@ static tn_status compile_plan(tn_circuit *c, tn_plan *p) {
   };
   auto slice_tables = [&](int i, std::vector<int64_t> &sa, std::vector<int64_t> &sbv) {
     std::vector<int64_t> sk, sb;
-    leg_strides(i, c->ket, sk);
-    leg_strides(i, c->bra, sb);
+    leg_strides(i, c.dk, sk);
+    leg_strides(i, c.db, sb);
     sa.assign(p->n_slices, 0);
     sbv.assign(p->n_slices, 0);
     for (int64_t s = 0; s < p->n_slices; ++s) {
       for (size_t j = 0; j < p->cuts.size(); ++j) {
         int e = p->cuts[j];
-        auto it = std::find(c->legs[i].begin(), c->legs[i].end(), e);
-        if (it == c->legs[i].end()) continue;
-        int li = (int)(it - c->legs[i].begin());
-        int64_t cval = (s / cut_stride[j]) % dc_of(c, e);
-        int64_t db = c->bra.dims[e];
+        auto it = std::find(c.legs[i].begin(), c.legs[i].end(), e);
+        if (it == c.legs[i].end()) continue;
+        int li = (int)(it - c.legs[i].begin());
+        int64_t cval = (s / cut_stride[j]) % c.dc(e);
+        int64_t db = c.db[e];
         sa[s] += (cval / db) * sk[li];
         sbv[s] += (cval % db) * sb[li];
       }
@@ -1002,12 +1284,12 @@ static tn_status compile_plan(tn_circuit *c, tn_plan *p) {
   };
   auto new_legs_of = [&](int i, const std::vector<char> &open) {
     std::vector<int> nl;
-    for (int e : c->legs[i])
+    for (int e : c.legs[i])
       if (!is_cut[e] && !open[e]) nl.push_back(e);
     // later-absorbed neighbours first, so the next consumer's legs are innermost
     std::sort(nl.begin(), nl.end(), [&](int a, int b) {
-      int oa = c->eu[a] == i ? c->ev[a] : c->eu[a];
-      int ob = c->eu[b] == i ? c->ev[b] : c->eu[b];
+      int oa = c.eu[a] == i ? c.ev[a] : c.eu[a];
+      int ob = c.eu[b] == i ? c.ev[b] : c.eu[b];
       return pos[oa] > pos[ob];
     });
     return nl;
@@ -1018,11 +1300,11 @@ static tn_status compile_plan(tn_circuit *c, tn_plan *p) {
   // [rest_j, shared_j], both in the order the legs were created
   std::vector<std::vector<int>> R(n), Sh(n), Nw(n);
   {
-    std::vector<char> open(c->ne, 0);
+    std::vector<char> open(c.ne, 0);
     std::vector<int> cur;
     for (int j = 0; j < n; ++j) {
       const int i = p->order[j];
-      for (int e : cur) ((c->eu[e] == i || c->ev[e] == i) ? Sh[j] : R[j]).push_back(e);
+      for (int e : cur) ((c.eu[e] == i || c.ev[e] == i) ? Sh[j] : R[j]).push_back(e);
       Nw[j] = new_legs_of(i, open);
       for (int e : Sh[j]) open[e] = 0;
       for (int e : Nw[j]) open[e] = 1;
@@ -1032,7 +1314,7 @@ static tn_status compile_plan(tn_circuit *c, tn_plan *p) {
   }
   auto prod_dims = [&](const std::vector<int> &legs) {
     int64_t x = 1;
-    for (int e : legs) x *= dc_of(c, e);
+    for (int e : legs) x *= c.dc(e);
     return x;
   };
   // pass 2: kernels' parameters; output strides are those of the next step's input layout
@@ -1054,14 +1336,14 @@ static tn_status compile_plan(tn_circuit *c, tn_plan *p) {
       int64_t st = 1;
       for (int q = (int)Lnext.size() - 1; q >= 0; --q) {
         if (Lnext[q] == e) return st;
-        st *= dc_of(c, Lnext[q]);
+        st *= c.dc(Lnext[q]);
       }
       return 0;
     };
     s.n_rest = (int)R[j].size();
     s.rest_pow2 = 1;
     for (size_t r = 0; r < R[j].size(); ++r) {
-      const int64_t d = dc_of(c, R[j][r]);
+      const int64_t d = c.dc(R[j][r]);
       s.rest_dim[r] = (int)d;
       s.rest_ostride[r] = (int)ostride(R[j][r]);
       int lg = 0;
@@ -1073,7 +1355,7 @@ static tn_status compile_plan(tn_circuit *c, tn_plan *p) {
     for (int64_t nn = 0; nn < N; ++nn) {
       int64_t r = nn, off = 0;
       for (int q = (int)Nw[j].size() - 1; q >= 0; --q) {
-        const int64_t d = dc_of(c, Nw[j][q]);
+        const int64_t d = c.dc(Nw[j][q]);
         off += (r % d) * ostride(Nw[j][q]);
         r /= d;
       }
@@ -1091,10 +1373,11 @@ static tn_status compile_plan(tn_circuit *c, tn_plan *p) {
     s.t_sa = push_tab(sa);
     s.t_sb = push_tab(sb);
     std::vector<int64_t> skk, sbb;
-    s.ket_sig = leg_strides(i, c->ket, skk);
-    s.bra_sig = leg_strides(i, c->bra, sbb);
-    s.ket_off = c->ket.node_off[i];
-    s.bra_off = c->bra.node_off[i];
+    s.ket_sig = leg_strides(i, c.dk, skk);
+    s.bra_sig = leg_strides(i, c.db, sbb);
+    s.phys = c.phys[i];
+    s.ket_off = c.ket_off[i];
+    s.bra_off = c.bra_off[i];
     p->steps.push_back(s);
     p->step_mkn.push_back({M, K, N});
     if (j > 0) {
@@ -1119,7 +1402,8 @@ static void fill_info(const tn_plan *p, tn_plan_info *info) {
   if (!info) return;
   std::memset(info, 0, sizeof *info);
   info->n_qubits = p->c->n;
-  info->n_steps = p->c->n - 1;
+  info->n_steps = p->net.n - 1;
+  info->n_nodes = p->net.n;
   info->n_cuts = (int32_t)p->cuts.size();
   info->n_slices = p->n_slices;
   info->score = p->score;
@@ -1140,8 +1424,9 @@ int64_t plan_ws_bytes(const tn_plan *p, int kind, int64_t chunk, int64_t slices)
   const int words = (c->n + 63) / 64;
   int64_t b = 0;
   b += chunk * words * 8;                                   // bits
-  b += chunk * c->bra.item_elems * 16;                      // bra FP64
-  if (kind) b += chunk * c->bra.item_elems * 8;             // bra c64 copy
+  b += chunk * p->net.bra_elems * 16;                       // bra FP64 (with merged nodes)
+  if (kind) b += chunk * p->net.bra_elems * 8;              // bra c64 copy
+  if (p->net.merged()) b += p->net.ket_elems * (kind ? 24 : 16);   // the ket with merged nodes
   b += chunk * std::max<int64_t>(c->bra.max_work, 1) * 16;  // SVD work beyond shared memory
   // ping-pong intermediates (complex64 or three bf16 pieces per real on the complex64 paths)
   b += 2 * chunk * slices * p->maxT * (kind ? 12 : el);
@@ -1156,40 +1441,42 @@ extern "C" tn_status tn_path(tn_circuit *c, const tn_path_opts *opts, tn_plan **
   if (!c->evolved) return tn_fail(TN_ERR_STATE, "tn_path: call tn_evolve_two_sided first");
   tn_path_opts o = opts ? *opts : tn_default_opts();
   const double limit = o.max_intermediate > 0 ? (double)o.max_intermediate : (double)(1LL << 24);
-  std::vector<double> dims(c->ne);
-  for (int e = 0; e < c->ne; ++e) dims[e] = (double)dc_of(c, e);
+  if (o.n_cut_edges > 0 && !o.cut_edges) return tn_fail(TN_ERR_ARG, "tn_path: cut_edges is NULL");
+  std::vector<char> keep(c->ne, 0);   // explicit cut edges stay edges of the network
+  for (int j = 0; j < o.n_cut_edges; ++j) {
+    const int e = o.cut_edges[j];
+    if (e < 0 || e >= c->ne || keep[e]) return tn_fail(TN_ERR_ARG, "tn_path: bad or repeated cut edge %d", e);
+    keep[e] = 1;
+  }
   tn_plan *p = new tn_plan();
   p->c = c;
   p->generation = c->generation;
-  PathGraph pg = make_pg(c->n, c->eu, c->ev, dims);
+  p->net = identity_net(c);
+  if (!o.no_merge) merge_nodes(p->net, keep);
+  const Net &g = p->net;
+  std::vector<double> dims(g.ne);
+  for (int e = 0; e < g.ne; ++e) dims[e] = (double)g.dc(e);
+  PathGraph pg = make_pg(g.n, g.eu, g.ev, dims);
   int64_t pops = 0;
   tn_status s = path_auto(pg, o, p->order, p->score, pops, p->rank_used);
   p->pops = pops;
   if (s != TN_OK) { delete p; return s; }
   // cuts: explicit, counted or automatic (thinnest frontier first), then the path of the cut network
   if (o.n_cut_edges > 0) {
-    if (!o.cut_edges) { delete p; return tn_fail(TN_ERR_ARG, "tn_path: cut_edges is NULL"); }
-    for (int j = 0; j < o.n_cut_edges; ++j) {
-      int e = o.cut_edges[j];
-      if (e < 0 || e >= c->ne || std::find(p->cuts.begin(), p->cuts.end(), e) != p->cuts.end()) {
-        delete p;
-        return tn_fail(TN_ERR_ARG, "tn_path: bad or repeated cut edge %d", e);
-      }
-      p->cuts.push_back(e);
-    }
-  } else {
-    s = choose_cuts(c, o, dims, o.n_cuts, limit, p->cuts, p->order, p->score, p->pops, p->rank_used);
-    if (s != TN_OK) { delete p; return s; }
-  }
-  if (o.n_cut_edges > 0) {   // path of the network with the given cuts
+    for (int j = 0; j < o.n_cut_edges; ++j)
+      for (int e = 0; e < g.ne; ++e)
+        if (g.eid[e] == o.cut_edges[j]) p->cuts.push_back(e);
     std::vector<double> cd2 = dims;
     for (int e : p->cuts) cd2[e] = 1;
-    PathGraph pg2 = make_pg(c->n, c->eu, c->ev, cd2);
+    PathGraph pg2 = make_pg(g.n, g.eu, g.ev, cd2);
     s = path_auto(pg2, o, p->order, p->score, pops, p->rank_used);
     p->pops += pops;
     if (s != TN_OK) { delete p; return s; }
+  } else {
+    s = choose_cuts(g, o, dims, o.n_cuts, limit, p->cuts, p->order, p->score, p->pops, p->rank_used);
+    if (s != TN_OK) { delete p; return s; }
   }
-  s = compile_plan(c, p);
+  s = compile_plan(p);
   if (s != TN_OK) { delete p; return s; }
   const double budget = o.mem_budget_bytes > 0 ? o.mem_budget_bytes : 8.0 * (1ull << 30);
   for (int kind = 0; kind < 2; ++kind) {
@@ -1230,9 +1517,9 @@ extern "C" tn_status tn_path(tn_circuit *c, const tn_path_opts *opts, tn_plan **
 extern "C" tn_status tn_plan_details(const tn_plan *p, int32_t *order, int32_t *cuts, int64_t *steps) {
   if (!p) return tn_fail(TN_ERR_ARG, "tn_plan_details: NULL plan");
   if (order)
-    for (int j = 0; j < p->c->n; ++j) order[j] = p->order[j];
+    for (int j = 0; j < p->c->n; ++j) order[j] = j < p->net.n ? p->net.rep[p->order[j]] : -1;
   if (cuts)
-    for (size_t j = 0; j < p->cuts.size(); ++j) cuts[j] = p->cuts[j];
+    for (size_t j = 0; j < p->cuts.size(); ++j) cuts[j] = p->net.eid[p->cuts[j]];
   if (steps)
     for (size_t j = 1; j < p->step_mkn.size(); ++j)
       for (int t = 0; t < 3; ++t) steps[3 * (j - 1) + t] = p->step_mkn[j][t];
@@ -1252,19 +1539,23 @@ void ws_release(DevMem &mem, Workspace &w) {
   mem.release(w.res);
   mem.release(w.err);
   mem.release(w.cbuf);
+  mem.release(w.ket64);
+  mem.release(w.ket32);
 }
 
-tn_status ws_ensure(tn_plan *p, Workspace &w, int kind, cudaStream_t st) {
+tn_status ws_ensure_sized(tn_plan *p, Workspace &w, int kind, int64_t ch, int64_t sc, cudaStream_t st) {
   tn_circuit *c = p->c;
   DevMem &mem = c->mem;
-  const int64_t ch = p->chunk[kind];
-  const int64_t sc = p->slice_chunk[kind];
   const int words = (c->n + 63) / 64;
   const int64_t el = kind == 0 ? 16 : 8;
   tn_status s;
   if ((s = mem.ensure(w.bits, ch * words * 8, st)) != TN_OK) return s;
-  if ((s = mem.ensure(w.bra64, ch * c->bra.item_elems * 16, st)) != TN_OK) return s;
-  if (kind && (s = mem.ensure(w.bra32, ch * c->bra.item_elems * 8, st)) != TN_OK) return s;
+  if ((s = mem.ensure(w.bra64, ch * p->net.bra_elems * 16, st)) != TN_OK) return s;
+  if (kind && (s = mem.ensure(w.bra32, ch * p->net.bra_elems * 8, st)) != TN_OK) return s;
+  if (p->net.merged()) {
+    if ((s = mem.ensure(w.ket64, p->net.ket_elems * 16, st)) != TN_OK) return s;
+    if (kind && (s = mem.ensure(w.ket32, p->net.ket_elems * 8, st)) != TN_OK) return s;
+  }
   if ((s = mem.ensure(w.gwork, ch * std::max<int64_t>(c->bra.max_work, 1) * 16, st)) != TN_OK) return s;
   const int64_t tel = kind ? 12 : el;
   if ((s = mem.ensure(w.t0, ch * sc * p->maxT * tel, st)) != TN_OK) return s;
@@ -1277,7 +1568,32 @@ tn_status ws_ensure(tn_plan *p, Workspace &w, int kind, cudaStream_t st) {
   return TN_OK;
 }
 
-static bool is_device_ptr(const void *p) {
+tn_status ws_ensure(tn_plan *p, Workspace &w, int kind, cudaStream_t st) {
+  return ws_ensure_sized(p, w, kind, p->chunk[kind], p->slice_chunk[kind], st);
+}
+
+bool step_kernel_ok(const StepParams &s, tn_precision prec, int k) {
+  if (k < SK_TC) return simt_variant_ok(s, k);
+  if (k == SK_TC) return prec != TN_FP64 && prec != TN_FP32 && prec != TN_BF16X6 && tc_step_supported(s);
+  if (!sk_is_tma(k) || k > SK_TMAF64 || (k > SK_TMA64 && k < SK_TMAF)) return false;
+  if (prec != TN_BF16X6 || !tma_step_supported(s)) return false;
+  return sk_tma_bn(k) != 128 || 2 * s.N >= 128;
+}
+
+// The tuned kernels of the plan for this precision, else the shape heuristic: TMA-fed tcgen05 for
+// BF16x6, the in-kernel split tcgen05 kernel for the other tensor-core forms, SIMT elsewhere.
+std::vector<int> step_kernels(const tn_plan *p, tn_precision prec) {
+  const std::vector<int> &t = p->tune[prec];
+  if (t.size() == p->steps.size()) return t;
+  std::vector<int> k(p->steps.size(), SIMT_AUTO);
+  for (size_t j = 1; j < p->steps.size(); ++j) {
+    if (prec == TN_BF16X6 && step_kernel_ok(p->steps[j], prec, SK_TMA)) k[j] = SK_TMA;
+    else if (step_kernel_ok(p->steps[j], prec, SK_TC)) k[j] = SK_TC;
+  }
+  return k;
+}
+
+bool is_device_ptr(const void *p) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
@@ -1286,130 +1602,195 @@ static bool is_device_ptr(const void *p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// The intermediate's output format: bf16 pieces when the consuming step is TMA-fed, else complex.
+static OutDesc out_desc(void *buf, const std::vector<int> &ks, size_t consumer, int64_t plane_u32) {
+  OutDesc o;
+  o.p = buf;
+  o.fmt = (consumer < ks.size() && sk_is_tma(ks[consumer])) ? 1 : 0;
+  o.plane_u32 = plane_u32;
+  return o;
+}
+
+// One contraction step j of a slice group with kernel k, with the overlap formation that kernel
+// needs as a separate pass (tcgen05 paths); SIMT steps form the overlap tensor on the fly.
+cudaError_t enqueue_step(const tn_plan *p, const Workspace &w, size_t j, int k, tn_precision prec,
+                         const ContractArgs &a, const void *ket, const void *bra, const void *tin, void *tout,
+                         const OutDesc &od, cudaStream_t st) {
+  const StepParams &sp = p->steps[j];
+  const int kind = prec == TN_FP64 ? 0 : 1;
+  const double el = kind ? 8.0 : 16.0;
+  const double items = (double)a.items;
+  const double by = el * items * ((double)sp.M * sp.K + (double)sp.M * sp.N);
+  const double fl = 8.0 * items * (double)sp.M * sp.K * sp.N;
+  const int64_t cap = (int64_t)w.chunk * w.slice_chunk;
+  if (prec == TN_FP64) {
+    ProfScope ps("contract_step_fp64", st, by, fl);
+    return launch_step<double>(sp, a, ket, bra, tin, od, st, k);
+  }
+  if (k < SK_TC) {
+    ProfScope ps(prec == TN_FP32 ? "contract_step_fp32" : "contract_step_fp32_tc_fallback", st, by, fl);
+    return launch_step<float>(sp, a, ket, bra, tin, od, st, k);
+  }
+  if (k == SK_TC) {
+    {
+      ProfScope ps("overlap_form_c64", st, 8.0 * items * (double)sp.K * sp.N, 16.0 * items * (double)sp.K * sp.N);
+      cudaError_t e = launch_form_c(sp, a, (const float2 *)ket, (const float2 *)bra, (float2 *)w.cbuf.p, p->maxKN, st);
+      if (e != cudaSuccess) return e;
+    }
+    ProfScope ps("contract_step_tcgen05", st, by + 8.0 * items * (double)sp.K * sp.N, fl);
+    return launch_step_tc((int)prec, sp, a, (const float2 *)w.cbuf.p, p->maxKN, (const float2 *)tin, (float2 *)tout,
+                          (int *)w.err.p + 1, st);
+  }
+  Pieces A, B;
+  A.base = const_cast<void *>(tin);
+  A.item_elems = 2 * p->maxT;
+  A.plane_elems = cap * A.item_elems;
+  B.base = w.cbuf.p;
+  B.item_elems = 4 * p->maxKN;
+  B.plane_elems = cap * B.item_elems;
+  const double out_b = (od.fmt ? 12.0 : 8.0) * (double)sp.M * sp.N;
+  if (!sk_loads_b(k)) {
+    // algorithmic bytes: A pieces read, output written (B is built on chip from the node tensors)
+    ProfScope ps("contract_step_tcgen05_tma", st, items * (12.0 * (double)sp.M * sp.K + out_b), fl);
+    return launch_step_tma(sp, a, A, B, od, (int *)w.err.p + 1, st, sk_tma_bn(k), (const float2 *)ket,
+                           (const float2 *)bra);
+  }
+  {
+    ProfScope ps("overlap_form_bf16_pieces", st, 24.0 * items * (double)sp.K * sp.N, 16.0 * items * (double)sp.K * sp.N);
+    cudaError_t e = launch_form_b_pieces(sp, a, (const float2 *)ket, (const float2 *)bra, B, st);
+    if (e != cudaSuccess) return e;
+  }
+  // algorithmic bytes of the step in its operand format: A and B pieces read, output written
+  ProfScope ps("contract_step_tcgen05_tma_loadb", st, items * (12.0 * (double)sp.M * sp.K + 24.0 * (double)sp.K * sp.N + out_b),
+               fl);
+  return launch_step_tma(sp, a, A, B, od, (int *)w.err.p + 1, st, sk_tma_bn(k));
+}
+
+// Bra evolution and contraction of nb <= w.chunk bitstrings already on the device, amplitudes to
+// res_dev (nb complex128 on the device). Stream-ordered work only (no allocation, no host
+// synchronisation), so it can also be captured into a CUDA graph. The error words in w.err are
+// set, never cleared, here.
+tn_status enqueue_chunk(tn_plan *p, Workspace &w, const uint64_t *bits_dev, int64_t nb, tn_precision prec,
+                        const std::vector<int> &ks, double2 *res_dev, cudaStream_t st, int64_t slice_begin,
+                        int64_t slice_end) {
+  tn_circuit *c = p->c;
+  const int kind = prec == TN_FP64 ? 0 : 1;
+  const int words = (c->n + 63) / 64;
+  const int64_t S = slice_end < 0 ? p->n_slices : std::min<int64_t>(slice_end, p->n_slices);
+  const int64_t S0 = std::max<int64_t>(slice_begin, 0);
+  if (S0 >= S) {   // no slice: the partial sum is zero
+    CUDA_TRY(cudaMemsetAsync(res_dev, 0, nb * sizeof(double2), st));
+    return TN_OK;
+  }
+  const Net &g = p->net;
+  tn_status s = run_half(c->bra, c->n, (double2 *)w.bra64.p, (int)nb, (const int64_t *)c->bra_off_dev.p, bits_dev,
+                         words, (double2 *)w.gwork.p, (int *)w.err.p, st, nullptr, nullptr, g.bra_elems);
+  if (s != TN_OK) return s;
+  if (g.merged()) {
+    // merged nodes: the ket's once per batch (one item), the bra's per bitstring, in FP64
+    CUDA_TRY(cudaMemcpyAsync(w.ket64.p, c->ket_dev.p, c->ket.item_elems * sizeof(double2), cudaMemcpyDeviceToDevice,
+                             st));
+    for (const MergeParams &m : g.mk) {
+      ProfScope ps("merge_nodes_fp64", st, 16.0 * (m.out_size + m.out_size * m.da), 8.0 * m.out_size * m.da);
+      CUDA_TRY(launch_merge(m, (double2 *)w.ket64.p, g.ket_elems, 1, st));
+    }
+    for (const MergeParams &m : g.mb) {
+      ProfScope ps("merge_nodes_fp64", st, 16.0 * nb * (m.out_size + m.out_size * m.da), 8.0 * nb * m.out_size * m.da);
+      CUDA_TRY(launch_merge(m, (double2 *)w.bra64.p, g.bra_elems, nb, st));
+    }
+    if (kind) CUDA_TRY(launch_to_c64((const double2 *)w.ket64.p, (float2 *)w.ket32.p, g.ket_elems, st));
+  }
+  const void *ket = g.merged() ? (kind ? w.ket32.p : w.ket64.p) : (kind ? c->ket_c64.p : c->ket_dev.p);
+  const void *bra = w.bra64.p;
+  if (kind) {
+    ProfScope ps("to_c64", st, 24.0 * nb * g.bra_elems, 0);
+    CUDA_TRY(launch_to_c64((const double2 *)w.bra64.p, (float2 *)w.bra32.p, nb * g.bra_elems, st));
+    bra = w.bra32.p;
+  }
+  const size_t nsteps = p->steps.size();
+  const int64_t cap = (int64_t)w.chunk * w.slice_chunk;     // items the buffers hold
+  for (int64_t s0 = S0; s0 < S; s0 += w.slice_chunk) {
+    const int64_t sg = std::min<int64_t>(w.slice_chunk, S - s0);
+    ContractArgs a;
+    a.tab = (const int32_t *)p->tab_dev.p;
+    a.n_slices = sg;
+    a.slice0 = s0;
+    a.items = nb * sg;
+    a.t_stride = p->maxT;
+    a.bra_stride = g.bra_elems;
+    void *tin = w.t0.p, *tout = w.t1.p;
+    const double el = kind ? 8.0 : 16.0;
+    {
+      ProfScope ps(kind ? "overlap_form_c64" : "overlap_form_c128", st, el * a.items * p->steps[0].N, 0);
+      const OutDesc od = out_desc(tin, ks, 1, cap * p->maxT);
+      if (kind) CUDA_TRY(launch_form<float>(p->steps[0], a, ket, bra, od, st));
+      else CUDA_TRY(launch_form<double>(p->steps[0], a, ket, bra, od, st));
+    }
+    for (size_t j = 1; j < nsteps; ++j) {
+      CUDA_TRY(enqueue_step(p, w, j, ks[j], prec, a, ket, bra, tin, tout,
+                            out_desc(tout, ks, j + 1, cap * p->maxT), st));
+      std::swap(tin, tout);
+    }
+    {
+      ProfScope ps("slice_sum_fp64", st, (el * sg + 16.0) * nb, 0);
+      if (kind) CUDA_TRY(launch_slice_sum<float>(tin, p->maxT, nb, sg, s0 > S0, res_dev, st));
+      else CUDA_TRY(launch_slice_sum<double>(tin, p->maxT, nb, sg, s0 > S0, res_dev, st));
+    }
+  }
+  return TN_OK;
+}
+
+tn_status check_err_words(const int *err) {
+  if (err[0]) return tn_fail(TN_ERR_TIMEOUT, "Jacobi SVD did not converge within its sweep limit (bra half)");
+  if (err[1]) return tn_fail(TN_ERR_TIMEOUT, "tensor-core GEMM: a bounded pipeline wait expired (code %d)", err[1]);
+  return TN_OK;
+}
+
 tn_status run_amplitudes(tn_plan *p, Workspace &w, const uint64_t *bits, int64_t n, tn_precision prec,
-                         tn_c128 *out, cudaStream_t st) {
+                         tn_c128 *out, cudaStream_t st, int64_t slice_begin, int64_t slice_end) {
   tn_circuit *c = p->c;
   if (p->generation != c->generation) return tn_fail(TN_ERR_STATE, "plan is stale: the circuit was re-evolved");
   if (prec < TN_FP64 || prec > TN_TF32X6) return tn_fail(TN_ERR_ARG, "unknown precision %d", (int)prec);
   if (n == 0) return TN_OK;
   if (n < 0 || !bits || !out) return tn_fail(TN_ERR_ARG, "tn_amplitudes: bad arguments");
   const int kind = prec == TN_FP64 ? 0 : 1;
-  tn_status s = ws_ensure(p, w, kind, st);
+  // buffers for min(n, chunk) bitstrings (they grow when a later call needs more)
+  tn_status s = ws_ensure_sized(p, w, kind, std::min<int64_t>(std::max<int64_t>(n, w.chunk), p->chunk[kind]),
+                                p->slice_chunk[kind], st);
   if (s != TN_OK) return s;
   const int words = (c->n + 63) / 64;
   const bool bits_dev = is_device_ptr(bits), out_dev = is_device_ptr(out);
-  const int64_t S = p->n_slices;
+  const std::vector<int> ks = step_kernels(p, prec);
   CUDA_TRY(cudaMemsetAsync(w.err.p, 0, 2 * sizeof(int), st));
   for (int64_t start = 0; start < n; start += w.chunk) {
     const int64_t nb = std::min<int64_t>(w.chunk, n - start);
     CUDA_TRY(cudaMemcpyAsync(w.bits.p, bits + start * words, nb * words * 8,
                              bits_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
-    s = run_half(c->bra, c->n, (double2 *)w.bra64.p, (int)nb, (const int64_t *)c->bra_off_dev.p,
-                 (const uint64_t *)w.bits.p, words, (double2 *)w.gwork.p, (int *)w.err.p, st);
+    s = enqueue_chunk(p, w, (const uint64_t *)w.bits.p, nb, prec, ks, (double2 *)w.res.p, st, slice_begin,
+                      slice_end);
     if (s != TN_OK) return s;
-    const void *ket = kind ? c->ket_c64.p : c->ket_dev.p;
-    const void *bra = w.bra64.p;
-    if (kind) {
-      ProfScope ps("to_c64", st, 24.0 * nb * c->bra.item_elems, 0);
-      CUDA_TRY(launch_to_c64((const double2 *)w.bra64.p, (float2 *)w.bra32.p, nb * c->bra.item_elems, st));
-      bra = w.bra32.p;
-    }
-    // kernel per step: 0 SIMT, 1 tcgen05 with in-kernel operand split, 2 TMA-fed tcgen05 (BF16x6);
-    // a producer writes bf16 pieces when its consumer is a TMA step, else complex64
-    const size_t nsteps = p->steps.size();
-    std::vector<int> path(nsteps, 0);
-    for (size_t j = 1; j < nsteps; ++j) {
-      const StepParams &sp = p->steps[j];
-      if (prec == TN_BF16X6) path[j] = tma_step_supported(sp) ? 2 : 0;
-      else if (prec != TN_FP64 && prec != TN_FP32) path[j] = tc_step_supported(sp) ? 1 : 0;
-    }
-    const int64_t cap = (int64_t)w.chunk * w.slice_chunk;     // items the buffers hold
-    for (int64_t s0 = 0; s0 < S; s0 += w.slice_chunk) {
-      const int64_t sg = std::min<int64_t>(w.slice_chunk, S - s0);
-      ContractArgs a;
-      a.tab = (const int32_t *)p->tab_dev.p;
-      a.n_slices = sg;
-      a.slice0 = s0;
-      a.items = nb * sg;
-      a.t_stride = p->maxT;
-      a.bra_stride = c->bra.item_elems;
-      void *tin = w.t0.p, *tout = w.t1.p;
-      const double el = kind ? 8.0 : 16.0;
-      auto out_for = [&](void *buf, size_t consumer) {
-        OutDesc o;
-        o.p = buf;
-        o.fmt = (consumer < nsteps && path[consumer] == 2) ? 1 : 0;
-        o.plane_u32 = cap * p->maxT;
-        return o;
-      };
-      {
-        ProfScope ps(kind ? "overlap_form_c64" : "overlap_form_c128", st, el * a.items * p->steps[0].N, 0);
-        if (kind) CUDA_TRY(launch_form<float>(p->steps[0], a, ket, bra, out_for(tin, 1), st));
-        else CUDA_TRY(launch_form<double>(p->steps[0], a, ket, bra, out_for(tin, 1), st));
-      }
-      for (size_t j = 1; j < nsteps; ++j) {
-        const StepParams &sp = p->steps[j];
-        const double items = (double)a.items;
-        const double by = el * items * ((double)sp.M * sp.K + (double)sp.M * sp.N);
-        const double fl = 8.0 * items * (double)sp.M * sp.K * sp.N;
-        const OutDesc od = out_for(tout, j + 1);
-        if (prec == TN_FP64) {
-          ProfScope ps("contract_step_fp64", st, by, fl);
-          CUDA_TRY(launch_step<double>(sp, a, ket, bra, tin, od, st));
-        } else if (path[j] == 0) {
-          ProfScope ps(prec == TN_FP32 ? "contract_step_fp32" : "contract_step_fp32_tc_fallback", st, by, fl);
-          CUDA_TRY(launch_step<float>(sp, a, ket, bra, tin, od, st));
-        } else if (path[j] == 1) {
-          {
-            ProfScope ps("overlap_form_c64", st, 8.0 * items * (double)sp.K * sp.N, 16.0 * items * (double)sp.K * sp.N);
-            CUDA_TRY(launch_form_c(sp, a, (const float2 *)ket, (const float2 *)bra, (float2 *)w.cbuf.p, p->maxKN, st));
-          }
-          ProfScope ps("contract_step_tcgen05", st, by + 8.0 * items * (double)sp.K * sp.N, fl);
-          CUDA_TRY(launch_step_tc((int)prec, sp, a, (const float2 *)w.cbuf.p, p->maxKN, (const float2 *)tin,
-                                  (float2 *)tout, (int *)w.err.p + 1, st));
-        } else {
-          Pieces B;
-          B.base = w.cbuf.p;
-          B.item_elems = 4 * p->maxKN;
-          B.plane_elems = cap * B.item_elems;
-          {
-            ProfScope ps("overlap_form_bf16_pieces", st, 24.0 * items * (double)sp.K * sp.N,
-                         16.0 * items * (double)sp.K * sp.N);
-            CUDA_TRY(launch_form_b_pieces(sp, a, (const float2 *)ket, (const float2 *)bra, B, st));
-          }
-          Pieces A;
-          A.base = tin;
-          A.item_elems = 2 * p->maxT;
-          A.plane_elems = cap * A.item_elems;
-          // algorithmic bytes of the step in its operand format: A and B pieces read, output written
-          const double byp = items * (12.0 * (double)sp.M * sp.K + 24.0 * (double)sp.K * sp.N +
-                                      (od.fmt ? 12.0 : 8.0) * (double)sp.M * sp.N);
-          ProfScope ps("contract_step_tcgen05_tma", st, byp, fl);
-          CUDA_TRY(launch_step_tma(sp, a, A, B, od, (int *)w.err.p + 1, st));
-        }
-        std::swap(tin, tout);
-      }
-      {
-        ProfScope ps("slice_sum_fp64", st, (el * sg + 16.0) * nb, 0);
-        if (kind) CUDA_TRY(launch_slice_sum<float>(tin, p->maxT, nb, sg, s0 > 0, (double2 *)w.res.p, st));
-        else CUDA_TRY(launch_slice_sum<double>(tin, p->maxT, nb, sg, s0 > 0, (double2 *)w.res.p, st));
-      }
-    }
     CUDA_TRY(cudaMemcpyAsync(out + start, w.res.p, nb * sizeof(tn_c128),
                              out_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
   }
   int err[2] = {0, 0};
   CUDA_TRY(cudaMemcpyAsync(err, w.err.p, sizeof err, cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaStreamSynchronize(st));
-  if (err[0]) return tn_fail(TN_ERR_TIMEOUT, "Jacobi SVD did not converge within its sweep limit (bra half)");
-  if (err[1]) return tn_fail(TN_ERR_TIMEOUT, "tensor-core GEMM: a bounded pipeline wait expired (code %d)", err[1]);
-  return TN_OK;
+  return check_err_words(err);
 }
 
 extern "C" tn_status tn_amplitudes(tn_plan *p, const uint64_t *bits, int64_t n, tn_precision prec, tn_c128 *out,
                                    void *cuda_stream) {
   if (!p) return tn_fail(TN_ERR_ARG, "tn_amplitudes: NULL plan");
   return run_amplitudes(p, p->ws, bits, n, prec, out, (cudaStream_t)cuda_stream);
+}
+
+extern "C" tn_status tn_amplitudes_slices(tn_plan *p, const uint64_t *bits, int64_t n, tn_precision prec,
+                                          int64_t slice_begin, int64_t slice_end, tn_c128 *out, void *cuda_stream) {
+  if (!p) return tn_fail(TN_ERR_ARG, "tn_amplitudes_slices: NULL plan");
+  if (slice_begin < 0 || slice_end < slice_begin || slice_end > p->n_slices)
+    return tn_fail(TN_ERR_ARG, "tn_amplitudes_slices: slice range [%lld, %lld) outside [0, %lld)",
+                   (long long)slice_begin, (long long)slice_end, (long long)p->n_slices);
+  return run_amplitudes(p, p->ws, bits, n, prec, out, (cudaStream_t)cuda_stream, slice_begin, slice_end);
 }
 
 extern "C" void tn_plan_free(tn_plan *p) {

@@ -47,7 +47,7 @@ size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
 // Byte sizes of the workspace buffers for `ch` bitstrings of `sc` slices each (the sizes the
 // workspace set-up asks for; each buffer is given exactly that capacity below).
 struct Sizes {
-  size_t bits, bra64, bra32, gwork, t, cbuf, res, err, total;
+  size_t bits, bra64, bra32, gwork, t, cbuf, res, err, ket64, ket32, total;
 };
 
 Sizes sizes_for(const tn_plan *p, int kind, int64_t ch, int64_t sc) {
@@ -56,15 +56,17 @@ Sizes sizes_for(const tn_plan *p, int kind, int64_t ch, int64_t sc) {
   const int64_t tel = kind ? 12 : 16;
   Sizes z;
   z.bits = (size_t)(ch * words * 8);
-  z.bra64 = (size_t)(ch * c->bra.item_elems * 16);
-  z.bra32 = kind ? (size_t)(ch * c->bra.item_elems * 8) : 0;
+  z.bra64 = (size_t)(ch * p->net.bra_elems * 16);
+  z.bra32 = kind ? (size_t)(ch * p->net.bra_elems * 8) : 0;
+  z.ket64 = p->net.merged() ? (size_t)(p->net.ket_elems * 16) : 0;
+  z.ket32 = p->net.merged() && kind ? (size_t)(p->net.ket_elems * 8) : 0;
   z.gwork = (size_t)(ch * std::max<int64_t>(c->bra.max_work, 1) * 16);
   z.t = (size_t)(ch * sc * p->maxT * tel);
   z.cbuf = kind ? (size_t)(ch * sc * p->maxKN * 24) : 0;
   z.res = (size_t)(ch * 16);
   z.err = 64;
   z.total = up256(z.bits) + up256(z.bra64) + up256(z.bra32) + up256(z.gwork) + 2 * up256(z.t) + up256(z.cbuf) +
-            up256(z.res) + up256(z.err);
+            up256(z.res) + up256(z.err) + up256(z.ket64) + up256(z.ket32);
   return z;
 }
 
@@ -133,6 +135,8 @@ extern "C" tn_status tn_amplitudes_static(tn_plan *p, const uint64_t *bits, int6
   carve(q.ws.cbuf, z.cbuf);
   carve(q.ws.res, z.res);
   carve(q.ws.err, z.err);
+  carve(q.ws.ket64, z.ket64);
+  carve(q.ws.ket32, z.ket32);
   // the error words are cleared by the run itself; every other buffer is written before read
   return run_amplitudes(&q, q.ws, bits, n, prec, out, (cudaStream_t)cuda_stream);
 }

@@ -100,12 +100,6 @@ __device__ __forceinline__ float bf16_rn(float x) {   // round to the nearest bf
   return __uint_as_float(r);
 }
 
-__device__ __forceinline__ float2 cfma2(float2 a, float2 b, float2 c) {
-  c.x = fmaf(a.x, b.x, fmaf(-a.y, b.y, c.x));
-  c.y = fmaf(a.x, b.y, fmaf(a.y, b.x, c.y));
-  return c;
-}
-
 // Operand kinds: tf32 (4-byte elements, MMA K = 8) or bf16 (2-byte elements, MMA K = 16).
 // A stage row is always 128 bytes (one 128B swizzle row), i.e. BKR = 32 tf32 or 64 bf16 reals.
 template <int KIND> struct Op;
@@ -368,13 +362,10 @@ cudaError_t launch_bn(const StepParams &s, const ContractArgs &a, const float2 *
   constexpr size_t stage = (size_t)P * (BM * 128 + BN * 128);
   const size_t smem = 2 * stage + 1024;
   static_assert(2 * (size_t)P * (BM * 128 + BN * 128) + 1024 <= 227 * 1024, "shared memory");
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(tc_step_kernel<KIND, P, ORD, BN, R>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  // once per instantiation (a function-local static is initialised by one thread)
+  static const cudaError_t attr = cudaFuncSetAttribute(tc_step_kernel<KIND, P, ORD, BN, R>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (attr != cudaSuccess) return attr;
   const int64_t tiles = ((s.M + BM - 1) / BM) * ((2 * s.N + BN - 1) / BN);
   const int64_t grid = tiles * a.items;
   if (grid <= 0) return cudaSuccess;

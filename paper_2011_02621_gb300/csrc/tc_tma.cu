@@ -16,6 +16,12 @@
 //   warps 2-5 wait for "done", read the accumulators with tcgen05.ld, add them smallest first
 //            and write the result straight into the next step's layout, as complex64 or as
 //            bf16 pieces for the next tensor-core step.
+// In the building mode (BUILD) no overlap tensor is stored at all: during the main loop warps 2-5
+// compute each stage's B tile themselves from the absorbed node's ket and bra tensors (Eq.
+// overlap, the same arithmetic as the formation kernel), split it into the three bf16 pieces and
+// store it in the 128-byte-swizzled K-major layout the MMA reads; each of those 128 threads then
+// makes its writes visible to the tensor core's async proxy and arrives on the stage's "full"
+// mbarrier next to the TMA's byte count. Only the A pieces come from memory.
 // Every wait is bounded by a clock limit and raises an error code instead of hanging.
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -96,6 +102,22 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t ad, uint64_t bd
       : "memory");
 }
 
+__device__ __forceinline__ void bar_arrive(uint32_t a) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
+}
+
+__device__ __forceinline__ void sts128(uint32_t a, const uint32_t w[4]) {
+  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3])
+               : "memory");
+}
+
+// byte offset of 16-byte chunk c of row r in a 128-byte-swizzled K-major tile (1024-byte aligned):
+// rows of 128 bytes, groups of 8 rows, chunk index XOR (row mod 8) -- the layout TMA writes with
+// CU_TENSOR_MAP_SWIZZLE_128B and the MMA descriptor reads with layout type SWIZZLE_128B
+__device__ __forceinline__ uint32_t sw128_off(int r, int c) {
+  return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((c ^ (r & 7)) << 4));
+}
+
 __device__ __forceinline__ void mma_commit_to(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
@@ -104,12 +126,12 @@ __device__ __forceinline__ void mma_commit_to(uint32_t bar) {
 
 namespace {
 
-template <int BN, int R, int S>
+template <int BN, int R, int S, bool BUILD>
 __global__ void __launch_bounds__(T_THREADS, 1)
 tma_step_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMap tA1,
                 const __grid_constant__ CUtensorMap tA2, const __grid_constant__ CUtensorMap tB0,
                 const __grid_constant__ CUtensorMap tB1, const __grid_constant__ CUtensorMap tB2, StepParams s,
-                ContractArgs a, OutDesc out, int *err) {
+                ContractArgs a, OutDesc out, int *err, const float2 *ket, const float2 *bra) {
   constexpr int A_BYTES = T_BM * 128, B_BYTES = BN * 128;
   constexpr int STAGE = T_P * (A_BYTES + B_BYTES);
   constexpr int GROUPS = R + 2;
@@ -133,7 +155,7 @@ tma_step_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__
 
   if (tid == 0) {
     for (int i = 0; i < S; ++i) {
-      bar_init(s_u32(&full[i]), 1);
+      bar_init(s_u32(&full[i]), BUILD ? 1 + 4 * 32 : 1);   // TMA (+ the 128 B builders)
       bar_init(s_u32(&empty[i]), 1);
     }
     bar_init(s_u32(&done), 1);
@@ -181,11 +203,12 @@ tma_step_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__
         const uint32_t it = (uint32_t)(kc / S);
         if (kc >= S && !bar_wait(s_u32(&empty[st]), (it - 1) & 1, err, 11)) break;
         uint8_t *base = smem + st * STAGE;
-        bar_expect_tx(s_u32(&full[st]), (uint32_t)STAGE);
+        bar_expect_tx(s_u32(&full[st]), (uint32_t)(BUILD ? T_P * A_BYTES : STAGE));
         for (int q = 0; q < T_P; ++q)
           tma_3d(s_u32(base + q * A_BYTES), mA[q], (int)(kc * 64), m0, item, s_u32(&full[st]));
-        for (int q = 0; q < T_P; ++q)
-          tma_3d(s_u32(base + T_P * A_BYTES + q * B_BYTES), mB[q], (int)(kc * 64), nr0, item, s_u32(&full[st]));
+        if (!BUILD)
+          for (int q = 0; q < T_P; ++q)
+            tma_3d(s_u32(base + T_P * A_BYTES + q * B_BYTES), mB[q], (int)(kc * 64), nr0, item, s_u32(&full[st]));
         ++issued;
       }
       if (issued > 0) {   // the last loads must have landed before the CTA may exit
@@ -225,6 +248,58 @@ tma_step_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__
       mma_commit_to(s_u32(&done));               // after every issued MMA, also on an early stop
     }
   } else {
+    if (BUILD) {
+      // ---------------- B builders (warps 2..5): stage kc's B tile, real rows nr0 .. nr0 + BN - 1
+      // (complex column n = row / 2; row 2n = (Re c, -Im c), row 2n + 1 = (Im c, Re c) along k),
+      // reals kc*64 .. kc*64 + 63 (complex k = kc*32 .. kc*32 + 31); zeros outside K and N
+      const int bt = tid - 64;
+      const ItemCtx c = item_ctx(a, s, item);
+      const float2 *kp = ket + s.ket_off + c.sa;
+      const float2 *bp = bra + c.b * a.bra_stride + s.bra_off + c.sb;
+      const int32_t *bka = a.tab + s.t_bka, *bkb = a.tab + s.t_bkb;
+      const int32_t *bna = a.tab + s.t_bna, *bnb = a.tab + s.t_bnb;
+      const int64_t n_base = nr0 >> 1;
+      for (int64_t kc = 0; kc < nk; ++kc) {
+        const int st = (int)(kc % S);
+        const uint32_t it = (uint32_t)(kc / S);
+        if (kc >= S && !bar_wait(s_u32(&empty[st]), (it - 1) & 1, err, 15)) break;
+        const uint32_t bbase = s_u32(smem + st * STAGE + T_P * A_BYTES);
+        for (int t = bt; t < (BN / 2) * 8; t += 128) {
+          const int c16 = t & 7, nl = t >> 3;        // 16-byte chunk = four complex k; complex column
+          const int64_t n = n_base + nl;
+          const int64_t k0 = kc * 32 + c16 * 4;
+          int64_t ia_n = 0, ib_n = 0;
+          if (n < s.N) {
+            ia_n = bna[n];
+            ib_n = bnb[n];
+          }
+          uint32_t w0[T_P][4], w1[T_P][4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int64_t k = k0 + i;
+            float2 v = make_float2(0.f, 0.f);
+            if (n < s.N && k < s.K)
+              v = overlap_elem(kp, bp, (int64_t)bka[k] + ia_n, (int64_t)bkb[k] + ib_n, s.ket_sig, s.bra_sig, s.phys);
+            uint32_t t0[T_P], t1[T_P];
+            tn_split3(v.x, -v.y, t0);
+            tn_split3(v.y, v.x, t1);
+#pragma unroll
+            for (int q = 0; q < T_P; ++q) {
+              w0[q][i] = t0[q];
+              w1[q][i] = t1[q];
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < T_P; ++q) {
+            sts128(bbase + q * B_BYTES + sw128_off(2 * nl, c16), w0[q]);
+            sts128(bbase + q * B_BYTES + sw128_off(2 * nl + 1, c16), w1[q]);
+          }
+        }
+        // generic-proxy writes -> visible to the tensor core (async proxy), then arrive
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        bar_arrive(s_u32(&full[st]));
+      }
+    }
     // ---------------- epilogue (warps 2..5 -> TMEM lane groups 2, 3, 0, 1)
     const bool ok = bar_wait(s_u32(&done), 0u, err, 14);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -305,34 +380,34 @@ bool make_map(CUtensorMap *m, const void *base, uint64_t inner, uint64_t rows, u
   return r == CUDA_SUCCESS;
 }
 
-template <int BN, int R, int S>
+template <int BN, int R, int S, bool BUILD>
 cudaError_t launch_t(const StepParams &s, const ContractArgs &a, const Pieces &A, const Pieces &B, const OutDesc &out,
-                     int *err, cudaStream_t st) {
+                     int *err, const float2 *ket, const float2 *bra, cudaStream_t st) {
   constexpr size_t stage = (size_t)T_P * (T_BM * 128 + BN * 128);
   const size_t smem = S * stage + 1024;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(tma_step_kernel<BN, R, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  // once per instantiation (a function-local static is initialised by one thread)
+  static const cudaError_t attr = cudaFuncSetAttribute(tma_step_kernel<BN, R, S, BUILD>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (attr != cudaSuccess) return attr;
   CUtensorMap mA[3], mB[3];
   const uint64_t K2 = (uint64_t)(2 * s.K), N2 = (uint64_t)(2 * s.N);
   for (int q = 0; q < T_P; ++q) {
     if (!make_map(&mA[q], (const uint16_t *)A.base + q * A.plane_elems, K2, (uint64_t)s.M, (uint64_t)a.items, K2 * 2,
                   (uint64_t)A.item_elems * 2, T_BM))
       return cudaErrorInvalidValue;
-    if (!make_map(&mB[q], (const uint16_t *)B.base + q * B.plane_elems, K2, N2, (uint64_t)a.items, K2 * 2,
-                  (uint64_t)B.item_elems * 2, BN))
+    if (BUILD) {
+      mB[q] = mA[q];   // unused: B is built in shared memory
+    } else if (!make_map(&mB[q], (const uint16_t *)B.base + q * B.plane_elems, K2, N2, (uint64_t)a.items, K2 * 2,
+                         (uint64_t)B.item_elems * 2, BN)) {
       return cudaErrorInvalidValue;
+    }
   }
   const int64_t tiles = ((s.M + T_BM - 1) / T_BM) * ((2 * s.N + BN - 1) / BN);
   const int64_t grid = tiles * a.items;
   if (grid <= 0) return cudaSuccess;
   if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-  tma_step_kernel<BN, R, S><<<(unsigned)grid, T_THREADS, smem, st>>>(mA[0], mA[1], mA[2], mB[0], mB[1], mB[2], s, a,
-                                                                     out, err);
+  tma_step_kernel<BN, R, S, BUILD><<<(unsigned)grid, T_THREADS, smem, st>>>(mA[0], mA[1], mA[2], mB[0], mB[1], mB[2],
+                                                                            s, a, out, err, ket, bra);
   tn_count_launch(1);
   return cudaGetLastError();
 }
@@ -345,7 +420,16 @@ bool tma_step_supported(const StepParams &s) {
 }
 
 cudaError_t launch_step_tma(const StepParams &s, const ContractArgs &a, const Pieces &A, const Pieces &B,
-                            const OutDesc &out, int *err, cudaStream_t st) {
-  if (2 * s.N >= 128) return launch_t<128, 2, 2>(s, a, A, B, out, err, st);
-  return launch_t<64, 6, 3>(s, a, A, B, out, err, st);
+                            const OutDesc &out, int *err, cudaStream_t st, int bn, const float2 *ket,
+                            const float2 *bra) {
+  if (bn == 0) bn = 2 * s.N >= 128 ? 128 : 64;
+  const bool build = ket != nullptr;
+  if (build && !bra) return cudaErrorInvalidValue;
+  if (bn == 128 && 2 * s.N >= 128)
+    return build ? launch_t<128, 2, 2, true>(s, a, A, B, out, err, ket, bra, st)
+                 : launch_t<128, 2, 2, false>(s, a, A, B, out, err, ket, bra, st);
+  if (bn == 64)
+    return build ? launch_t<64, 6, 3, true>(s, a, A, B, out, err, ket, bra, st)
+                 : launch_t<64, 6, 3, false>(s, a, A, B, out, err, ket, bra, st);
+  return cudaErrorInvalidValue;
 }

@@ -124,3 +124,61 @@ __device__ __forceinline__ void store_out4(const OutDesc &o, int64_t t_stride, i
 #pragma unroll
   for (int j = 0; j < 4; ++j) b[j] = make_double2(v[2 * j], v[2 * j + 1]);
 }
+
+// ---- overlap elements and item context (shared by the formation, SIMT and TMA kernels)
+
+template <typename V> __device__ __forceinline__ V cz() { V v; v.x = 0; v.y = 0; return v; }
+template <typename V> __device__ __forceinline__ V cfma(V a, V b, V c) {
+  c.x = fma(a.x, b.x, fma(-a.y, b.y, c.x));
+  c.y = fma(a.x, b.y, fma(a.y, b.x, c.y));
+  return c;
+}
+
+struct ItemCtx {
+  int64_t b, sl;
+  int32_t sa, sb;
+};
+
+__device__ __forceinline__ ItemCtx item_ctx(const ContractArgs &a, const StepParams &s, int64_t item) {
+  ItemCtx c;
+  if (a.n_slices == 1) {
+    c.b = item;
+    c.sl = a.slice0;
+  } else {
+    c.b = (unsigned)item / (unsigned)a.n_slices;
+    c.sl = a.slice0 + (unsigned)item % (unsigned)a.n_slices;
+  }
+  c.sa = a.tab[s.t_sa + c.sl];
+  c.sb = a.tab[s.t_sb + c.sl];
+  return c;
+}
+
+// output offset of row m: m decomposed over the rest legs, weighted by their output strides
+__device__ __forceinline__ int orow_of(const StepParams &s, int64_t m64) {
+  unsigned m = (unsigned)m64;   // rows < 2^31 (checked when the plan is compiled)
+  int off = 0;
+  if (s.rest_pow2) {
+    for (int j = s.n_rest - 1; j >= 0; --j) {
+      const int lg = s.rest_log2[j];
+      off += (int)(m & ((1u << lg) - 1u)) * s.rest_ostride[j];
+      m >>= lg;
+    }
+  } else {
+    for (int j = s.n_rest - 1; j >= 0; --j) {
+      const unsigned d = (unsigned)s.rest_dim[j];
+      off += (int)(m % d) * s.rest_ostride[j];
+      m /= d;
+    }
+  }
+  return off;
+}
+
+// C element (Eq. overlap) at table offsets: the sum over the node's physical index (two values,
+// or 4 / 8 for a node that absorbed neighbours), in index order
+template <typename V>
+__device__ __forceinline__ V overlap_elem(const V *ket, const V *bra, int64_t ia, int64_t ib, int64_t ksig,
+                                          int64_t bsig, int64_t phys) {
+  V acc = cfma(ket[ia + ksig], bra[ib + bsig], cfma(ket[ia], bra[ib], cz<V>()));
+  for (int64_t q = 2; q < phys; ++q) acc = cfma(ket[ia + q * ksig], bra[ib + q * bsig], acc);
+  return acc;
+}

@@ -9,6 +9,13 @@
 
 tn_status tn_fail(tn_status s, const char *fmt, ...);
 
+// return TN_ERR_CUDA with the failing call's text from a function returning tn_status
+#define CUDA_TRY(x)                                                                           \
+  do {                                                                                        \
+    cudaError_t e_ = (x);                                                                     \
+    if (e_ != cudaSuccess) return tn_fail(TN_ERR_CUDA, "%s: %s", #x, cudaGetErrorString(e_)); \
+  } while (0)
+
 struct Buf {
   void *p = nullptr;
   size_t bytes = 0;
@@ -58,6 +65,26 @@ struct Workspace {
   int chunk = 0;
   int64_t slice_chunk = 1;
   Buf bits, bra64, bra32, gwork, t0, t1, res, err, cbuf;
+  Buf ket64, ket32;                               // the ket with merged nodes (plans that merge)
+};
+
+// The overlap network a plan contracts: one node per qubit, or fewer when boundary nodes were
+// merged into a neighbour (exactly, on both halves, before the contraction). Edge ids are the
+// network's own; eid maps them to the circuit's edge ids. A node tensor is [p][legs in order],
+// p its physical index (phys values), stored in the ket item (one) and in every bitstring's bra
+// item at the node's offsets; merged nodes live past the halves' own slots.
+struct Net {
+  int n = 0, ne = 0;
+  std::vector<int> eu, ev, eid;
+  std::vector<std::vector<int>> legs;             // per node, network edge ids in tensor order
+  std::vector<int> rep;                           // representative qubit per node
+  std::vector<int> phys;                          // physical values per node
+  std::vector<int64_t> dk, db;                    // ket / bra dim per network edge
+  std::vector<int64_t> ket_off, bra_off;          // node offsets in the ket / bra item
+  int64_t ket_elems = 0, bra_elems = 0;           // item sizes including merged nodes
+  std::vector<MergeParams> mk, mb;                // merge program of the ket / bra, in order
+  int64_t dc(int e) const { return dk[e] * db[e]; }
+  bool merged() const { return !mk.empty(); }
 };
 
 struct tn_plan {
@@ -79,16 +106,40 @@ struct tn_plan {
   int64_t slice_chunk[2] = {1, 1};                // slices per launch group (all S when chunk > 1)
   int64_t ws_bytes[2] = {0, 0};
   Workspace ws;
+  Net net;                                        // nodes, legs and layouts the steps address
+  std::vector<int> tune[TN_TF32X6 + 1];           // per precision: a StepKernel per step (empty: heuristic)
 };
+
+// Kernel of one contraction step: a SimtVariant (SIMT, complex FMA), tcgen05 with the operand split in
+// the kernel, or TMA-fed tcgen05 (BF16x6) with a shape-picked or fixed tile width, building the
+// overlap operand in shared memory (SK_TMA*) or loading it after a formation pass (SK_TMAF*).
+enum StepKernel { SK_TC = 16, SK_TMA = 32, SK_TMA128 = 33, SK_TMA64 = 34, SK_TMAF = 40, SK_TMAF128 = 41, SK_TMAF64 = 42 };
+inline bool sk_is_tma(int k) { return k >= SK_TMA; }
+inline bool sk_loads_b(int k) { return k >= SK_TMAF; }
+inline int sk_tma_bn(int k) { return (k == SK_TMA128 || k == SK_TMAF128) ? 128 : (k == SK_TMA64 || k == SK_TMAF64) ? 64 : 0; }
+std::vector<int> step_kernels(const tn_plan *p, tn_precision prec);
+bool step_kernel_ok(const StepParams &s, tn_precision prec, int k);
 
 tn_path_opts tn_default_opts();
 int64_t plan_ws_bytes(const tn_plan *p, int kind, int64_t chunk, int64_t slices);
 tn_status ws_ensure(tn_plan *p, Workspace &w, int kind, cudaStream_t st);
+tn_status ws_ensure_sized(tn_plan *p, Workspace &w, int kind, int64_t chunk, int64_t slices, cudaStream_t st);
+bool is_device_ptr(const void *p);
+// one contraction step j with kernel k (with the overlap formation that kernel needs); no host sync
+cudaError_t enqueue_step(const tn_plan *p, const Workspace &w, size_t j, int k, tn_precision prec,
+                         const ContractArgs &a, const void *ket, const void *bra, const void *tin, void *tout,
+                         const OutDesc &od, cudaStream_t st);
+tn_status check_err_words(const int *err);   // the two error words of a workspace, read on the host
+tn_status enqueue_chunk(tn_plan *p, Workspace &w, const uint64_t *bits_dev, int64_t nb, tn_precision prec,
+                        const std::vector<int> &ks, double2 *res_dev, cudaStream_t st, int64_t slice_begin = 0,
+                        int64_t slice_end = -1);
 void ws_release(DevMem &mem, Workspace &w);
+// amplitudes, or with a slice range the FP64 partial sums over slices [slice_begin, slice_end)
 tn_status run_amplitudes(tn_plan *p, Workspace &w, const uint64_t *bits, int64_t n, tn_precision prec,
-                         tn_c128 *out, cudaStream_t st);
+                         tn_c128 *out, cudaStream_t st, int64_t slice_begin = 0, int64_t slice_end = -1);
 tn_status run_half(const Half &h, int n_qubits, double2 *base, int items, const int64_t *node_off_dev,
-                   const uint64_t *bits_dev, int words, double2 *gwork, int *errflag, cudaStream_t st);
+                   const uint64_t *bits_dev, int words, double2 *gwork, int *errflag, cudaStream_t st,
+                   int *rank_out_dev, const double2 *init_vec_dev, int64_t item_stride = 0);
 
 // tracing: events around launches, attributed to a kernel kind
 struct ProfScope {

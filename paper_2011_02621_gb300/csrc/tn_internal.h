@@ -42,11 +42,28 @@ struct Apply1Params {
 int64_t gate_work_elems(const GateParams &g);
 
 cudaError_t launch_init_product(double2 *base, int64_t item_stride, int items, const int64_t *node_off_dev,
-                                int n_qubits, const uint64_t *bits, int words, cudaStream_t st);
+                                int n_qubits, const uint64_t *bits, int words, const double2 *init_vec,
+                                cudaStream_t st);
+// rank_out (nullable): item 0 writes the numerical rank of its SVD there
 cudaError_t launch_gate(const GateParams &g, double2 *base, int64_t item_stride, int items,
-                        double2 *gwork, int *errflag, cudaStream_t st);
+                        double2 *gwork, int *errflag, int *rank_out, cudaStream_t st);
 cudaError_t launch_apply1(const Apply1Params &a, double2 *base, int64_t item_stride, int items, cudaStream_t st);
 cudaError_t launch_to_c64(const double2 *src, float2 *dst, int64_t n, cudaStream_t st);
+
+// Merging node v into its neighbour u through their shared edge a, on one half (ket or bra), in
+// FP64 and exactly: out[p_u, p_v, legs_u \ a, legs_v \ a] = sum_a U[p_u, legs_u] V[p_v, legs_v].
+// Element offsets are within one item's region; the rest legs are listed in output order.
+#define TN_MAXMLEGS 8
+struct MergeParams {
+  int64_t u_off, v_off, out_off, out_size;
+  int64_t su_p, sv_p;                   // physical-index strides in U and V
+  int64_t su_a, sv_a;                   // strides of the shared leg a in U and V
+  int pu, pv, da;                       // physical values of U and V, dim of a on this half
+  int nu, nv;                           // rest legs of U and V
+  int du[TN_MAXMLEGS], dv[TN_MAXMLEGS]; // their dims
+  int64_t su[TN_MAXMLEGS], sv[TN_MAXMLEGS];   // their strides in U and V
+};
+cudaError_t launch_merge(const MergeParams &m, double2 *base, int64_t item_stride, int64_t items, cudaStream_t st);
 cudaError_t launch_pack_bits(const uint64_t *src, uint64_t *dst, int64_t n_words, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
@@ -66,8 +83,9 @@ struct StepParams {
   int rest_dim[TN_MAXREST];     // rest legs of step j, slowest first
   int rest_log2[TN_MAXREST];    // log2 of the dims when rest_pow2
   int rest_ostride[TN_MAXREST]; // their strides in the output layout
-  int64_t ket_off, ket_sig;     // node tensor offset / sigma stride in the ket buffer
+  int64_t ket_off, ket_sig;     // node tensor offset / physical-index stride in the ket buffer
   int64_t bra_off, bra_sig;     // same in one bitstring's bra region
+  int64_t phys;                 // values of the node's physical index (2; 4 or 8 for merged nodes)
   // offsets of the int32 tables in the plan's table buffer
   int64_t t_ocol, t_bka, t_bkb, t_bna, t_bnb, t_sa, t_sb;
 };
@@ -104,7 +122,11 @@ cudaError_t launch_form(const StepParams &s, const ContractArgs &a, const void *
                         const OutDesc &out, cudaStream_t st);
 template <typename R>
 cudaError_t launch_step(const StepParams &s, const ContractArgs &a, const void *ket, const void *bra,
-                        const void *t_in, const OutDesc &out, cudaStream_t st);
+                        const void *t_in, const OutDesc &out, cudaStream_t st, int variant = 0);
+// SIMT step kernels: the shape heuristic or one kernel forced (the autotuner's candidates)
+enum SimtVariant { SIMT_AUTO = 0, SIMT_T64 = 1, SIMT_T128 = 2, SIMT_T256 = 3, SIMT_STREAM = 4, SIMT_FIXED = 5,
+                   SIMT_SMALL = 6 };
+bool simt_variant_ok(const StepParams &s, int variant);
 // out[b] (+)= sum over the group's slices, in slice order, in FP64 (accumulate: add to out)
 template <typename R>
 cudaError_t launch_slice_sum(const void *res, int64_t items_stride, int64_t n_bits, int64_t n_slices,
@@ -121,8 +143,12 @@ bool tc_step_supported(const StepParams &s);
 cudaError_t launch_form_b_pieces(const StepParams &s, const ContractArgs &a, const float2 *ket, const float2 *bra,
                                  const Pieces &B, cudaStream_t st);
 // TMA-fed tcgen05 step (BF16x6) from pre-split A and B pieces
+// bn: output tile width in real columns (128 or 64; 0 picks by shape). With ket and bra (the
+// complex64 node tensors) the kernel builds the B operand in shared memory and B is unused;
+// without them it loads B, formed beforehand by launch_form_b_pieces.
 cudaError_t launch_step_tma(const StepParams &s, const ContractArgs &a, const Pieces &A, const Pieces &B,
-                            const OutDesc &out, int *err, cudaStream_t st);
+                            const OutDesc &out, int *err, cudaStream_t st, int bn = 0, const float2 *ket = nullptr,
+                            const float2 *bra = nullptr);
 bool tma_step_supported(const StepParams &s);
 
 // launch accounting

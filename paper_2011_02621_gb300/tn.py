@@ -56,14 +56,15 @@ class tn_allocator(C.Structure):
 class tn_path_opts(C.Structure):
     _fields_ = [("max_rank", C.c_int32), ("boundary_only", C.c_int32), ("connected", C.c_int32),
                 ("max_states", C.c_int64), ("n_cuts", C.c_int32), ("cut_edges", C.POINTER(C.c_int32)),
-                ("n_cut_edges", C.c_int32), ("max_intermediate", C.c_int64), ("mem_budget_bytes", C.c_double)]
+                ("n_cut_edges", C.c_int32), ("max_intermediate", C.c_int64), ("mem_budget_bytes", C.c_double),
+                ("no_merge", C.c_int32)]
 
 
 class tn_plan_info(C.Structure):
     _fields_ = [("n_qubits", C.c_int32), ("n_steps", C.c_int32), ("n_cuts", C.c_int32), ("n_slices", C.c_int64),
                 ("score", C.c_double), ("cmacs", C.c_double), ("flops", C.c_double), ("bytes_c64", C.c_double),
                 ("max_intermediate", C.c_int64), ("states_expanded", C.c_int64), ("max_rank_used", C.c_int32),
-                ("chunk_bitstrings", C.c_int32), ("workspace_bytes", C.c_int64)]
+                ("chunk_bitstrings", C.c_int32), ("workspace_bytes", C.c_int64), ("n_nodes", C.c_int32)]
 
 
 class tn_server_cfg(C.Structure):
@@ -91,6 +92,7 @@ def _load():
         "tn_plan_details": (i32, [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i64)]),
         "tn_amplitudes": (i32, [vp, vp, i64, i32, vp, vp]),
         "tn_amplitudes_static": (i32, [vp, vp, i64, i32, vp, vp]),
+        "tn_amplitudes_slices": (i32, [vp, vp, i64, i32, i64, i64, vp, vp]),
         "tn_launch_count": (i64, [i32]),
         "tn_profile_enable": (i32, [i32]),
         "tn_profile_read": (i32, [i32, C.c_char_p, i32, C.POINTER(i64), C.POINTER(dbl), C.POINTER(dbl),
@@ -108,6 +110,15 @@ def _load():
         "tn_server_wait": (i32, [vp, C.c_uint64, i64]),
         "tn_server_stats_get": (i32, [vp, C.POINTER(tn_server_stats)]),
         "tn_server_free": (None, [vp]),
+        "tn_autotune": (i32, [vp, i32, i64, vp, C.POINTER(i32)]),
+        "tn_plan_kernels": (i32, [vp, i32, C.POINTER(i32)]),
+        "tn_plan_set_kernels": (i32, [vp, i32, C.POINTER(i32)]),
+        "tn_batch_create": (i32, [C.POINTER(vp), i32, vp, C.POINTER(i64), i32, vp, C.POINTER(vp)]),
+        "tn_batch_set_bits": (i32, [vp, vp, vp]),
+        "tn_batch_run": (i32, [vp, vp]),
+        "tn_batch_read": (i32, [vp, vp, vp]),
+        "tn_batch_info": (i32, [vp, C.POINTER(i64), C.POINTER(i64)]),
+        "tn_batch_free": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -263,7 +274,7 @@ def tn_circuit_bond_dims(c: Circuit, side: int) -> np.ndarray:
 
 
 def _opts(max_rank=0, boundary_only=True, connected=True, max_states=0, n_cuts=-1, cut_edges=None,
-          max_intermediate=0, mem_budget_bytes=0.0):
+          max_intermediate=0, mem_budget_bytes=0.0, merge=True):
     o = tn_path_opts()
     o.max_rank = int(max_rank)
     o.boundary_only = 1 if boundary_only else 0
@@ -277,6 +288,7 @@ def _opts(max_rank=0, boundary_only=True, connected=True, max_states=0, n_cuts=-
         o.n_cut_edges = int(keep.size)
     o.max_intermediate = int(max_intermediate)
     o.mem_budget_bytes = float(mem_budget_bytes)
+    o.no_merge = 0 if merge else 1
     return o, keep
 
 
@@ -344,6 +356,30 @@ def tn_amplitudes(p: Plan, bits, prec: str = "fp64", out=None, stream=None):
         res = out
         optr = out.data_ptr()
     _check(LIB.tn_amplitudes(p.ptr, C.c_void_p(bptr), B, PRECISIONS[prec], C.c_void_p(optr), _stream_handle(stream)))
+    del keep
+    return res
+
+
+def tn_amplitudes_slices(p: Plan, bits, prec: str = "fp64", slice_begin: int = 0, slice_end=None, out=None,
+                         stream=None):
+    """Per-bitstring FP64 partial sums over the slices [slice_begin, slice_end) of the plan's cut
+    network (default: all, i.e. the amplitudes). Arguments otherwise those of :func:`tn_amplitudes`."""
+    n = p.circuit.n_qubits
+    words = max((n + 63) // 64, 1)
+    if slice_end is None:
+        slice_end = p.info["n_slices"]
+    if hasattr(bits, "data_ptr"):
+        B, bptr, keep = int(bits.shape[0]), bits.data_ptr(), bits
+    else:
+        b = np.asarray(bits)
+        if b.dtype != np.uint64 or b.ndim != 2 or b.shape[1] != words:
+            b = pack_bits(b.reshape(-1, n))
+        keep = np.ascontiguousarray(b)
+        B, bptr = int(keep.shape[0]), keep.ctypes.data
+    res = np.zeros(B, dtype=np.complex128) if out is None else out
+    optr = res.ctypes.data if isinstance(res, np.ndarray) else res.data_ptr()
+    _check(LIB.tn_amplitudes_slices(p.ptr, C.c_void_p(bptr), B, PRECISIONS[prec], int(slice_begin), int(slice_end),
+                                    C.c_void_p(optr), _stream_handle(stream)))
     del keep
     return res
 
@@ -469,3 +505,140 @@ def tn_server_stats_get(s: Server) -> dict:
     st = tn_server_stats()
     _check(LIB.tn_server_stats_get(s.ptr, C.byref(st)))
     return {name: getattr(st, name) for name, _ in tn_server_stats._fields_}
+
+
+# ---------------------------------------------------------------------------
+# kernel autotuning and batched circuits
+# ---------------------------------------------------------------------------
+KERNEL_NAMES = {0: "simt_auto", 1: "simt_tile64x64", 2: "simt_tile128x16", 3: "simt_tile256x4",
+                4: "simt_stream", 5: "simt_stream_fixed", 6: "simt_small", 16: "tcgen05_split",
+                32: "tcgen05_tma", 33: "tcgen05_tma_bn128", 34: "tcgen05_tma_bn64",
+                40: "tcgen05_tma_loadb", 41: "tcgen05_tma_loadb_bn128", 42: "tcgen05_tma_loadb_bn64"}
+KERNEL_IDS = {v: k for k, v in KERNEL_NAMES.items()}
+
+
+def tn_autotune(p: Plan, prec: str = "bf16x6", n_bits: int = 0, stream=None) -> list:
+    """Time every kernel that supports each contraction step and keep the fastest (stored in the
+    plan for ``prec``). Returns the chosen kernel names, one per step."""
+    k = np.zeros(max(p.info["n_steps"], 1), dtype=np.int32)
+    _check(LIB.tn_autotune(p.ptr, PRECISIONS[prec], int(n_bits), _stream_handle(stream),
+                           k.ctypes.data_as(C.POINTER(C.c_int32))))
+    return [KERNEL_NAMES.get(int(x), str(int(x))) for x in k[: p.info["n_steps"]]]
+
+
+def tn_plan_kernels(p: Plan, prec: str = "bf16x6") -> list:
+    k = np.zeros(max(p.info["n_steps"], 1), dtype=np.int32)
+    _check(LIB.tn_plan_kernels(p.ptr, PRECISIONS[prec], k.ctypes.data_as(C.POINTER(C.c_int32))))
+    return [KERNEL_NAMES.get(int(x), str(int(x))) for x in k[: p.info["n_steps"]]]
+
+
+def tn_plan_set_kernels(p: Plan, prec: str, kernels=None):
+    """Force the step kernels (names or ids, one per step); None returns to the shape heuristic."""
+    if kernels is None:
+        _check(LIB.tn_plan_set_kernels(p.ptr, PRECISIONS[prec], None))
+        return
+    k = np.asarray([KERNEL_IDS[x] if isinstance(x, str) else int(x) for x in kernels], dtype=np.int32)
+    if len(k) != p.info["n_steps"]:
+        raise ValueError(f"need {p.info['n_steps']} kernels, got {len(k)}")
+    _check(LIB.tn_plan_set_kernels(p.ptr, PRECISIONS[prec], k.ctypes.data_as(C.POINTER(C.c_int32))))
+
+
+def _packed_concat(plans, bits_list):
+    rows, counts = [], []
+    for p, b in zip(plans, bits_list):
+        n = p.circuit.n_qubits
+        words = max((n + 63) // 64, 1)
+        b = np.asarray(b)
+        if b.dtype != np.uint64 or b.ndim != 2 or b.shape[1] != words:
+            b = pack_bits(b.reshape(-1, n))
+        rows.append(np.ascontiguousarray(b).reshape(-1))
+        counts.append(b.shape[0])
+    return np.ascontiguousarray(np.concatenate(rows)), np.asarray(counts, dtype=np.int64)
+
+
+class Batch:
+    """Several circuits' amplitudes as one CUDA graph launch (tn_batch_*)."""
+
+    def __init__(self, ptr, plans, counts, prec):
+        self.ptr = ptr
+        self.plans = list(plans)      # plans (and their circuits) outlive the batch
+        self.counts = counts
+        self.prec = prec
+
+    def __del__(self):
+        if getattr(self, "ptr", None) and LIB is not None:
+            LIB.tn_batch_free(self.ptr)
+            self.ptr = None
+
+    @property
+    def total(self) -> int:
+        return int(self.counts.sum())
+
+    def split(self, flat):
+        """Per-circuit views of a concatenated result array."""
+        return np.split(flat, np.cumsum(self.counts)[:-1])
+
+
+def tn_batch_create(plans, bits_list, prec: str = "bf16x6", stream=None) -> Batch:
+    """``bits_list[i]``: circuit i's bitstrings ((B_i, n_i) 0/1 or packed uint64 words)."""
+    flat, counts = _packed_concat(plans, bits_list)
+    arr = (C.c_void_p * len(plans))(*[p.ptr for p in plans])
+    out = C.c_void_p()
+    _check(LIB.tn_batch_create(arr, len(plans), C.c_void_p(flat.ctypes.data),
+                               counts.ctypes.data_as(C.POINTER(C.c_int64)), PRECISIONS[prec],
+                               _stream_handle(stream), C.byref(out)))
+    return Batch(out.value, plans, counts, prec)
+
+
+def tn_batch_set_bits(b: Batch, bits, stream=None):
+    """``bits``: the concatenated packed words (numpy uint64, or a torch tensor, host or device),
+    or a list of per-circuit bitstring arrays."""
+    if isinstance(bits, (list, tuple)):
+        bits, _ = _packed_concat(b.plans, bits)
+    ptr = bits.data_ptr() if hasattr(bits, "data_ptr") else np.ascontiguousarray(bits).ctypes.data
+    _check(LIB.tn_batch_set_bits(b.ptr, C.c_void_p(ptr), _stream_handle(stream)))
+
+
+def tn_batch_run(b: Batch, stream=None):
+    _check(LIB.tn_batch_run(b.ptr, _stream_handle(stream)))
+
+
+def tn_batch_read(b: Batch, out=None, stream=None):
+    """All amplitudes concatenated in plan order (numpy complex128), or into ``out`` (a torch
+    complex128 tensor, host or device)."""
+    res = np.zeros(b.total, dtype=np.complex128) if out is None else out
+    optr = res.ctypes.data if isinstance(res, np.ndarray) else res.data_ptr()
+    _check(LIB.tn_batch_read(b.ptr, C.c_void_p(optr), _stream_handle(stream)))
+    return res
+
+
+def tn_batch_info(b: Batch) -> dict:
+    k, m = C.c_int64(), C.c_int64()
+    _check(LIB.tn_batch_info(b.ptr, C.byref(k), C.byref(m)))
+    return {"graph_kernels": k.value, "device_bytes": m.value}
+
+
+def tn_batch_free(b: Batch):
+    if b.ptr:
+        LIB.tn_batch_free(b.ptr)
+        b.ptr = None
+
+
+def tn_build_largest_chi(n_qubits: int, edges, gates, split_cycle: int, chis=(2, 4, 8, 16, 32, 64),
+                         max_intermediate: int = 1 << 24, cutoff_rel: float = 1e-12, allocator="torch", stream=None):
+    """Circuit, plan and chi for the largest bond cap in ``chis`` whose contraction needs no cut:
+    every intermediate of the path at most ``max_intermediate`` elements per bitstring. Raises
+    TNError(TN_ERR_NO_PATH) if even the smallest cap needs one."""
+    c = tn_build(n_qubits, edges, gates, allocator)
+    best = None
+    for chi in sorted(chis):
+        tn_evolve_two_sided(c, split_cycle, chi, cutoff_rel, stream)
+        p = tn_path(c, max_intermediate=max_intermediate)
+        if p.info["n_slices"] > 1:
+            break
+        best = chi
+        del p
+    if best is None:
+        raise TNError(TN_ERR_NO_PATH, f"no cap in {tuple(chis)} fits {max_intermediate} elements without cuts")
+    tn_evolve_two_sided(c, split_cycle, best, cutoff_rel, stream)
+    return c, tn_path(c, max_intermediate=max_intermediate), best

@@ -56,8 +56,9 @@ def test_grid12_fp32(tn):
 
 
 def test_structural_bonds_bound_oracle_ranks(tn):
-    """Static bond shapes are upper bounds of the oracle's true ranks (Eqs. svd, shouwei); on the
-    53-qubit workload they are exact on both halves."""
+    """Bond shapes after the rank probe: the ket's equal the oracle's true ranks at every split,
+    the bra's bound the true ranks of every bitstring (Eqs. svd, shouwei); on the 53-qubit
+    workload both are exact."""
     from oracle import tns as otns
     w = gen.workload("grid12", n_bits=4)
     c = tn.tn_build(12, w.graph.edges, w.gates)
@@ -65,7 +66,7 @@ def test_structural_bonds_bound_oracle_ranks(tn):
         tn.tn_evolve_two_sided(c, split, 0, 1e-12)
         g1, g2 = otns.split_gates(w.gates, split)
         ket = otns.evolve_ket(12, w.graph.edges, g1)
-        assert all(int(x) >= y for x, y in zip(tn.tn_circuit_bond_dims(c, 0), ket.bonds()))
+        assert list(tn.tn_circuit_bond_dims(c, 0)) == ket.bonds()
         sb = tn.tn_circuit_bond_dims(c, 1)
         for b in w.bits:
             bra = otns.evolve_bra(12, w.graph.edges, g2, b)
@@ -236,12 +237,45 @@ def test_tensor_core_syc53_vs_oracle_and_fp64(tn):
 
 
 def test_tensor_core_cuts_and_ragged_tiles(tn):
-    """Slices, M not a multiple of 128 and N not a multiple of the tile on the tcgen05 path.
-    The 14-cycle circuit is deep enough that complex64 storage itself costs about 1.4e-5
-    (FP32 SIMT path), so the bound here is 2e-5."""
+    """Slices, M not a multiple of 128 and N not a multiple of the tile on the tcgen05 paths.
+    The 14-cycle circuit is deep enough that complex64 storage of the intermediates dominates the
+    error (FP32 SIMT alone is above 1e-5 here), so each tensor-core form is held to 5x the FP32
+    SIMT error of the same plan."""
     w = gen.workload("grid20", n_bits=4)
     ref = statevector_amplitudes(20, w.gates, w.bits)
-    a, _, p = gpu_amplitudes(tn, 20, w.graph.edges, w.gates, w.bits, w.split, prec="tf32x6",
-                             max_intermediate=1 << 22)
+    c = tn.tn_build(20, w.graph.edges, w.gates)
+    tn.tn_evolve_two_sided(c, w.split)
+    p = tn.tn_path(c, max_intermediate=1 << 22)
     assert p.info["n_slices"] > 1
-    assert rel_err(a, ref) < 2e-5
+    e32 = rel_err(tn.tn_amplitudes(p, w.bits, "fp32"), ref)
+    assert e32 < 1e-4
+    for prec in ("bf16x6", "tf32x6"):
+        assert rel_err(tn.tn_amplitudes(p, w.bits, prec), ref) < 5 * e32 + 1e-6, prec
+
+
+@pytest.mark.parametrize("name,n_bits,opts", [
+    ("syc53", 32, {}),
+    ("grid20", 2, {"max_intermediate": 1 << 22}),
+    ("grid12", 64, {"cut_edges": [3, 10]}),
+])
+def test_node_merging_is_exact(tn, name, n_bits, opts):
+    """Merging boundary nodes into neighbours (exact contractions of the ket and bra node tensors)
+    leaves the amplitudes unchanged: merged and unmerged plans agree in FP64 and in BF16x6."""
+    w = gen.workload(name, n_bits=n_bits)
+    c = tn.tn_build(w.graph.n, w.graph.edges, w.gates)
+    tn.tn_evolve_two_sided(c, w.split, w.chi, w.cutoff)
+    pm = tn.tn_path(c, **opts)
+    pu = tn.tn_path(c, merge=False, **opts)
+    assert pu.info["n_nodes"] == w.graph.n
+    assert pm.info["n_nodes"] < w.graph.n
+    assert pm.info["n_steps"] == pm.info["n_nodes"] - 1
+    order, cuts, steps = tn.tn_plan_details(pm)
+    reps = [q for q in order if q >= 0]
+    assert len(reps) == pm.info["n_nodes"] and len(set(reps)) == len(reps)
+    if "cut_edges" in opts:
+        assert sorted(cuts) == sorted(opts["cut_edges"])
+    a_m = tn.tn_amplitudes(pm, w.bits, "fp64")
+    a_u = tn.tn_amplitudes(pu, w.bits, "fp64")
+    assert rel_err(a_m, a_u) < 1e-12
+    if name != "grid12":
+        assert rel_err(tn.tn_amplitudes(pm, w.bits, "bf16x6"), a_u) < (TC_TOL if name == "syc53" else 5e-5)
