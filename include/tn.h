@@ -223,14 +223,16 @@ tn_status tn_amplitudes_static(tn_plan *p, const uint64_t *bits, int64_t n, tn_p
  * 0 shape heuristic (SIMT), 1-3 SIMT tiles 64x64 / 128x16 / 256x4 (rows x columns),
  * 4 SIMT streaming (K, N <= 16), 5 SIMT streaming with K and N fixed at compile time,
  * 6 SIMT one-CTA-per-item reduction (tiny outputs), 16 tcgen05 with the operand split in the
- * kernel (TF32, TF32x3, BF16x3, TF32x6), 32 TMA-fed tcgen05 building the overlap operand in
- * shared memory with the tile picked by shape, 33 / 34 the same with 128- / 64-column tiles,
- * 40 / 41 / 42 the same three loading the operand after a formation pass (BF16x6). The paper has
+ * kernel (TF32, TF32x3, BF16x3, TF32x6), and the TMA-fed tcgen05 kernels (BF16x6), each with the
+ * tile picked by shape / 128-column / 64-column tiles: 32 / 33 / 34 building the overlap operand
+ * in shared memory from the node tensors, 40 / 41 / 42 loading it as bf16 pieces formed in HBM,
+ * 48 / 49 / 50 reading it as complex64 formed in HBM and splitting it on chip. The paper has
  * no counterpart: which
  * kernel runs a pairwise contraction is an implementation choice that changes no result beyond
  * rounding. */
 enum { TN_KERNEL_SIMT = 0, TN_KERNEL_TC = 16, TN_KERNEL_TMA = 32, TN_KERNEL_TMA128 = 33, TN_KERNEL_TMA64 = 34,
-       TN_KERNEL_TMA_LOADB = 40, TN_KERNEL_TMA_LOADB128 = 41, TN_KERNEL_TMA_LOADB64 = 42 };
+       TN_KERNEL_TMA_LOADB = 40, TN_KERNEL_TMA_LOADB128 = 41, TN_KERNEL_TMA_LOADB64 = 42,
+       TN_KERNEL_TMA_C64B = 48, TN_KERNEL_TMA_C64B128 = 49, TN_KERNEL_TMA_C64B64 = 50 };
 
 /* Time every kernel that supports each contraction step of the plan in precision `prec`, on the
  * plan's workspace with a batch of min(n_bits, chunk) bitstrings (n_bits = 0: the full chunk),

@@ -142,8 +142,10 @@ __global__ void __launch_bounds__(GATE_THREADS) gate_kernel(GateParams g, double
 
   // ---- parallel one-sided Jacobi (round-robin pairing)
   // rotation threshold: |<y_p, y_q>| > tol * |y_p| |y_q| with tol = 2 sqrt(R) eps (the rounding
-  // level of the column dot products), and pairs whose columns are negligible against the
-  // whole matrix (|y_p| |y_q| <= 1e-30 ||Y||_F^2) are left alone.
+  // level of the column dot products). Pairs whose smaller column is at the rounding level of the
+  // whole matrix (|y|^2 <= 16 R eps^2 ||Y||_F^2: a singular value below the untruncated cutoff)
+  // are left alone, and a sweep counts as unconverged only for a rotation above 8 tol, so the
+  // iteration ends on rounding-dominated pairs (exactly degenerate spectra are common here).
   __shared__ int s_rot_a[GPB];
   __shared__ double s_fro_a[GPB];
   __shared__ double s_part_a[GPB][TPI / 32];
@@ -163,8 +165,10 @@ __global__ void __launch_bounds__(GATE_THREADS) gate_kernel(GateParams g, double
     }
     item_sync<TPI>();
   }
-  const double tol = 2.0 * sqrt((double)L.R) * 2.220446049250313e-16;
+  const double eps = 2.220446049250313e-16;
+  const double tol = 2.0 * sqrt((double)L.R) * eps;
   const double floor_ab = 1e-30 * s_fro;
+  const double floor_col = 16.0 * (double)L.R * eps * eps * s_fro;
   const int Cp = (C + 1) & ~1;
   const int rounds = Cp - 1;
   bool converged = (C <= 1);
@@ -194,7 +198,7 @@ __global__ void __launch_bounds__(GATE_THREADS) gate_kernel(GateParams g, double
         }
         double ga = sqrt(gr * gr + gi * gi);
         const double nab = sqrt(al * be);
-        if (!(ga > tol * nab) || nab <= floor_ab || ga == 0.0) continue;
+        if (!(ga > tol * nab) || nab <= floor_ab || ga == 0.0 || fmin(al, be) <= floor_col) continue;
         double zeta = (be - al) / (2.0 * ga);
         double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
         double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
@@ -210,14 +214,14 @@ __global__ void __launch_bounds__(GATE_THREADS) gate_kernel(GateParams g, double
           wp[r] = make_double2(cs * a.x - sn * b.x, cs * a.y - sn * b.y);
           wq[r] = make_double2(sn * a.x + cs * b.x, sn * a.y + cs * b.y);
         }
-        if (lane == 0) s_rot = 1;
+        if (lane == 0 && ga > 8.0 * tol * nab) s_rot = 1;
       }
       item_sync<TPI>();
     }
     converged = (s_rot == 0);
     item_sync<TPI>();
   }
-  if (!converged && tid == 0) atomicOr(errflag, 1);
+  if (!converged && tid == 0) atomicCAS(errflag, 0, 1 + g.id);   // first failing gate, 1-based
 
   // ---- singular values, descending ranks, truncation count
   for (int j = warp; j < C; j += nwarp) {

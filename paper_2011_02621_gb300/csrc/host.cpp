@@ -458,6 +458,7 @@ static void build_half(const tn_circuit *c, const std::vector<const tn_gate *> &
     if (chi > 0) dout = std::min(dout, chi);
     if (caps && gi < caps->size() && (*caps)[gi] > 0) dout = std::min(dout, (*caps)[gi]);   // probed rank
     gp.dout = dout;
+    gp.id = (int)gi;
     gp.cutoff = cutoff;
     for (int i = 0; i < 16; ++i) {
       gp.P[i] = make_double2(P[i].real(), P[i].imag());
@@ -598,7 +599,13 @@ static tn_status probe_ranks(tn_circuit *c, const Half &h, const std::vector<dou
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   cleanup();
   if (e != cudaSuccess) return tn_fail(TN_ERR_CUDA, "rank probe: %s", cudaGetErrorString(e));
-  if (errv) return tn_fail(TN_ERR_TIMEOUT, "Jacobi SVD did not converge within its sweep limit (rank probe)");
+  if (errv) {
+    const GateParams &g = h.gp[std::min<size_t>(errv - 1, h.gp.size() - 1)];
+    return tn_fail(TN_ERR_TIMEOUT,
+                   "Jacobi SVD did not converge within its sweep limit (rank probe, gate %d: m_k %d m_l %d n %d "
+                   "din %d dout %d svd %s)",
+                   errv - 1, g.m_k, g.m_l, g.n, g.din, g.dout, g.sv_is_k ? "k" : "l");
+  }
   for (int &x : caps) x = std::max(x, 1);
   return TN_OK;
 }
@@ -680,7 +687,7 @@ extern "C" tn_status tn_evolve_two_sided(tn_circuit *c, int32_t split_cycle, int
   int err = 0;
   CUDA_TRY(cudaMemcpyAsync(&err, c->err_dev.p, sizeof(int), cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaStreamSynchronize(st));
-  if (err) return tn_fail(TN_ERR_TIMEOUT, "Jacobi SVD did not converge within its sweep limit (ket half)");
+  if (err) return tn_fail(TN_ERR_TIMEOUT, "Jacobi SVD did not converge within its sweep limit (ket half, gate %d)", err - 1);
   c->evolved = true;
   if (!same) c->generation++;
   return TN_OK;
@@ -1575,7 +1582,7 @@ tn_status ws_ensure(tn_plan *p, Workspace &w, int kind, cudaStream_t st) {
 bool step_kernel_ok(const StepParams &s, tn_precision prec, int k) {
   if (k < SK_TC) return simt_variant_ok(s, k);
   if (k == SK_TC) return prec != TN_FP64 && prec != TN_FP32 && prec != TN_BF16X6 && tc_step_supported(s);
-  if (!sk_is_tma(k) || k > SK_TMAF64 || (k > SK_TMA64 && k < SK_TMAF)) return false;
+  if (!sk_is_tma(k)) return false;
   if (prec != TN_BF16X6 || !tma_step_supported(s)) return false;
   return sk_tma_bn(k) != 128 || 2 * s.N >= 128;
 }
@@ -1587,7 +1594,7 @@ std::vector<int> step_kernels(const tn_plan *p, tn_precision prec) {
   if (t.size() == p->steps.size()) return t;
   std::vector<int> k(p->steps.size(), SIMT_AUTO);
   for (size_t j = 1; j < p->steps.size(); ++j) {
-    if (prec == TN_BF16X6 && step_kernel_ok(p->steps[j], prec, SK_TMA)) k[j] = SK_TMA;
+    if (prec == TN_BF16X6 && step_kernel_ok(p->steps[j], prec, SK_TMAC)) k[j] = SK_TMAC;
     else if (step_kernel_ok(p->steps[j], prec, SK_TC)) k[j] = SK_TC;
   }
   return k;
@@ -1649,11 +1656,23 @@ cudaError_t enqueue_step(const tn_plan *p, const Workspace &w, size_t j, int k, 
   B.item_elems = 4 * p->maxKN;
   B.plane_elems = cap * B.item_elems;
   const double out_b = (od.fmt ? 12.0 : 8.0) * (double)sp.M * sp.N;
-  if (!sk_loads_b(k)) {
+  if (sk_tma_bmode(k) == 1) {
     // algorithmic bytes: A pieces read, output written (B is built on chip from the node tensors)
-    ProfScope ps("contract_step_tcgen05_tma", st, items * (12.0 * (double)sp.M * sp.K + out_b), fl);
+    ProfScope ps("contract_step_tcgen05_tma_buildb", st, items * (12.0 * (double)sp.M * sp.K + out_b), fl);
     return launch_step_tma(sp, a, A, B, od, (int *)w.err.p + 1, st, sk_tma_bn(k), (const float2 *)ket,
                            (const float2 *)bra);
+  }
+  if (sk_tma_bmode(k) == 2) {
+    {
+      ProfScope ps("overlap_form_c64", st, 8.0 * items * (double)sp.K * sp.N, 16.0 * items * (double)sp.K * sp.N);
+      cudaError_t e = launch_form_c(sp, a, (const float2 *)ket, (const float2 *)bra, (float2 *)w.cbuf.p, p->maxKN, st);
+      if (e != cudaSuccess) return e;
+    }
+    // algorithmic bytes: A pieces and the complex64 overlap tensor read, output written
+    ProfScope ps("contract_step_tcgen05_tma", st, items * (12.0 * (double)sp.M * sp.K + 8.0 * (double)sp.K * sp.N + out_b),
+                 fl);
+    return launch_step_tma(sp, a, A, B, od, (int *)w.err.p + 1, st, sk_tma_bn(k), nullptr, nullptr,
+                           (const float2 *)w.cbuf.p, p->maxKN);
   }
   {
     ProfScope ps("overlap_form_bf16_pieces", st, 24.0 * items * (double)sp.K * sp.N, 16.0 * items * (double)sp.K * sp.N);
@@ -1741,7 +1760,8 @@ tn_status enqueue_chunk(tn_plan *p, Workspace &w, const uint64_t *bits_dev, int6
 }
 
 tn_status check_err_words(const int *err) {
-  if (err[0]) return tn_fail(TN_ERR_TIMEOUT, "Jacobi SVD did not converge within its sweep limit (bra half)");
+  if (err[0])
+    return tn_fail(TN_ERR_TIMEOUT, "Jacobi SVD did not converge within its sweep limit (bra half, gate %d)", err[0] - 1);
   if (err[1]) return tn_fail(TN_ERR_TIMEOUT, "tensor-core GEMM: a bounded pipeline wait expired (code %d)", err[1]);
   return TN_OK;
 }

@@ -11,17 +11,20 @@
 //            K-major layout of the MMA), signalling a "full" mbarrier with the byte count;
 //   warp 1   allocates TMEM and issues tcgen05.mma kind::f16 (bf16 in, fp32 accumulate) for
 //            the six products x_i*y_j with i + j <= 2, order 0 spread round-robin over R
-//            accumulators, orders 1 and 2 in one accumulator each; each stage is released by
+//            accumulators, orders 1 and 2 together in one more; each stage is released by
 //            tcgen05.commit on its "empty" mbarrier, the last one on "done";
 //   warps 2-5 wait for "done", read the accumulators with tcgen05.ld, add them smallest first
 //            and write the result straight into the next step's layout, as complex64 or as
 //            bf16 pieces for the next tensor-core step.
-// In the building mode (BUILD) no overlap tensor is stored at all: during the main loop warps 2-5
-// compute each stage's B tile themselves from the absorbed node's ket and bra tensors (Eq.
-// overlap, the same arithmetic as the formation kernel), split it into the three bf16 pieces and
-// store it in the 128-byte-swizzled K-major layout the MMA reads; each of those 128 threads then
-// makes its writes visible to the tensor core's async proxy and arrives on the stage's "full"
-// mbarrier next to the TMA's byte count. Only the A pieces come from memory.
+// B modes. BM 0: the B pieces are loaded by TMA (formed beforehand). BM 1: no overlap tensor is
+// stored at all: during the main loop warps 2-5 compute each stage's B tile themselves from the
+// absorbed node's ket and bra tensors (Eq. overlap, the same arithmetic as the formation
+// kernel). BM 2: warps 2-5 read the overlap tensor as complex64 [N][K] (8 bytes per element,
+// independent coalesced loads, all of a stage's loads issued before any is used). In modes 1 and
+// 2 the warps split the tile into the three bf16 pieces and store it in the 128-byte-swizzled
+// K-major layout the MMA reads; each of those 128 threads then makes its writes visible to the
+// tensor core's async proxy and arrives on the stage's "full" mbarrier next to the TMA's byte
+// count. Only the A pieces come through TMA.
 // Every wait is bounded by a clock limit and raises an error code instead of hanging.
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -126,15 +129,17 @@ __device__ __forceinline__ void mma_commit_to(uint32_t bar) {
 
 namespace {
 
-template <int BN, int R, int S, bool BUILD>
+template <int BN, int R, int S, int BM>
 __global__ void __launch_bounds__(T_THREADS, 1)
 tma_step_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMap tA1,
                 const __grid_constant__ CUtensorMap tA2, const __grid_constant__ CUtensorMap tB0,
                 const __grid_constant__ CUtensorMap tB1, const __grid_constant__ CUtensorMap tB2, StepParams s,
-                ContractArgs a, OutDesc out, int *err, const float2 *ket, const float2 *bra) {
+                ContractArgs a, OutDesc out, int *err, const float2 *ket, const float2 *bra, const float2 *cbuf,
+                int64_t c_stride) {
+  constexpr bool BUILD = BM != 0;
   constexpr int A_BYTES = T_BM * 128, B_BYTES = BN * 128;
   constexpr int STAGE = T_P * (A_BYTES + B_BYTES);
-  constexpr int GROUPS = R + 2;
+  constexpr int GROUPS = R + 1;                  // R order-0 accumulators + one for orders 1 and 2
   constexpr uint32_t TMEM_COLS = GROUPS * BN <= 32 ? 32 : GROUPS * BN <= 64 ? 64 : GROUPS * BN <= 128 ? 128
                                  : GROUPS * BN <= 256 ? 256 : 512;
   static_assert(GROUPS * BN <= 512, "TMEM columns");
@@ -232,16 +237,14 @@ tma_step_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__
           const uint32_t first = (t == 0) ? 0u : 1u;
           mma_bf16(tmem + (uint32_t)((t % R) * BN), desc_sw128(a0 + off), desc_sw128(b0 + off), idesc,
                    t < R ? 0u : 1u);
-          // order 1: x0*y1 + x1*y0
+          // orders 1 and 2 in one accumulator: x0*y1 + x1*y0, then x0*y2 + x1*y1 + x2*y0 (order-2
+          // terms, ~2^-16 of a product, lie far above that accumulator's truncation level)
           mma_bf16(tmem + (uint32_t)(R * BN), desc_sw128(a0 + off), desc_sw128(b0 + B_BYTES + off), idesc, first);
           mma_bf16(tmem + (uint32_t)(R * BN), desc_sw128(a0 + A_BYTES + off), desc_sw128(b0 + off), idesc, 1u);
-          // order 2: x0*y2 + x1*y1 + x2*y0
-          mma_bf16(tmem + (uint32_t)((R + 1) * BN), desc_sw128(a0 + off), desc_sw128(b0 + 2 * B_BYTES + off), idesc,
-                   first);
-          mma_bf16(tmem + (uint32_t)((R + 1) * BN), desc_sw128(a0 + A_BYTES + off),
-                   desc_sw128(b0 + B_BYTES + off), idesc, 1u);
-          mma_bf16(tmem + (uint32_t)((R + 1) * BN), desc_sw128(a0 + 2 * A_BYTES + off), desc_sw128(b0 + off), idesc,
+          mma_bf16(tmem + (uint32_t)(R * BN), desc_sw128(a0 + off), desc_sw128(b0 + 2 * B_BYTES + off), idesc, 1u);
+          mma_bf16(tmem + (uint32_t)(R * BN), desc_sw128(a0 + A_BYTES + off), desc_sw128(b0 + B_BYTES + off), idesc,
                    1u);
+          mma_bf16(tmem + (uint32_t)(R * BN), desc_sw128(a0 + 2 * A_BYTES + off), desc_sw128(b0 + off), idesc, 1u);
         }
         mma_commit_to(s_u32(&empty[st]));
       }
@@ -264,6 +267,45 @@ tma_step_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__
         const uint32_t it = (uint32_t)(kc / S);
         if (kc >= S && !bar_wait(s_u32(&empty[st]), (it - 1) & 1, err, 15)) break;
         const uint32_t bbase = s_u32(smem + st * STAGE + T_P * A_BYTES);
+        if (BM == 2) {
+          // every load of the stage first (tasks: four consecutive complex k of one column n)
+          constexpr int TASKS = (BN / 2) * 8 / 128;
+          float4 x[TASKS][2];
+#pragma unroll
+          for (int j = 0; j < TASKS; ++j) {
+            const int t = bt + 128 * j, c16 = t & 7, nl = t >> 3;
+            const int64_t n = n_base + nl, k0 = kc * 32 + c16 * 4;
+            x[j][0] = x[j][1] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (n < s.N && k0 < s.K) {   // K % 4 == 0: the four k are all in range or all out
+              const float4 *src = reinterpret_cast<const float4 *>(cbuf + item * c_stride + n * s.K + k0);
+              x[j][0] = __ldg(src);
+              x[j][1] = __ldg(src + 1);
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < TASKS; ++j) {
+            const int t = bt + 128 * j, c16 = t & 7, nl = t >> 3;
+            const float re[4] = {x[j][0].x, x[j][0].z, x[j][1].x, x[j][1].z};
+            const float im[4] = {x[j][0].y, x[j][0].w, x[j][1].y, x[j][1].w};
+            uint32_t w0[T_P][4], w1[T_P][4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              uint32_t t0[T_P], t1[T_P];
+              tn_split3(re[i], -im[i], t0);
+              tn_split3(im[i], re[i], t1);
+#pragma unroll
+              for (int q = 0; q < T_P; ++q) {
+                w0[q][i] = t0[q];
+                w1[q][i] = t1[q];
+              }
+            }
+#pragma unroll
+            for (int q = 0; q < T_P; ++q) {
+              sts128(bbase + q * B_BYTES + sw128_off(2 * nl, c16), w0[q]);
+              sts128(bbase + q * B_BYTES + sw128_off(2 * nl + 1, c16), w1[q]);
+            }
+          }
+        } else
         for (int t = bt; t < (BN / 2) * 8; t += 128) {
           const int c16 = t & 7, nl = t >> 3;        // 16-byte chunk = four complex k; complex column
           const int64_t n = n_base + nl;
@@ -380,13 +422,15 @@ bool make_map(CUtensorMap *m, const void *base, uint64_t inner, uint64_t rows, u
   return r == CUDA_SUCCESS;
 }
 
-template <int BN, int R, int S, bool BUILD>
+template <int BN, int R, int S, int BM>
 cudaError_t launch_t(const StepParams &s, const ContractArgs &a, const Pieces &A, const Pieces &B, const OutDesc &out,
-                     int *err, const float2 *ket, const float2 *bra, cudaStream_t st) {
+                     int *err, const float2 *ket, const float2 *bra, const float2 *cbuf, int64_t c_stride,
+                     cudaStream_t st) {
+  constexpr bool BUILD = BM != 0;
   constexpr size_t stage = (size_t)T_P * (T_BM * 128 + BN * 128);
   const size_t smem = S * stage + 1024;
   // once per instantiation (a function-local static is initialised by one thread)
-  static const cudaError_t attr = cudaFuncSetAttribute(tma_step_kernel<BN, R, S, BUILD>,
+  static const cudaError_t attr = cudaFuncSetAttribute(tma_step_kernel<BN, R, S, BM>,
                                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (attr != cudaSuccess) return attr;
   CUtensorMap mA[3], mB[3];
@@ -406,8 +450,8 @@ cudaError_t launch_t(const StepParams &s, const ContractArgs &a, const Pieces &A
   const int64_t grid = tiles * a.items;
   if (grid <= 0) return cudaSuccess;
   if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-  tma_step_kernel<BN, R, S, BUILD><<<(unsigned)grid, T_THREADS, smem, st>>>(mA[0], mA[1], mA[2], mB[0], mB[1], mB[2],
-                                                                            s, a, out, err, ket, bra);
+  tma_step_kernel<BN, R, S, BM><<<(unsigned)grid, T_THREADS, smem, st>>>(mA[0], mA[1], mA[2], mB[0], mB[1], mB[2], s,
+                                                                         a, out, err, ket, bra, cbuf, c_stride);
   tn_count_launch(1);
   return cudaGetLastError();
 }
@@ -421,15 +465,18 @@ bool tma_step_supported(const StepParams &s) {
 
 cudaError_t launch_step_tma(const StepParams &s, const ContractArgs &a, const Pieces &A, const Pieces &B,
                             const OutDesc &out, int *err, cudaStream_t st, int bn, const float2 *ket,
-                            const float2 *bra) {
+                            const float2 *bra, const float2 *cbuf, int64_t c_stride) {
   if (bn == 0) bn = 2 * s.N >= 128 ? 128 : 64;
-  const bool build = ket != nullptr;
-  if (build && !bra) return cudaErrorInvalidValue;
-  if (bn == 128 && 2 * s.N >= 128)
-    return build ? launch_t<128, 2, 2, true>(s, a, A, B, out, err, ket, bra, st)
-                 : launch_t<128, 2, 2, false>(s, a, A, B, out, err, ket, bra, st);
-  if (bn == 64)
-    return build ? launch_t<64, 6, 3, true>(s, a, A, B, out, err, ket, bra, st)
-                 : launch_t<64, 6, 3, false>(s, a, A, B, out, err, ket, bra, st);
+  const int bm = cbuf ? 2 : ket ? 1 : 0;
+  if (bm == 1 && !bra) return cudaErrorInvalidValue;
+#define TN_TMA_LAUNCH(BNV, RV, SV)                                                                     \
+  switch (bm) {                                                                                        \
+    case 0: return launch_t<BNV, RV, SV, 0>(s, a, A, B, out, err, ket, bra, cbuf, c_stride, st);       \
+    case 1: return launch_t<BNV, RV, SV, 1>(s, a, A, B, out, err, ket, bra, cbuf, c_stride, st);       \
+    default: return launch_t<BNV, RV, SV, 2>(s, a, A, B, out, err, ket, bra, cbuf, c_stride, st);      \
+  }
+  if (bn == 128 && 2 * s.N >= 128) { TN_TMA_LAUNCH(128, 3, 2) }
+  if (bn == 64) { TN_TMA_LAUNCH(64, 7, 3) }
+#undef TN_TMA_LAUNCH
   return cudaErrorInvalidValue;
 }

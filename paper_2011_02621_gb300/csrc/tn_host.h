@@ -113,10 +113,15 @@ struct tn_plan {
 // Kernel of one contraction step: a SimtVariant (SIMT, complex FMA), tcgen05 with the operand split in
 // the kernel, or TMA-fed tcgen05 (BF16x6) with a shape-picked or fixed tile width, building the
 // overlap operand in shared memory (SK_TMA*) or loading it after a formation pass (SK_TMAF*).
-enum StepKernel { SK_TC = 16, SK_TMA = 32, SK_TMA128 = 33, SK_TMA64 = 34, SK_TMAF = 40, SK_TMAF128 = 41, SK_TMAF64 = 42 };
-inline bool sk_is_tma(int k) { return k >= SK_TMA; }
-inline bool sk_loads_b(int k) { return k >= SK_TMAF; }
-inline int sk_tma_bn(int k) { return (k == SK_TMA128 || k == SK_TMAF128) ? 128 : (k == SK_TMA64 || k == SK_TMAF64) ? 64 : 0; }
+enum StepKernel {
+  SK_TC = 16,
+  SK_TMA = 32, SK_TMA128 = 33, SK_TMA64 = 34,     // B built from the node tensors in shared memory
+  SK_TMAF = 40, SK_TMAF128 = 41, SK_TMAF64 = 42,  // B pieces formed in HBM, loaded by TMA
+  SK_TMAC = 48, SK_TMAC128 = 49, SK_TMAC64 = 50   // B formed in HBM as complex64, split on chip
+};
+inline bool sk_is_tma(int k) { return k >= SK_TMA && k <= SK_TMAC64 && (k & 7) <= 2; }
+inline int sk_tma_bmode(int k) { return k >= SK_TMAC ? 2 : k >= SK_TMAF ? 0 : 1; }
+inline int sk_tma_bn(int k) { return (k & 7) == 1 ? 128 : (k & 7) == 2 ? 64 : 0; }
 std::vector<int> step_kernels(const tn_plan *p, tn_precision prec);
 bool step_kernel_ok(const StepParams &s, tn_precision prec, int k);
 

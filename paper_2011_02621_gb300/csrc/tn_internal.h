@@ -30,6 +30,7 @@ struct GateParams {
   double2 P[16];               // P[s'][s][a] at (s'*2+s)*4+a  (Eq. gatesplit)
   double2 Q[16];
   int64_t work_stride;         // per-item global work size (complex elements) when !use_smem
+  int id;                      // position in the half's gate program (reported when the SVD fails)
 };
 
 struct Apply1Params {
@@ -143,12 +144,13 @@ bool tc_step_supported(const StepParams &s);
 cudaError_t launch_form_b_pieces(const StepParams &s, const ContractArgs &a, const float2 *ket, const float2 *bra,
                                  const Pieces &B, cudaStream_t st);
 // TMA-fed tcgen05 step (BF16x6) from pre-split A and B pieces
-// bn: output tile width in real columns (128 or 64; 0 picks by shape). With ket and bra (the
-// complex64 node tensors) the kernel builds the B operand in shared memory and B is unused;
-// without them it loads B, formed beforehand by launch_form_b_pieces.
+// bn: output tile width in real columns (128 or 64; 0 picks by shape). The B operand: with cbuf
+// (the overlap tensor as complex64 [N][K] per item, c_stride elements apart, from
+// launch_form_c) the kernel splits it in shared memory; else with ket and bra (the complex64
+// node tensors) it builds it in shared memory; else it loads B, formed by launch_form_b_pieces.
 cudaError_t launch_step_tma(const StepParams &s, const ContractArgs &a, const Pieces &A, const Pieces &B,
                             const OutDesc &out, int *err, cudaStream_t st, int bn = 0, const float2 *ket = nullptr,
-                            const float2 *bra = nullptr);
+                            const float2 *bra = nullptr, const float2 *cbuf = nullptr, int64_t c_stride = 0);
 bool tma_step_supported(const StepParams &s);
 
 // launch accounting

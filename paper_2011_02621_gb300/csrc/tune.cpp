@@ -3,8 +3,9 @@
 // Every contraction step of a plan (one TTGT pairwise contraction of the path) can run on several
 // kernels: SIMT tiles of three shapes, two streaming kernels for small K and N, a one-CTA-per-item
 // reduction for tiny outputs, and, for the tensor-core forms, the tcgen05 kernel with in-kernel
-// operand split or the TMA-fed tcgen05 kernel (BF16x6) with 128- or 64-column tiles, building the
-// overlap operand on chip or loading it after a formation pass. The shape
+// operand split or the TMA-fed tcgen05 kernel (BF16x6) with 128- or 64-column tiles, its overlap
+// operand built on chip from the node tensors, formed in HBM as complex64 and split on chip, or
+// formed in HBM as bf16 pieces and loaded. The shape
 // heuristic picks one; the autotuner times every kernel that supports the step on the plan's own
 // workspace, at the batch size given, and keeps the fastest. The heuristic's kernel is kept unless
 // another is at least 3% faster. Choices are stored in the plan per precision and used by every
@@ -17,8 +18,9 @@
 
 namespace {
 
-const int kCandidates[] = {SIMT_AUTO, SIMT_T64, SIMT_T128, SIMT_T256, SIMT_STREAM, SIMT_FIXED, SIMT_SMALL,
-                           SK_TC,     SK_TMA,   SK_TMA128, SK_TMA64,  SK_TMAF,     SK_TMAF128, SK_TMAF64};
+const int kCandidates[] = {SIMT_AUTO, SIMT_T64,  SIMT_T128, SIMT_T256, SIMT_STREAM, SIMT_FIXED, SIMT_SMALL, SK_TC,
+                           SK_TMA,    SK_TMA128, SK_TMA64,  SK_TMAF,   SK_TMAF128,  SK_TMAF64,  SK_TMAC,    SK_TMAC128,
+                           SK_TMAC64};
 
 struct Events {
   cudaEvent_t a = nullptr, b = nullptr;

@@ -90,7 +90,7 @@ def test_untruncated_24_qubits_12_cycles_matches_state_vector(tn):
 def test_full_family_one_launch(tn, family):
     """All 32 circuits x 1024 bitstrings, truncated: one graph launch; the batch equals single
     calls, a replay repeats it bit for bit, new bitstrings run through the same graph, and BF16x6
-    stays within 1e-5 of FP64 for nearly every amplitude (the bench counts only those)."""
+    stays within 1e-5 of FP64 for nearly every amplitude above round-off."""
     plans = _plans(tn, family)
     chis = [chi for _, _, _, chi in plans]
     assert min(chis) >= 2
@@ -106,12 +106,19 @@ def test_full_family_one_launch(tn, family):
     a_tc = tn.tn_batch_read(btc)
     tn.tn_batch_run(b64)
     a64 = tn.tn_batch_read(b64)
-    within, worst = 0, 0.0
-    for g_tc, g64 in zip(btc.split(a_tc), b64.split(a64)):
-        r = np.abs(g_tc - g64) / np.sqrt(np.mean(np.abs(g64) ** 2))
+    # at chi = 2 the truncation leaves round-off-level amplitudes (rms ~1e-17 against 2^-n/2 for
+    # the exact ones): precisions are compared on the circuits whose amplitudes lie above that
+    checked, within, worst = 0, 0, 0.0
+    for g_tc, g64, w in zip(btc.split(a_tc), b64.split(a64), family):
+        rms = np.sqrt(np.mean(np.abs(g64) ** 2))
+        if not rms > 1e-8 * 2.0 ** (-w.graph.n / 2):
+            continue
+        r = np.abs(g_tc - g64) / rms
+        checked += len(r)
         within += int(np.sum(r <= TC_TOL))
         worst = max(worst, float(r.max()))
-    assert within >= 0.99 * len(a64) and worst < 1e-4
+    assert checked >= 1024
+    assert within >= 0.99 * checked and worst < 1e-4
     for i in (0, 15, 31):
         assert np.array_equal(btc.split(a_tc)[i], tn.tn_amplitudes(ps[i], bits[i], "bf16x6"))
     tn.tn_batch_run(btc)
@@ -156,10 +163,16 @@ def test_autotune_keeps_results(tn, name, n_bits, prec, tol):
     assert tn.tn_plan_kernels(p, prec) == chosen
     assert all(not k.isdigit() for k in chosen)
     a1 = tn.tn_amplitudes(p, w.bits, prec)
-    assert rel_err(a1, ref) < tol
-    assert rel_err(a0, ref) < tol
     if prec == "bf16x6":
+        # the amplitudes/s metric counts an amplitude when it is within 1e-5 of FP64
+        rms = np.sqrt(np.mean(np.abs(ref) ** 2))
+        for a in (a0, a1):
+            r = np.abs(a - ref) / rms
+            assert np.mean(r <= tol) >= 0.99 and r.max() < 2 * tol
         assert any(k.startswith("tcgen05") for k in chosen)
+    else:
+        assert rel_err(a1, ref) < tol
+        assert rel_err(a0, ref) < tol
 
 
 @pytest.mark.parametrize("name,n_bits,opts", [
@@ -167,8 +180,9 @@ def test_autotune_keeps_results(tn, name, n_bits, prec, tol):
     ("grid20", 2, {"max_intermediate": 1 << 22}),       # slices, ragged K and N tiles
 ])
 def test_tma_built_operand_equals_loaded_operand(tn, name, n_bits, opts):
-    """The TMA-fed BF16x6 step building its overlap operand in shared memory computes exactly what
-    the step loading the same operand from a formation pass computes (same values, same MMAs)."""
+    """The three ways the TMA-fed BF16x6 step gets its overlap operand (built in shared memory from
+    the node tensors, read as complex64 and split on chip, loaded as bf16 pieces from a formation
+    pass) give the same values to the same MMAs: identical amplitudes."""
     w = gen.workload(name, n_bits=n_bits)
     c = tn.tn_build(w.graph.n, w.graph.edges, w.gates)
     tn.tn_evolve_two_sided(c, w.split, w.chi, w.cutoff)
@@ -176,14 +190,16 @@ def test_tma_built_operand_equals_loaded_operand(tn, name, n_bits, opts):
     ks = tn.tn_plan_kernels(p, "bf16x6")
     assert "tcgen05_tma" in ks
     results = {}
-    for build in ("tcgen05_tma", "tcgen05_tma_loadb"):
+    modes = ("tcgen05_tma", "tcgen05_tma_buildb", "tcgen05_tma_loadb")
+    for mode in modes:
         for bn in ("", "_bn64"):
-            forced = [k if not k.startswith("tcgen05_tma") else build + bn for k in ks]
+            forced = [k if not k.startswith("tcgen05_tma") else mode + bn for k in ks]
             tn.tn_plan_set_kernels(p, "bf16x6", forced)
-            results[(build, bn)] = tn.tn_amplitudes(p, w.bits, "bf16x6")
+            results[(mode, bn)] = tn.tn_amplitudes(p, w.bits, "bf16x6")
     tn.tn_plan_set_kernels(p, "bf16x6", None)
-    assert np.array_equal(results[("tcgen05_tma", "")], results[("tcgen05_tma_loadb", "")])
-    assert np.array_equal(results[("tcgen05_tma", "_bn64")], results[("tcgen05_tma_loadb", "_bn64")])
+    for bn in ("", "_bn64"):
+        for mode in modes[1:]:
+            assert np.array_equal(results[(modes[0], bn)], results[(mode, bn)]), (mode, bn)
     ref = tn.tn_amplitudes(p, w.bits, "fp64")
     tol = TC_TOL if name == "syc53" else 5e-5
     for v in results.values():
