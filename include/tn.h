@@ -222,7 +222,8 @@ tn_status tn_amplitudes_static(tn_plan *p, const uint64_t *bits, int64_t n, tn_p
 /* Step kernels (values written by tn_autotune / tn_plan_kernels, one per contraction step):
  * 0 shape heuristic (SIMT), 1-3 SIMT tiles 64x64 / 128x16 / 256x4 (rows x columns),
  * 4 SIMT streaming (K, N <= 16), 5 SIMT streaming with K and N fixed at compile time,
- * 6 SIMT one-CTA-per-item reduction (tiny outputs), 16 tcgen05 with the operand split in the
+ * 6 SIMT one-CTA-per-item reduction (small outputs), 7 SIMT few-rows kernel (M <= 16, M*K <= 2048,
+ * one thread per output column), 16 tcgen05 with the operand split in the
  * kernel (TF32, TF32x3, BF16x3, TF32x6), and the TMA-fed tcgen05 kernels (BF16x6), each with the
  * tile picked by shape / 128-column / 64-column tiles: 32 / 33 / 34 building the overlap operand
  * in shared memory from the node tensors, 40 / 41 / 42 loading it as bf16 pieces formed in HBM,
@@ -255,14 +256,16 @@ typedef struct tn_batch tn_batch;
  * CUDA graph. bits: every circuit's bitstrings concatenated in plan order, circuit i taking
  * n_bits[i] rows of ceil(n_qubits_i/64) words; host or device memory, copied. The batch owns
  * device buffers for the bitstrings, the results and one workspace per circuit (allocated through
- * each circuit's allocator), runs every circuit once on `cuda_stream` to validate it, and
+ * each circuit's allocator); hbm_budget_bytes > 0 bounds the workspaces together (each circuit
+ * then runs its bitstrings in chunks that fit a share of the budget proportional to its whole
+ * need; 0: each plan's own chunk). It runs every circuit once on `cuda_stream` to validate it, and
  * captures the whole batch (one independent branch per circuit: bra evolution, overlap,
  * contraction with the plan's kernels, FP64 slice sum) into one graph. Plans and circuits must
  * outlive the batch; re-evolving a circuit invalidates it. The paper has no counterpart: this is
  * the batching of many circuits into one launch.
  * Errors: TN_ERR_ARG, TN_ERR_STATE, TN_ERR_CUDA, TN_ERR_OOM, TN_ERR_TIMEOUT. */
 tn_status tn_batch_create(tn_plan *const *plans, int32_t n_plans, const uint64_t *bits, const int64_t *n_bits,
-                          tn_precision prec, void *cuda_stream, tn_batch **out);
+                          tn_precision prec, double hbm_budget_bytes, void *cuda_stream, tn_batch **out);
 
 /* Replace every circuit's bitstrings (same layout and counts as at creation); stream-ordered. */
 tn_status tn_batch_set_bits(tn_batch *b, const uint64_t *bits, void *cuda_stream);

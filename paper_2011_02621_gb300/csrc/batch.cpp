@@ -146,7 +146,8 @@ tn_status upload_bits(tn_batch *b, const uint64_t *bits, cudaStream_t st) {
 }  // namespace
 
 extern "C" tn_status tn_batch_create(tn_plan *const *plans, int32_t n_plans, const uint64_t *bits,
-                                     const int64_t *n_bits, tn_precision prec, void *cuda_stream, tn_batch **out) {
+                                     const int64_t *n_bits, tn_precision prec, double hbm_budget_bytes,
+                                     void *cuda_stream, tn_batch **out) {
   if (!out) return tn_fail(TN_ERR_ARG, "tn_batch_create: out is NULL");
   *out = nullptr;
   if (!plans || n_plans <= 0 || !bits || !n_bits) return tn_fail(TN_ERR_ARG, "tn_batch_create: bad arguments");
@@ -180,9 +181,20 @@ extern "C" tn_status tn_batch_create(tn_plan *const *plans, int32_t n_plans, con
   tn_status s = b->mem->ensure(b->bits, (size_t)b->total_words * 8, st);
   if (s == TN_OK) s = b->mem->ensure(b->res, (size_t)b->total_amps * sizeof(tn_c128), st);
   b->device_bytes = (int64_t)(b->bits.bytes + b->res.bytes);
+  // each circuit's batch of bitstrings: its whole set, within its plan's chunk, and within its
+  // share of the budget (shares proportional to what the whole sets would need)
+  double need = 0;
+  for (auto &it : b->items) need += (double)plan_ws_bytes(it.p, kind, it.n, it.p->slice_chunk[kind]);
   for (auto &it : b->items) {
     if (s != TN_OK) break;
-    const int64_t ch = std::min<int64_t>(it.n, it.p->chunk[kind]);
+    int64_t ch = std::min<int64_t>(it.n, it.p->chunk[kind]);
+    if (hbm_budget_bytes > 0 && need > hbm_budget_bytes) {
+      const double whole = (double)plan_ws_bytes(it.p, kind, it.n, it.p->slice_chunk[kind]);
+      const double share = hbm_budget_bytes * whole / need;
+      const double fixed = (double)plan_ws_bytes(it.p, kind, 0, it.p->slice_chunk[kind]);
+      const double per = (double)plan_ws_bytes(it.p, kind, 1, it.p->slice_chunk[kind]) - fixed;
+      ch = std::min<int64_t>(ch, std::max<int64_t>(1, (int64_t)((share - fixed) / std::max(per, 1.0))));
+    }
     s = ws_ensure_sized(it.p, it.w, kind, ch, it.p->slice_chunk[kind], st);
     b->device_bytes += plan_ws_bytes(it.p, kind, ch, it.p->slice_chunk[kind]);
   }

@@ -151,25 +151,25 @@ step_kernel(StepParams s, ContractArgs a, const typename C2T<R>::T *ket, const t
   }
 }
 
-// Small outputs (M*N <= 16, e.g. the last step): one CTA per item reduces over K.
+// Small outputs (M*N <= 256, e.g. the last steps): one CTA per item, one warp per output at a
+// time, each reducing over K with its lanes and a shuffle tree (no block barriers).
 template <typename R>
 __global__ void __launch_bounds__(256)
 step_small_kernel(StepParams s, ContractArgs a, const typename C2T<R>::T *ket, const typename C2T<R>::T *bra,
                   const typename C2T<R>::T *tin, OutDesc out) {
   using V = typename C2T<R>::T;
-  __shared__ V red[256 / 32];
   const int64_t item = blockIdx.x;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   ItemCtx c = item_ctx(a, s, item);
   const V *kp = ket + s.ket_off + c.sa;
   const V *bp = bra + c.b * a.bra_stride + s.bra_off + c.sb;
   const V *tp = tin + item * a.t_stride;
   const int32_t *bka = a.tab + s.t_bka, *bkb = a.tab + s.t_bkb;
   const int32_t *bna = a.tab + s.t_bna, *bnb = a.tab + s.t_bnb, *ocol = a.tab + s.t_ocol;
-  for (int64_t oi = 0; oi < s.M * s.N; ++oi) {
-    int64_t m = oi / s.N, n = oi % s.N;
+  for (int64_t oi = warp; oi < s.M * s.N; oi += 8) {
+    const int64_t m = oi / s.N, n = oi % s.N;
     V acc = cz<V>();
-    for (int64_t k = tid; k < s.K; k += 256) {
+    for (int64_t k = lane; k < s.K; k += 32) {
       V cv = overlap_elem(kp, bp, (int64_t)bka[k] + bna[n], (int64_t)bkb[k] + bnb[n], s.ket_sig, s.bra_sig, s.phys);
       acc = cfma(tp[m * s.K + k], cv, acc);
     }
@@ -177,15 +177,44 @@ step_small_kernel(StepParams s, ContractArgs a, const typename C2T<R>::T *ket, c
       acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
       acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
     }
-    if (lane == 0) red[warp] = acc;
-    __syncthreads();
-    if (tid == 0) {
-      V t = cz<V>();
-      for (int w = 0; w < 256 / 32; ++w) { t.x += red[w].x; t.y += red[w].y; }
-      store_out(out, a.t_stride, item, orow_of(s, m) + ocol[n], t);
-    }
-    __syncthreads();
+    if (lane == 0) store_out(out, a.t_stride, item, orow_of(s, m) + ocol[n], acc);
   }
+}
+
+// Few rows, many columns (M <= 16, M * K <= 2048): the item's M x K input block sits in shared memory
+// and each thread forms its column n of the overlap tensor on the fly and writes M outputs.
+template <typename R>
+__global__ void __launch_bounds__(256)
+step_narrow_kernel(StepParams s, ContractArgs a, const typename C2T<R>::T *ket, const typename C2T<R>::T *bra,
+                   const typename C2T<R>::T *tin, OutDesc out) {
+  using V = typename C2T<R>::T;
+  __shared__ V Ts[2048];
+  const int64_t ctas_n = (s.N + 255) / 256;
+  const int64_t item = blockIdx.x / ctas_n;
+  const int64_t n = (blockIdx.x % ctas_n) * 256 + threadIdx.x;
+  ItemCtx c = item_ctx(a, s, item);
+  const V *tp = tin + item * a.t_stride;
+  const int MK = (int)(s.M * s.K);
+  for (int i = threadIdx.x; i < MK; i += 256) Ts[i] = tp[i];
+  __syncthreads();
+  if (n >= s.N) return;
+  const V *kp = ket + s.ket_off + c.sa;
+  const V *bp = bra + c.b * a.bra_stride + s.bra_off + c.sb;
+  const int32_t *bka = a.tab + s.t_bka, *bkb = a.tab + s.t_bkb;
+  const int64_t ia_n = a.tab[s.t_bna + n], ib_n = a.tab[s.t_bnb + n];
+  V acc[16];
+#pragma unroll
+  for (int m = 0; m < 16; ++m) acc[m] = cz<V>();
+  for (int64_t k = 0; k < s.K; ++k) {
+    const V cv = overlap_elem(kp, bp, (int64_t)bka[k] + ia_n, (int64_t)bkb[k] + ib_n, s.ket_sig, s.bra_sig, s.phys);
+#pragma unroll
+    for (int m = 0; m < 16; ++m)
+      if (m < s.M) acc[m] = cfma(Ts[m * s.K + k], cv, acc[m]);
+  }
+  const int oc = a.tab[s.t_ocol + n];
+#pragma unroll
+  for (int m = 0; m < 16; ++m)
+    if (m < s.M) store_out(out, a.t_stride, item, orow_of(s, m) + oc, acc[m]);
 }
 
 // Streaming step for small K and N (K, N <= 16) and many rows: the item's C tile sits in shared
@@ -396,6 +425,7 @@ bool simt_variant_ok(const StepParams &s, int v) {
     case SIMT_STREAM: return s.K <= 16 && s.N <= 16;
     case SIMT_FIXED: return has_fixed(s.K, s.N);
     case SIMT_SMALL: return s.M * s.N <= 256;
+    case SIMT_NARROW: return s.M <= 16 && s.M * s.K <= 2048;
     default: return false;
   }
 }
@@ -410,6 +440,7 @@ cudaError_t launch_step(const StepParams &s, const ContractArgs &a, const void *
     if (s.M >= 512 && has_fixed(s.K, s.N)) variant = SIMT_FIXED;
     else if (s.K <= 16 && s.N <= 16 && s.M >= 512) variant = SIMT_STREAM;
     else if (s.M * s.N <= 16) variant = SIMT_SMALL;
+    else if (s.M <= 16 && s.M * s.K <= 2048 && s.N >= 256) variant = SIMT_NARROW;
     else variant = s.N >= 48 ? SIMT_T64 : s.N >= 12 ? SIMT_T128 : SIMT_T256;
   }
   switch (variant) {
@@ -425,6 +456,14 @@ cudaError_t launch_step(const StepParams &s, const ContractArgs &a, const void *
       if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
       step_stream_kernel<R><<<(unsigned)grid, 256, 0, st>>>(s, a, (const V *)ket, (const V *)bra, (const V *)t_in,
                                                             t_out, rows);
+      tn_count_launch(1);
+      return cudaGetLastError();
+    }
+    case SIMT_NARROW: {
+      const int64_t grid = ((s.N + 255) / 256) * a.items;
+      if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+      step_narrow_kernel<R><<<(unsigned)grid, 256, 0, st>>>(s, a, (const V *)ket, (const V *)bra, (const V *)t_in,
+                                                            t_out);
       tn_count_launch(1);
       return cudaGetLastError();
     }

@@ -126,7 +126,7 @@ cudaError_t launch_step(const StepParams &s, const ContractArgs &a, const void *
                         const void *t_in, const OutDesc &out, cudaStream_t st, int variant = 0);
 // SIMT step kernels: the shape heuristic or one kernel forced (the autotuner's candidates)
 enum SimtVariant { SIMT_AUTO = 0, SIMT_T64 = 1, SIMT_T128 = 2, SIMT_T256 = 3, SIMT_STREAM = 4, SIMT_FIXED = 5,
-                   SIMT_SMALL = 6 };
+                   SIMT_SMALL = 6, SIMT_NARROW = 7 };
 bool simt_variant_ok(const StepParams &s, int variant);
 // out[b] (+)= sum over the group's slices, in slice order, in FP64 (accumulate: add to out)
 template <typename R>

@@ -113,7 +113,7 @@ def _load():
         "tn_autotune": (i32, [vp, i32, i64, vp, C.POINTER(i32)]),
         "tn_plan_kernels": (i32, [vp, i32, C.POINTER(i32)]),
         "tn_plan_set_kernels": (i32, [vp, i32, C.POINTER(i32)]),
-        "tn_batch_create": (i32, [C.POINTER(vp), i32, vp, C.POINTER(i64), i32, vp, C.POINTER(vp)]),
+        "tn_batch_create": (i32, [C.POINTER(vp), i32, vp, C.POINTER(i64), i32, dbl, vp, C.POINTER(vp)]),
         "tn_batch_set_bits": (i32, [vp, vp, vp]),
         "tn_batch_run": (i32, [vp, vp]),
         "tn_batch_read": (i32, [vp, vp, vp]),
@@ -511,7 +511,7 @@ def tn_server_stats_get(s: Server) -> dict:
 # kernel autotuning and batched circuits
 # ---------------------------------------------------------------------------
 KERNEL_NAMES = {0: "simt_auto", 1: "simt_tile64x64", 2: "simt_tile128x16", 3: "simt_tile256x4",
-                4: "simt_stream", 5: "simt_stream_fixed", 6: "simt_small", 16: "tcgen05_split",
+                4: "simt_stream", 5: "simt_stream_fixed", 6: "simt_small", 7: "simt_narrow", 16: "tcgen05_split",
                 32: "tcgen05_tma_buildb", 33: "tcgen05_tma_buildb_bn128", 34: "tcgen05_tma_buildb_bn64",
                 40: "tcgen05_tma_loadb", 41: "tcgen05_tma_loadb_bn128", 42: "tcgen05_tma_loadb_bn64",
                 48: "tcgen05_tma", 49: "tcgen05_tma_bn128", 50: "tcgen05_tma_bn64"}
@@ -580,14 +580,15 @@ class Batch:
         return np.split(flat, np.cumsum(self.counts)[:-1])
 
 
-def tn_batch_create(plans, bits_list, prec: str = "bf16x6", stream=None) -> Batch:
-    """``bits_list[i]``: circuit i's bitstrings ((B_i, n_i) 0/1 or packed uint64 words)."""
+def tn_batch_create(plans, bits_list, prec: str = "bf16x6", hbm_budget_bytes: float = 0.0, stream=None) -> Batch:
+    """``bits_list[i]``: circuit i's bitstrings ((B_i, n_i) 0/1 or packed uint64 words);
+    ``hbm_budget_bytes``: bound on all circuits' workspaces together (0: none)."""
     flat, counts = _packed_concat(plans, bits_list)
     arr = (C.c_void_p * len(plans))(*[p.ptr for p in plans])
     out = C.c_void_p()
     _check(LIB.tn_batch_create(arr, len(plans), C.c_void_p(flat.ctypes.data),
                                counts.ctypes.data_as(C.POINTER(C.c_int64)), PRECISIONS[prec],
-                               _stream_handle(stream), C.byref(out)))
+                               float(hbm_budget_bytes), _stream_handle(stream), C.byref(out)))
     return Batch(out.value, plans, counts, prec)
 
 
