@@ -1218,6 +1218,61 @@ static void merge_nodes(Net &g, const std::vector<char> &keep_edge) {
   g = h;
 }
 
+// Every device index a compiled plan can produce, checked on the host before any launch: node
+// tensors inside their items, the tables' offsets inside their node's tensor, each step's input
+// and output inside the intermediate's item stride, the merges' reads and writes inside their
+// slots. A violation is an internal error of the compiler, reported instead of launched.
+static tn_status validate_plan(const tn_plan *p) {
+  const Net &g = p->net;
+  const std::vector<int32_t> &tab = p->tab_host;
+  auto bad = [](const char *what, int j, long long v, long long lim) {
+    return tn_fail(TN_ERR_UNSUPPORTED, "plan check failed: %s (step or node %d: %lld >= %lld)", what, j, v, lim);
+  };
+  auto tmax = [&](int64_t off, int64_t n) {
+    int64_t m = 0;
+    for (int64_t i = 0; i < n; ++i) m = std::max<int64_t>(m, tab[off + i]);
+    return m;
+  };
+  for (int i = 0; i < g.n; ++i) {
+    int64_t sk = g.phys[i], sb = g.phys[i];
+    for (int e : g.legs[i]) { sk *= g.dk[e]; sb *= g.db[e]; }
+    if (g.ket_off[i] + sk > g.ket_elems) return bad("ket node tensor outside the item", i, g.ket_off[i] + sk, g.ket_elems);
+    if (g.bra_off[i] + sb > g.bra_elems) return bad("bra node tensor outside the item", i, g.bra_off[i] + sb, g.bra_elems);
+  }
+  for (int h = 0; h < 2; ++h) {
+    const std::vector<MergeParams> &ms = h ? g.mb : g.mk;
+    const int64_t lim = h ? g.bra_elems : g.ket_elems;
+    for (size_t t = 0; t < ms.size(); ++t) {
+      const MergeParams &m = ms[t];
+      int64_t ru = (int64_t)(m.pu - 1) * m.su_p + (int64_t)(m.da - 1) * m.su_a, rv = (int64_t)(m.pv - 1) * m.sv_p + (int64_t)(m.da - 1) * m.sv_a;
+      for (int q = 0; q < m.nu; ++q) ru += (int64_t)(m.du[q] - 1) * m.su[q];
+      for (int q = 0; q < m.nv; ++q) rv += (int64_t)(m.dv[q] - 1) * m.sv[q];
+      if (ru >= (int64_t)m.pu * m.su_p) return bad("merge reads outside U", (int)t, ru, (int64_t)m.pu * m.su_p);
+      if (rv >= (int64_t)m.pv * m.sv_p) return bad("merge reads outside V", (int)t, rv, (int64_t)m.pv * m.sv_p);
+      if (m.u_off + m.pu * m.su_p > lim || m.v_off + m.pv * m.sv_p > lim || m.out_off + m.out_size > lim)
+        return bad("merge slot outside the item", (int)t, m.out_off + m.out_size, lim);
+    }
+  }
+  for (size_t j = 0; j < p->steps.size(); ++j) {
+    const StepParams &s = p->steps[j];
+    const int i = p->order[j];
+    int64_t tk = s.phys * s.ket_sig, tb = s.phys * s.bra_sig;   // the node's tensor sizes
+    const int64_t ka = tmax(s.t_sa, p->n_slices) + tmax(s.t_bna, s.N) + (j ? tmax(s.t_bka, s.K) : 0) +
+                       (s.phys - 1) * s.ket_sig;
+    const int64_t kb = tmax(s.t_sb, p->n_slices) + tmax(s.t_bnb, s.N) + (j ? tmax(s.t_bkb, s.K) : 0) +
+                       (s.phys - 1) * s.bra_sig;
+    if (ka >= tk) return bad("ket offsets outside the node tensor", (int)j, ka, tk);
+    if (kb >= tb) return bad("bra offsets outside the node tensor", (int)j, kb, tb);
+    if (s.ket_off != g.ket_off[i] || s.bra_off != g.bra_off[i]) return bad("node offset mismatch", (int)j, 0, 0);
+    if (j > 0 && s.M * s.K > p->maxT) return bad("step input larger than the item stride", (int)j, s.M * s.K, p->maxT);
+    int64_t orow = 0;
+    for (int r = 0; r < s.n_rest; ++r) orow += (int64_t)(s.rest_dim[r] - 1) * s.rest_ostride[r];
+    const int64_t omax = orow + tmax(s.t_ocol, s.N);
+    if (omax >= p->maxT) return bad("step output outside the item stride", (int)j, omax, p->maxT);
+  }
+  return TN_OK;
+}
+
 static tn_status compile_plan(tn_plan *p) {
   const Net &c = p->net;
   const int n = c.n;
@@ -1402,7 +1457,7 @@ static tn_status compile_plan(tn_plan *p) {
   p->maxT = maxT;
   p->cmacs = cmacs * (double)p->n_slices;
   p->bytes = bytes * (double)p->n_slices;
-  return TN_OK;
+  return validate_plan(p);
 }
 
 static void fill_info(const tn_plan *p, tn_plan_info *info) {
