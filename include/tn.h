@@ -254,16 +254,18 @@ typedef struct tn_batch tn_batch;
 
 /* Several circuits (their plans, each with its own batch of bitstrings; shapes may differ) as one
  * CUDA graph. bits: every circuit's bitstrings concatenated in plan order, circuit i taking
- * n_bits[i] rows of ceil(n_qubits_i/64) words; host or device memory, copied. The batch owns
- * device buffers for the bitstrings, the results and one workspace per circuit (allocated through
- * each circuit's allocator); hbm_budget_bytes > 0 bounds the workspaces together (each circuit
- * then runs its bitstrings in chunks that fit a share of the budget proportional to its whole
- * need; 0: each plan's own chunk). It runs every circuit once on `cuda_stream` to validate it, and
- * captures the whole batch (one independent branch per circuit: bra evolution, overlap,
- * contraction with the plan's kernels, FP64 slice sum) into one graph. Plans and circuits must
- * outlive the batch; re-evolving a circuit invalidates it. The paper has no counterpart: this is
- * the batching of many circuits into one launch.
- * Errors: TN_ERR_ARG, TN_ERR_STATE, TN_ERR_CUDA, TN_ERR_OOM, TN_ERR_TIMEOUT. */
+ * n_bits[i] rows of ceil(n_qubits_i/64) words; host or device memory, copied. Each circuit runs
+ * its bitstrings in chunks of its plan's batch size (info.chunk_bitstrings). The circuits are
+ * grouped, in order, into waves whose workspaces fit hbm_budget_bytes side by side (0: one wave
+ * of all); the waves run one after another and share one workspace arena, so the batch holds the
+ * largest wave's workspaces plus the bitstrings and results (allocated through the first
+ * circuit's allocator). It runs every circuit once on `cuda_stream` to validate it and captures
+ * the whole batch (per wave one independent branch per circuit: bra evolution, overlap,
+ * contraction with the plan's kernels, FP64 slice sum) into one graph; a graph of more than
+ * 100000 kernels is refused (TN_ERR_UNSUPPORTED). Plans and circuits must outlive the batch;
+ * re-evolving a circuit invalidates it. The paper has no counterpart: this is the batching of
+ * many circuits into one launch.
+ * Errors: TN_ERR_ARG, TN_ERR_STATE, TN_ERR_CUDA, TN_ERR_OOM, TN_ERR_TIMEOUT, TN_ERR_UNSUPPORTED. */
 tn_status tn_batch_create(tn_plan *const *plans, int32_t n_plans, const uint64_t *bits, const int64_t *n_bits,
                           tn_precision prec, double hbm_budget_bytes, void *cuda_stream, tn_batch **out);
 

@@ -1,18 +1,24 @@
 // Batched circuits: the amplitudes of many circuits (each with its own graph, gates, plan and batch
 // of bitstrings, shapes uneven) computed by one CUDA graph launch.
 //
-// tn_batch_create gives every circuit its own resident workspace, bitstring and result buffers,
-// runs each circuit once on the stream (this validates the plans and sets up the kernels), and
-// then captures the whole batch into one CUDA graph: a fork into one branch per circuit, each
-// branch the circuit's full path (bra evolution with the batched FP64 SVD, overlap formation, the
-// path-ordered contraction steps with the plan's tuned kernels, the FP64 cross-slice sum), and a
-// join. The branches have no dependencies between them, so the device runs the circuits
-// concurrently and small circuits fill the SMs together. tn_batch_run is one cudaGraphLaunch.
+// tn_batch_create groups the circuits into waves whose workspaces fit the memory budget side by
+// side (each circuit keeps its plan's batch size), carves every wave's workspaces from one
+// resident arena that the next wave reuses, runs each circuit once on the stream (this validates
+// the plans and sets the kernels up), and captures the whole batch into one CUDA graph: per wave
+// a fork into one branch per circuit, each branch the circuit's full path (bra evolution with the
+// batched FP64 SVD, overlap formation, the path-ordered contraction steps with the plan's tuned
+// kernels, the FP64 cross-slice sum), and a join before the next wave. Branches of a wave have no
+// dependencies, so the device runs those circuits concurrently and small circuits fill the SMs
+// together. Graphs above TN_BATCH_MAX_NODES kernel nodes are refused (a budget too small for the
+// circuits' batch sizes would otherwise make one from very many tiny chunks). tn_batch_run is one
+// cudaGraphLaunch.
 #include <algorithm>
 #include <cstring>
 #include <vector>
 
 #include "tn_host.h"
+
+#define TN_BATCH_MAX_NODES 100000
 
 struct tn_batch {
   struct Item {
@@ -21,12 +27,14 @@ struct tn_batch {
     int64_t n = 0;
     int words = 1;
     int64_t bits_off = 0, res_off = 0;   // in words / in amplitudes
-    Workspace w;
+    int wave = 0;
+    Workspace w;                         // carved from the arena (not owned)
   };
   std::vector<Item> items;
+  int n_waves = 0;
   tn_precision prec = TN_FP64;
   DevMem *mem = nullptr;                 // allocator of the shared buffers (the first plan's circuit)
-  Buf bits, res;
+  Buf bits, res, arena, errs;            // errs: two error words per circuit, outside the arena
   int64_t total_words = 0, total_amps = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -41,10 +49,11 @@ void destroy(tn_batch *b) {
   cudaDeviceSynchronize();
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
-  for (auto &it : b->items) ws_release(it.p->c->mem, it.w);
   if (b->mem) {
     b->mem->release(b->bits);
     b->mem->release(b->res);
+    b->mem->release(b->arena);
+    b->mem->release(b->errs);
   }
   delete b;
 }
@@ -100,12 +109,24 @@ tn_status capture(tn_batch *b) {
     return tn_fail(TN_ERR_CUDA, "cudaStreamBeginCapture: %s", cudaGetErrorString(e));
   }
   const int64_t counted = tn_launch_count(0);   // captured launches run later, counted per graph launch
-  e = cudaEventRecord(ev[n], cs);   // fork
-  for (size_t i = 0; i < n && e == cudaSuccess && s == TN_OK; ++i) {
-    e = cudaStreamWaitEvent(bs[i], ev[n], 0);
-    if (e == cudaSuccess) s = enqueue_item(b, b->items[i], bs[i]);
-    if (e == cudaSuccess && s == TN_OK) e = cudaEventRecord(ev[i], bs[i]);
-    if (e == cudaSuccess && s == TN_OK) e = cudaStreamWaitEvent(cs, ev[i], 0);   // join
+  e = cudaEventRecord(ev[n], cs);   // fork of the first wave
+  for (int wv = 0; wv < b->n_waves && e == cudaSuccess && s == TN_OK; ++wv) {
+    std::vector<size_t> members;
+    for (size_t i = 0; i < n; ++i)
+      if (b->items[i].wave == wv) members.push_back(i);
+    for (size_t i : members) {
+      if (e != cudaSuccess || s != TN_OK) break;
+      e = cudaStreamWaitEvent(bs[i], ev[n], 0);
+      if (e == cudaSuccess) s = enqueue_item(b, b->items[i], bs[i]);
+      if (e == cudaSuccess && s == TN_OK) e = cudaEventRecord(ev[i], bs[i]);
+      if (e == cudaSuccess && s == TN_OK) e = cudaStreamWaitEvent(cs, ev[i], 0);   // join
+    }
+    if (e == cudaSuccess && s == TN_OK) e = cudaEventRecord(ev[n], cs);   // fork of the next wave
+    if (s == TN_OK && tn_launch_count(0) - counted > TN_BATCH_MAX_NODES)
+      s = tn_fail(TN_ERR_UNSUPPORTED,
+                  "tn_batch_create: more than %d kernels in one graph; give the batch more memory "
+                  "(hbm_budget_bytes) or plans with larger batches",
+                  TN_BATCH_MAX_NODES);
   }
   cudaGraph_t g = nullptr;
   const cudaError_t ee = cudaStreamEndCapture(cs, &g);
@@ -180,24 +201,38 @@ extern "C" tn_status tn_batch_create(tn_plan *const *plans, int32_t n_plans, con
   b->mem = &plans[0]->c->mem;
   tn_status s = b->mem->ensure(b->bits, (size_t)b->total_words * 8, st);
   if (s == TN_OK) s = b->mem->ensure(b->res, (size_t)b->total_amps * sizeof(tn_c128), st);
-  b->device_bytes = (int64_t)(b->bits.bytes + b->res.bytes);
-  // each circuit's batch of bitstrings: its whole set, within its plan's chunk, and within its
-  // share of the budget (shares proportional to what the whole sets would need)
-  double need = 0;
-  for (auto &it : b->items) need += (double)plan_ws_bytes(it.p, kind, it.n, it.p->slice_chunk[kind]);
-  for (auto &it : b->items) {
-    if (s != TN_OK) break;
-    int64_t ch = std::min<int64_t>(it.n, it.p->chunk[kind]);
-    if (hbm_budget_bytes > 0 && need > hbm_budget_bytes) {
-      const double whole = (double)plan_ws_bytes(it.p, kind, it.n, it.p->slice_chunk[kind]);
-      const double share = hbm_budget_bytes * whole / need;
-      const double fixed = (double)plan_ws_bytes(it.p, kind, 0, it.p->slice_chunk[kind]);
-      const double per = (double)plan_ws_bytes(it.p, kind, 1, it.p->slice_chunk[kind]) - fixed;
-      ch = std::min<int64_t>(ch, std::max<int64_t>(1, (int64_t)((share - fixed) / std::max(per, 1.0))));
+  // waves: circuits in order, each with its plan's own batch size, side by side while their
+  // workspaces fit the budget (a circuit alone is always a wave); one arena for the largest wave
+  std::vector<WsSizes> z(b->items.size());
+  std::vector<int64_t> chunk(b->items.size());
+  int64_t wave_bytes = 0, arena = 0;
+  for (size_t i = 0; i < b->items.size(); ++i) {
+    tn_batch::Item &it = b->items[i];
+    chunk[i] = std::max<int64_t>(1, std::min<int64_t>(it.n, it.p->chunk[kind]));
+    z[i] = ws_sizes(it.p, kind, chunk[i], it.p->slice_chunk[kind]);
+    if (i > 0 && hbm_budget_bytes > 0 && (double)(wave_bytes + z[i].total) > hbm_budget_bytes) {
+      ++b->n_waves;
+      wave_bytes = 0;
     }
-    s = ws_ensure_sized(it.p, it.w, kind, ch, it.p->slice_chunk[kind], st);
-    b->device_bytes += plan_ws_bytes(it.p, kind, ch, it.p->slice_chunk[kind]);
+    it.wave = b->n_waves;
+    wave_bytes += z[i].total;
+    arena = std::max(arena, wave_bytes);
   }
+  ++b->n_waves;
+  if (s == TN_OK) s = b->mem->ensure(b->arena, (size_t)std::max<int64_t>(arena, 256), st);
+  if (s == TN_OK) s = b->mem->ensure(b->errs, b->items.size() * 64, st);
+  if (s == TN_OK) {
+    int64_t off = 0;
+    int cur = -1;
+    for (size_t i = 0; i < b->items.size(); ++i) {
+      tn_batch::Item &it = b->items[i];
+      if (it.wave != cur) { cur = it.wave; off = 0; }
+      ws_carve(it.w, static_cast<unsigned char *>(b->arena.p) + off, z[i], chunk[i], it.p->slice_chunk[kind], st);
+      it.w.err.p = static_cast<unsigned char *>(b->errs.p) + i * 64;   // survives the later waves
+      off += z[i].total;
+    }
+  }
+  b->device_bytes = (int64_t)(b->bits.bytes + b->res.bytes + b->arena.bytes + b->errs.bytes);
   if (s == TN_OK) s = upload_bits(b, bits, st);
   // one eager pass: validates every plan and sets the kernels up before the capture
   for (auto &it : b->items)

@@ -1605,26 +1605,52 @@ void ws_release(DevMem &mem, Workspace &w) {
   mem.release(w.ket32);
 }
 
-tn_status ws_ensure_sized(tn_plan *p, Workspace &w, int kind, int64_t ch, int64_t sc, cudaStream_t st) {
-  tn_circuit *c = p->c;
-  DevMem &mem = c->mem;
+// Byte sizes of a workspace's buffers for `ch` bitstrings of `sc` slices each (the FP64 form when
+// kind == 0, the complex64 / tensor-core forms when kind == 1).
+WsSizes ws_sizes(const tn_plan *p, int kind, int64_t ch, int64_t sc) {
+  const tn_circuit *c = p->c;
   const int words = (c->n + 63) / 64;
-  const int64_t el = kind == 0 ? 16 : 8;
-  tn_status s;
-  if ((s = mem.ensure(w.bits, ch * words * 8, st)) != TN_OK) return s;
-  if ((s = mem.ensure(w.bra64, ch * p->net.bra_elems * 16, st)) != TN_OK) return s;
-  if (kind && (s = mem.ensure(w.bra32, ch * p->net.bra_elems * 8, st)) != TN_OK) return s;
-  if (p->net.merged()) {
-    if ((s = mem.ensure(w.ket64, p->net.ket_elems * 16, st)) != TN_OK) return s;
-    if (kind && (s = mem.ensure(w.ket32, p->net.ket_elems * 8, st)) != TN_OK) return s;
+  WsSizes z;
+  z.b[WS_BITS] = ch * words * 8;
+  z.b[WS_BRA64] = ch * p->net.bra_elems * 16;
+  z.b[WS_BRA32] = kind ? ch * p->net.bra_elems * 8 : 0;
+  z.b[WS_KET64] = p->net.merged() ? p->net.ket_elems * 16 : 0;
+  z.b[WS_KET32] = p->net.merged() && kind ? p->net.ket_elems * 8 : 0;
+  z.b[WS_GWORK] = ch * std::max<int64_t>(c->bra.max_work, 1) * 16;
+  z.b[WS_T0] = z.b[WS_T1] = ch * sc * p->maxT * (kind ? 12 : 16);
+  z.b[WS_CBUF] = kind ? ch * sc * p->maxKN * 24 : 0;
+  z.b[WS_RES] = ch * 16;
+  z.b[WS_ERR] = 64;
+  z.total = 0;
+  for (int i = 0; i < WS_NBUF; ++i) z.total += (z.b[i] + 255) & ~int64_t(255);
+  return z;
+}
+
+static Buf *ws_buf(Workspace &w, int i) {
+  Buf *t[WS_NBUF] = {&w.bits, &w.bra64, &w.bra32, &w.ket64, &w.ket32, &w.gwork, &w.t0, &w.t1, &w.cbuf, &w.res, &w.err};
+  return t[i];
+}
+
+void ws_carve(Workspace &w, void *base, const WsSizes &z, int64_t ch, int64_t sc, cudaStream_t st) {
+  unsigned char *cur = static_cast<unsigned char *>(base);
+  for (int i = 0; i < WS_NBUF; ++i) {
+    Buf &b = *ws_buf(w, i);
+    b.p = z.b[i] ? cur : nullptr;
+    b.bytes = (size_t)z.b[i];
+    b.stream = st;
+    cur += (z.b[i] + 255) & ~int64_t(255);
   }
-  if ((s = mem.ensure(w.gwork, ch * std::max<int64_t>(c->bra.max_work, 1) * 16, st)) != TN_OK) return s;
-  const int64_t tel = kind ? 12 : el;
-  if ((s = mem.ensure(w.t0, ch * sc * p->maxT * tel, st)) != TN_OK) return s;
-  if ((s = mem.ensure(w.t1, ch * sc * p->maxT * tel, st)) != TN_OK) return s;
-  if (kind && (s = mem.ensure(w.cbuf, ch * sc * p->maxKN * 24, st)) != TN_OK) return s;
-  if ((s = mem.ensure(w.res, ch * 16, st)) != TN_OK) return s;
-  if ((s = mem.ensure(w.err, 64, st)) != TN_OK) return s;
+  w.chunk = (int)ch;
+  w.slice_chunk = sc;
+}
+
+tn_status ws_ensure_sized(tn_plan *p, Workspace &w, int kind, int64_t ch, int64_t sc, cudaStream_t st) {
+  DevMem &mem = p->c->mem;
+  const WsSizes z = ws_sizes(p, kind, ch, sc);
+  for (int i = 0; i < WS_NBUF; ++i) {
+    tn_status s = mem.ensure(*ws_buf(w, i), (size_t)z.b[i], st);
+    if (s != TN_OK) return s;
+  }
   w.chunk = (int)ch;
   w.slice_chunk = sc;
   return TN_OK;

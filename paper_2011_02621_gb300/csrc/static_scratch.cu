@@ -42,34 +42,6 @@ tn_status scratch_address(void **out) {
   return TN_OK;
 }
 
-size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
-
-// Byte sizes of the workspace buffers for `ch` bitstrings of `sc` slices each (the sizes the
-// workspace set-up asks for; each buffer is given exactly that capacity below).
-struct Sizes {
-  size_t bits, bra64, bra32, gwork, t, cbuf, res, err, ket64, ket32, total;
-};
-
-Sizes sizes_for(const tn_plan *p, int kind, int64_t ch, int64_t sc) {
-  const tn_circuit *c = p->c;
-  const int words = (c->n + 63) / 64;
-  const int64_t tel = kind ? 12 : 16;
-  Sizes z;
-  z.bits = (size_t)(ch * words * 8);
-  z.bra64 = (size_t)(ch * p->net.bra_elems * 16);
-  z.bra32 = kind ? (size_t)(ch * p->net.bra_elems * 8) : 0;
-  z.ket64 = p->net.merged() ? (size_t)(p->net.ket_elems * 16) : 0;
-  z.ket32 = p->net.merged() && kind ? (size_t)(p->net.ket_elems * 8) : 0;
-  z.gwork = (size_t)(ch * std::max<int64_t>(c->bra.max_work, 1) * 16);
-  z.t = (size_t)(ch * sc * p->maxT * tel);
-  z.cbuf = kind ? (size_t)(ch * sc * p->maxKN * 24) : 0;
-  z.res = (size_t)(ch * 16);
-  z.err = 64;
-  z.total = up256(z.bits) + up256(z.bra64) + up256(z.bra32) + up256(z.gwork) + 2 * up256(z.t) + up256(z.cbuf) +
-            up256(z.res) + up256(z.err) + up256(z.ket64) + up256(z.ket32);
-  return z;
-}
-
 // allocator that refuses: if the workspace set-up ever asked for more than was carved, the call
 // fails with TN_ERR_OOM instead of allocating
 void *refuse_alloc(size_t, void *, void *) { return nullptr; }
@@ -84,23 +56,23 @@ extern "C" tn_status tn_amplitudes_static(tn_plan *p, const uint64_t *bits, int6
   if (n == 0) return TN_OK;
   if (n < 0 || !bits || !out) return tn_fail(TN_ERR_ARG, "tn_amplitudes_static: bad arguments");
   const int kind = prec == TN_FP64 ? 0 : 1;
-  const size_t cap = TN_STATIC_SCRATCH_BYTES;
+  const int64_t cap = (int64_t)TN_STATIC_SCRATCH_BYTES;
   // as many whole bitstrings as fit; else one bitstring with as many of its slices as fit
   int64_t ch = 0, sc = p->n_slices;
   {
-    const size_t one = sizes_for(p, kind, 1, sc).total;
+    const int64_t one = ws_sizes(p, kind, 1, sc).total;
     if (one <= cap) {
-      ch = (int64_t)(cap / one);
+      ch = cap / one;
       ch = std::min<int64_t>(std::min<int64_t>(ch, n), 1 << 16);
-      while (ch > 1 && sizes_for(p, kind, ch, sc).total > cap) --ch;
+      while (ch > 1 && ws_sizes(p, kind, ch, sc).total > cap) --ch;
     } else {
       ch = 1;
-      while (sc > 1 && sizes_for(p, kind, 1, sc).total > cap) sc = (sc + 1) / 2;
-      if (sizes_for(p, kind, 1, sc).total > cap)
+      while (sc > 1 && ws_sizes(p, kind, 1, sc).total > cap) sc = (sc + 1) / 2;
+      if (ws_sizes(p, kind, 1, sc).total > cap)
         return tn_fail(TN_ERR_UNSUPPORTED,
-                       "tn_amplitudes_static: one bitstring and one slice need %zu bytes of scratch, more than the "
-                       "%zu-byte static scratch; use tn_amplitudes or more cuts (smaller max_intermediate)",
-                       sizes_for(p, kind, 1, 1).total, cap);
+                       "tn_amplitudes_static: one bitstring and one slice need %lld bytes of scratch, more than the "
+                       "%lld-byte static scratch; use tn_amplitudes or more cuts (smaller max_intermediate)",
+                       (long long)ws_sizes(p, kind, 1, 1).total, (long long)cap);
     }
   }
   void *base = nullptr;
@@ -118,25 +90,7 @@ extern "C" tn_status tn_amplitudes_static(tn_plan *p, const uint64_t *bits, int6
   q.chunk[kind] = (int)ch;
   q.slice_chunk[kind] = sc;
   q.ws = Workspace();
-  const Sizes z = sizes_for(p, kind, ch, sc);
-  unsigned char *cur = static_cast<unsigned char *>(base);
-  auto carve = [&](Buf &b, size_t bytes) {
-    b.p = bytes ? cur : nullptr;
-    b.bytes = bytes;
-    b.stream = (cudaStream_t)cuda_stream;
-    cur += up256(bytes);
-  };
-  carve(q.ws.bits, z.bits);
-  carve(q.ws.bra64, z.bra64);
-  carve(q.ws.bra32, z.bra32);
-  carve(q.ws.gwork, z.gwork);
-  carve(q.ws.t0, z.t);
-  carve(q.ws.t1, z.t);
-  carve(q.ws.cbuf, z.cbuf);
-  carve(q.ws.res, z.res);
-  carve(q.ws.err, z.err);
-  carve(q.ws.ket64, z.ket64);
-  carve(q.ws.ket32, z.ket32);
+  ws_carve(q.ws, base, ws_sizes(p, kind, ch, sc), ch, sc, (cudaStream_t)cuda_stream);
   // the error words are cleared by the run itself; every other buffer is written before read
   return run_amplitudes(&q, q.ws, bits, n, prec, out, (cudaStream_t)cuda_stream);
 }

@@ -129,6 +129,14 @@ tn_path_opts tn_default_opts();
 int64_t plan_ws_bytes(const tn_plan *p, int kind, int64_t chunk, int64_t slices);
 tn_status ws_ensure(tn_plan *p, Workspace &w, int kind, cudaStream_t st);
 tn_status ws_ensure_sized(tn_plan *p, Workspace &w, int kind, int64_t chunk, int64_t slices, cudaStream_t st);
+// buffer sizes of a workspace, and a workspace laid out (256-byte aligned, not owned) in given memory
+enum { WS_BITS, WS_BRA64, WS_BRA32, WS_KET64, WS_KET32, WS_GWORK, WS_T0, WS_T1, WS_CBUF, WS_RES, WS_ERR, WS_NBUF };
+struct WsSizes {
+  int64_t b[WS_NBUF];
+  int64_t total;                                  // with 256-byte alignment of every buffer
+};
+WsSizes ws_sizes(const tn_plan *p, int kind, int64_t chunk, int64_t slices);
+void ws_carve(Workspace &w, void *base, const WsSizes &z, int64_t chunk, int64_t slices, cudaStream_t st);
 bool is_device_ptr(const void *p);
 // one contraction step j with kernel k (with the overlap formation that kernel needs); no host sync
 cudaError_t enqueue_step(const tn_plan *p, const Workspace &w, size_t j, int k, tn_precision prec,
