@@ -182,7 +182,8 @@ class Clocks:
 # GPU arm
 # ---------------------------------------------------------------------------
 def traffic_record(kind):
-    """dram bytes per launch of `kind` from the committed ncu summary, if the kernel source is unchanged."""
+    """DRAM bytes of `kind` per bitstring and step, from a committed ncu capture of a small case
+    (profiles/traffic.json), if the kernel sources are unchanged since the capture."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
@@ -518,7 +519,8 @@ def main():
         roof = {"bound": "hbm", "achieved": bytes_pl / per_launch_s / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     tr = traffic_record(kind)
-    roof["traffic"] = tr["dram_bytes_per_launch"] if tr else None
+    # scaled to this run's launches by the bitstrings they process (traffic grows in proportion)
+    roof["traffic"] = tr["dram_bytes_per_bitstring_step"] * B / (rec["launches"] / args.steps) if tr else None
     roof.update({"kernel": kind, "launches_per_step": rec["launches"] / args.steps,
                  "algorithmic_bytes_per_launch": bytes_pl, "algorithmic_flops_per_launch": flops_pl,
                  "avg_launch_ms": per_launch_s * 1000,
@@ -553,12 +555,16 @@ def main():
     if not args.no_batch and world == 1:
         del plan                       # its workspace goes back to the allocator first
         torch.cuda.synchronize()
-        line["batch"] = batch_run(tn, np, torch, args.prec, args.steps, args.warmup, flush)
-        line["batch_untruncated_8_cycles"] = batch_run(tn, np, torch, args.prec, args.steps, args.warmup, flush,
-                                                       depth=8, truncated=False)
+        try:
+            line["batch"] = batch_run(tn, np, torch, args.prec, args.steps, args.warmup, flush)
+        except tn.TNError as e:
+            line["batch"] = {"error": str(e)}
     if args.serve_seconds > 0 and world == 1:
-        _, sv = serving_run(tn, np, args.prec, args.serve_seconds)
-        line["serving"] = sv
+        try:
+            _, sv = serving_run(tn, np, args.prec, args.serve_seconds)
+            line["serving"] = sv
+        except tn.TNError as e:
+            line["serving"] = {"error": str(e)}
     if not args.no_cpu and world == 1:
         cs = min(args.cpu_sample, B)
         r = cpu_oracle("syc53", args.bits, cs)
