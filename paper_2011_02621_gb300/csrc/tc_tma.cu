@@ -262,15 +262,12 @@ tma_step_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__
       const int32_t *bka = a.tab + s.t_bka, *bkb = a.tab + s.t_bkb;
       const int32_t *bna = a.tab + s.t_bna, *bnb = a.tab + s.t_bnb;
       const int64_t n_base = nr0 >> 1;
-      for (int64_t kc = 0; kc < nk; ++kc) {
-        const int st = (int)(kc % S);
-        const uint32_t it = (uint32_t)(kc / S);
-        if (kc >= S && !bar_wait(s_u32(&empty[st]), (it - 1) & 1, err, 15)) break;
-        const uint32_t bbase = s_u32(smem + st * STAGE + T_P * A_BYTES);
-        if (BM == 2) {
-          // every load of the stage first (tasks: four consecutive complex k of one column n)
-          constexpr int TASKS = (BN / 2) * 8 / 128;
-          float4 x[TASKS][2];
+      if (BM == 2) {
+        // software-pipelined: the next stage's loads are issued before this stage waits for its
+        // buffer and splits (tasks: four consecutive complex k of one column n)
+        constexpr int TASKS = (BN / 2) * 8 / 128;
+        float4 xn[TASKS][2];
+        auto load = [&](int64_t kc, float4 (&x)[TASKS][2]) {
 #pragma unroll
           for (int j = 0; j < TASKS; ++j) {
             const int t = bt + 128 * j, c16 = t & 7, nl = t >> 3;
@@ -282,6 +279,20 @@ tma_step_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__
               x[j][1] = __ldg(src + 1);
             }
           }
+        };
+        if (nk > 0) load(0, xn);
+        for (int64_t kc = 0; kc < nk; ++kc) {
+          float4 x[TASKS][2];
+#pragma unroll
+          for (int j = 0; j < TASKS; ++j) {
+            x[j][0] = xn[j][0];
+            x[j][1] = xn[j][1];
+          }
+          if (kc + 1 < nk) load(kc + 1, xn);
+          const int st = (int)(kc % S);
+          const uint32_t it = (uint32_t)(kc / S);
+          if (kc >= S && !bar_wait(s_u32(&empty[st]), (it - 1) & 1, err, 15)) break;
+          const uint32_t bbase = s_u32(smem + st * STAGE + T_P * A_BYTES);
 #pragma unroll
           for (int j = 0; j < TASKS; ++j) {
             const int t = bt + 128 * j, c16 = t & 7, nl = t >> 3;
@@ -305,7 +316,15 @@ tma_step_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__
               sts128(bbase + q * B_BYTES + sw128_off(2 * nl + 1, c16), w1[q]);
             }
           }
-        } else
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          bar_arrive(s_u32(&full[st]));
+        }
+      } else
+      for (int64_t kc = 0; kc < nk; ++kc) {
+        const int st = (int)(kc % S);
+        const uint32_t it = (uint32_t)(kc / S);
+        if (kc >= S && !bar_wait(s_u32(&empty[st]), (it - 1) & 1, err, 15)) break;
+        const uint32_t bbase = s_u32(smem + st * STAGE + T_P * A_BYTES);
         for (int t = bt; t < (BN / 2) * 8; t += 128) {
           const int c16 = t & 7, nl = t >> 3;        // 16-byte chunk = four complex k; complex column
           const int64_t n = n_base + nl;
