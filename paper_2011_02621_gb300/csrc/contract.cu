@@ -75,6 +75,35 @@ __global__ void form_c_kernel(StepParams s, ContractArgs a, const float2 *ket, c
                                            (int64_t)a.tab[s.t_bkb + k] + a.tab[s.t_bnb + n], s.ket_sig, s.bra_sig, s.phys);
 }
 
+// The same overlap tensor with the node's ket and bra tensors staged in shared memory first (they
+// are small for most steps): every element then reads shared memory instead of chasing table
+// offsets into global memory. Each CTA forms FORM_E * 256 consecutive elements of one item.
+constexpr int FORM_E = 8;
+__global__ void __launch_bounds__(256)
+form_c_smem_kernel(StepParams s, ContractArgs a, const float2 *ket, const float2 *bra, float2 *cbuf,
+                   int64_t c_stride, int64_t tk, int64_t tb, int64_t item0) {
+  extern __shared__ float2 nodes[];   // tk ket elements, then tb bra elements
+  const int64_t item = item0 + blockIdx.y;
+  const ItemCtx c = item_ctx(a, s, item);
+  const float2 *kg = ket + s.ket_off;
+  const float2 *bg = bra + c.b * a.bra_stride + s.bra_off;
+  for (int64_t i = threadIdx.x; i < tk; i += 256) nodes[i] = kg[i];
+  for (int64_t i = threadIdx.x; i < tb; i += 256) nodes[tk + i] = bg[i];
+  __syncthreads();
+  const float2 *kp = nodes + c.sa, *bp = nodes + tk + c.sb;
+  const int64_t K = s.K, kn = s.K * s.N;
+  const int64_t r0 = (int64_t)blockIdx.x * (256 * FORM_E) + threadIdx.x;
+#pragma unroll 4
+  for (int e = 0; e < FORM_E; ++e) {
+    const int64_t r = r0 + (int64_t)e * 256;
+    if (r >= kn) break;
+    const int64_t n = r / K, k = r % K;
+    cbuf[item * c_stride + r] = overlap_elem(kp, bp, (int64_t)a.tab[s.t_bka + k] + a.tab[s.t_bna + n],
+                                             (int64_t)a.tab[s.t_bkb + k] + a.tab[s.t_bnb + n], s.ket_sig, s.bra_sig,
+                                             s.phys);
+  }
+}
+
 // Tiled SIMT complex GEMM: one CTA per (item, BM x BN output tile).
 template <typename R, int BM, int BN, int BK, int TM, int TN>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN))
@@ -387,6 +416,17 @@ cudaError_t launch_form_c(const StepParams &s, const ContractArgs &a, const floa
                           float2 *cbuf, int64_t c_stride, cudaStream_t st) {
   const int64_t kn = s.K * s.N;
   if (kn <= 0 || a.items <= 0) return cudaSuccess;
+  const int64_t tk = s.phys * s.ket_sig, tb = s.phys * s.bra_sig;   // the node's tensors
+  if ((tk + tb) * (int64_t)sizeof(float2) <= 48 * 1024 && kn >= 1024) {
+    const int64_t gx = (kn + 256 * FORM_E - 1) / (256 * FORM_E);
+    for (int64_t i0 = 0; i0 < a.items; i0 += 65535) {
+      const int64_t ni = a.items - i0 < 65535 ? a.items - i0 : 65535;
+      form_c_smem_kernel<<<dim3((unsigned)gx, (unsigned)ni), 256, (size_t)(tk + tb) * sizeof(float2), st>>>(
+          s, a, ket, bra, cbuf, c_stride, tk, tb, i0);
+    }
+    tn_count_launch(1);
+    return cudaGetLastError();
+  }
   for (int64_t i0 = 0; i0 < a.items; i0 += 65535) {
     const int64_t ni = a.items - i0 < 65535 ? a.items - i0 : 65535;
     form_c_kernel<<<dim3((unsigned)((kn + 255) / 256), (unsigned)ni), 256, 0, st>>>(s, a, ket, bra, cbuf, c_stride,

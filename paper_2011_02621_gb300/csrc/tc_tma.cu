@@ -135,7 +135,7 @@ tma_step_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__
                 const __grid_constant__ CUtensorMap tA2, const __grid_constant__ CUtensorMap tB0,
                 const __grid_constant__ CUtensorMap tB1, const __grid_constant__ CUtensorMap tB2, StepParams s,
                 ContractArgs a, OutDesc out, int *err, const float2 *ket, const float2 *bra, const float2 *cbuf,
-                int64_t c_stride) {
+                int64_t c_stride, int staged) {
   constexpr bool BUILD = BM != 0;
   constexpr int A_BYTES = T_BM * 128, B_BYTES = BN * 128;
   constexpr int STAGE = T_P * (A_BYTES + B_BYTES);
@@ -259,6 +259,17 @@ tma_step_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__
       const ItemCtx c = item_ctx(a, s, item);
       const float2 *kp = ket + s.ket_off + c.sa;
       const float2 *bp = bra + c.b * a.bra_stride + s.bra_off + c.sb;
+      if (BM == 1 && staged) {
+        // the node's ket and bra tensors (small) into shared memory past the stage ring, once
+        float2 *nodes = reinterpret_cast<float2 *>(smem + S * STAGE);
+        const int64_t tk = s.phys * s.ket_sig, tb = s.phys * s.bra_sig;
+        const float2 *kg = ket + s.ket_off, *bg = bra + c.b * a.bra_stride + s.bra_off;
+        for (int64_t i = bt; i < tk; i += 128) nodes[i] = kg[i];
+        for (int64_t i = bt; i < tb; i += 128) nodes[tk + i] = bg[i];
+        asm volatile("bar.sync 1, 128;" ::: "memory");   // the four builder warps only
+        kp = nodes + c.sa;
+        bp = nodes + tk + c.sb;
+      }
       const int32_t *bka = a.tab + s.t_bka, *bkb = a.tab + s.t_bkb;
       const int32_t *bna = a.tab + s.t_bna, *bnb = a.tab + s.t_bnb;
       const int64_t n_base = nr0 >> 1;
@@ -447,11 +458,28 @@ cudaError_t launch_t(const StepParams &s, const ContractArgs &a, const Pieces &A
                      cudaStream_t st) {
   constexpr bool BUILD = BM != 0;
   constexpr size_t stage = (size_t)T_P * (T_BM * 128 + BN * 128);
-  const size_t smem = S * stage + 1024;
-  // once per instantiation (a function-local static is initialised by one thread)
-  static const cudaError_t attr = cudaFuncSetAttribute(tma_step_kernel<BN, R, S, BM>,
-                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (attr != cudaSuccess) return attr;
+  // once per instantiation (a function-local static is initialised by one thread): the dynamic
+  // shared memory limit = the device's opt-in maximum minus the kernel's static shared memory
+  static const int max_dyn = [] {
+    int dev = 0, optin = 0;
+    cudaFuncAttributes fa;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa, tma_step_kernel<BN, R, S, BM>) != cudaSuccess)
+      return -1;
+    const int lim = optin - (int)fa.sharedSizeBytes;
+    return cudaFuncSetAttribute(tma_step_kernel<BN, R, S, BM>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) ==
+                   cudaSuccess
+               ? lim
+               : -1;
+  }();
+  if (max_dyn < 0) return cudaErrorInvalidValue;
+  size_t smem = S * stage + 1024;
+  if (smem > (size_t)max_dyn) return cudaErrorInvalidValue;
+  // BM 1: stage the node tensors in shared memory when they fit beside the stage ring
+  const size_t node_bytes = (size_t)(s.phys * s.ket_sig + s.phys * s.bra_sig) * sizeof(float2);
+  const int staged = (BM == 1 && smem + node_bytes <= (size_t)max_dyn) ? 1 : 0;
+  if (staged) smem += node_bytes;
   CUtensorMap mA[3], mB[3];
   const uint64_t K2 = (uint64_t)(2 * s.K), N2 = (uint64_t)(2 * s.N);
   for (int q = 0; q < T_P; ++q) {
@@ -470,7 +498,7 @@ cudaError_t launch_t(const StepParams &s, const ContractArgs &a, const Pieces &A
   if (grid <= 0) return cudaSuccess;
   if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
   tma_step_kernel<BN, R, S, BM><<<(unsigned)grid, T_THREADS, smem, st>>>(mA[0], mA[1], mA[2], mB[0], mB[1], mB[2], s,
-                                                                         a, out, err, ket, bra, cbuf, c_stride);
+                                                                         a, out, err, ket, bra, cbuf, c_stride, staged);
   tn_count_launch(1);
   return cudaGetLastError();
 }
