@@ -552,6 +552,11 @@ def main():
     }
     if tuned is not None:
         line["config"]["step_kernels"] = {k: tuned.count(k) for k in sorted(set(tuned))}
+    from paper_2011_02621_gb300 import verify
+    f_dev = verify.circuit_fidelity(w.gates, w.graph.n)
+    line["verification"] = {"eq_fidelity_sycamore_error_rates": f_dev,
+                            "required_bitstrings_3_sigma": verify.required_bitstrings(f_dev),
+                            "linear_xeb_of_uniform_bitstrings": verify.linear_xeb(a_tc, w.graph.n)}
     if not args.no_batch and world == 1:
         del plan                       # its workspace goes back to the allocator first
         torch.cuda.synchronize()
