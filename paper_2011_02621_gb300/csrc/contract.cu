@@ -185,13 +185,24 @@ step_kernel(StepParams s, ContractArgs a, const typename C2T<R>::T *ket, const t
 template <typename R>
 __global__ void __launch_bounds__(256)
 step_small_kernel(StepParams s, ContractArgs a, const typename C2T<R>::T *ket, const typename C2T<R>::T *bra,
-                  const typename C2T<R>::T *tin, OutDesc out) {
+                  const typename C2T<R>::T *tin, OutDesc out, int staged) {
   using V = typename C2T<R>::T;
+  extern __shared__ unsigned char small_nodes_raw[];
   const int64_t item = blockIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   ItemCtx c = item_ctx(a, s, item);
   const V *kp = ket + s.ket_off + c.sa;
   const V *bp = bra + c.b * a.bra_stride + s.bra_off + c.sb;
+  if (staged) {   // the node's tensors (small) in shared memory first
+    V *nodes = reinterpret_cast<V *>(small_nodes_raw);
+    const int64_t tk = s.phys * s.ket_sig, tb = s.phys * s.bra_sig;
+    const V *kg = ket + s.ket_off, *bg = bra + c.b * a.bra_stride + s.bra_off;
+    for (int64_t i = threadIdx.x; i < tk; i += 256) nodes[i] = kg[i];
+    for (int64_t i = threadIdx.x; i < tb; i += 256) nodes[tk + i] = bg[i];
+    __syncthreads();
+    kp = nodes + c.sa;
+    bp = nodes + tk + c.sb;
+  }
   const V *tp = tin + item * a.t_stride;
   const int32_t *bka = a.tab + s.t_bka, *bkb = a.tab + s.t_bkb;
   const int32_t *bna = a.tab + s.t_bna, *bnb = a.tab + s.t_bnb, *ocol = a.tab + s.t_ocol;
@@ -507,12 +518,15 @@ cudaError_t launch_step(const StepParams &s, const ContractArgs &a, const void *
       tn_count_launch(1);
       return cudaGetLastError();
     }
-    case SIMT_SMALL:
+    case SIMT_SMALL: {
       if (a.items > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-      step_small_kernel<R><<<(unsigned)a.items, 256, 0, st>>>(s, a, (const V *)ket, (const V *)bra,
-                                                              (const V *)t_in, t_out);
+      const size_t node_bytes = (size_t)(s.phys * s.ket_sig + s.phys * s.bra_sig) * sizeof(V);
+      const int staged = node_bytes <= 32 * 1024 ? 1 : 0;
+      step_small_kernel<R><<<(unsigned)a.items, 256, staged ? node_bytes : 0, st>>>(
+          s, a, (const V *)ket, (const V *)bra, (const V *)t_in, t_out, staged);
       tn_count_launch(1);
       return cudaGetLastError();
+    }
     case SIMT_T64: return launch_tiled<R, 64, 64, 8, 4, 4>(s, a, ket, bra, t_in, t_out, st);
     case SIMT_T128: return launch_tiled<R, 128, 16, 8, 8, 2>(s, a, ket, bra, t_in, t_out, st);
     default: return launch_tiled<R, 256, 4, 8, 8, 1>(s, a, ket, bra, t_in, t_out, st);
