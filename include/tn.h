@@ -323,6 +323,16 @@ tn_status tn_path_search(const tn_graph *g, const double *dims, const tn_path_op
 tn_status tn_cut_search(const tn_graph *g, const double *dims, const tn_path_opts *opts, int32_t *order,
                         int32_t *cuts, int32_t *n_cuts, double *total_cmacs);
 
+/* The network tn_path contracts, on an arbitrary graph with per-edge ket and bra dimensions:
+ * boundary nodes merged into neighbours (unless opts->no_merge; explicit cut edges are never
+ * merged away), then Algorithm 1 and the cuts as in tn_path. owner[n_qubits]: the node each qubit
+ * belongs to, named by its representative qubit; *n_nodes nodes; order[*n_nodes]: the contraction
+ * order (representative qubits); *n_cuts and *total_cmacs (slices x score) may be NULL. Host only.
+ * Errors: TN_ERR_ARG, TN_ERR_GRAPH, TN_ERR_NO_PATH. */
+tn_status tn_merge_search(const tn_graph *g, const int32_t *ket_dims, const int32_t *bra_dims,
+                          const tn_path_opts *opts, int32_t *owner, int32_t *n_nodes, int32_t *order, int32_t *n_cuts,
+                          double *total_cmacs);
+
 /* ---- serving loop (continuous batching over resident plans) -------------- */
 
 typedef struct tn_server tn_server;

@@ -1081,8 +1081,9 @@ static Net identity_net(const tn_circuit *c) {
     g.db[e] = c->bra.dims[e];
   }
   g.rep.resize(c->n);
+  g.owner.resize(c->n);
   g.phys.assign(c->n, 2);
-  for (int q = 0; q < c->n; ++q) g.rep[q] = q;
+  for (int q = 0; q < c->n; ++q) g.rep[q] = g.owner[q] = q;
   g.ket_off = c->ket.node_off;
   g.bra_off = c->bra.node_off;
   g.ket_elems = c->ket.item_elems;
@@ -1147,6 +1148,8 @@ static void apply_merge(Net &g, int v, int a) {
   g.legs[v].clear();
   g.phys[u] *= g.phys[v];
   g.eu[a] = g.ev[a] = -1;
+  for (int &o : g.owner)
+    if (o == v) o = u;
 }
 
 // Repeatedly merge a not-yet-merged node v of degree <= 2 into the neighbour u across its widest
@@ -1211,11 +1214,73 @@ static void merge_nodes(Net &g, const std::vector<char> &keep_edge) {
   for (int v = 0; v < g.n; ++v)
     if (alive[v])
       for (int e : g.legs[v]) h.legs[nid[v]].push_back(eidx[e]);
+  h.owner.resize(g.owner.size());
+  for (size_t q = 0; q < g.owner.size(); ++q) h.owner[q] = nid[g.owner[q]];
   h.ket_elems = g.ket_elems;
   h.bra_elems = g.bra_elems;
   h.mk = g.mk;
   h.mb = g.mb;
   g = h;
+}
+
+extern "C" tn_status tn_merge_search(const tn_graph *g, const int32_t *ket_dims, const int32_t *bra_dims,
+                                     const tn_path_opts *opts, int32_t *owner, int32_t *n_nodes, int32_t *order,
+                                     int32_t *n_cuts, double *total_cmacs) {
+  if (!g || !ket_dims || !bra_dims || !owner || !n_nodes || !order)
+    return tn_fail(TN_ERR_ARG, "tn_merge_search: NULL argument");
+  Net net;
+  tn_status s = check_graph(g, net.eu, net.ev, net.legs);
+  if (s != TN_OK) return s;
+  net.n = g->n_qubits;
+  net.ne = g->n_edges;
+  net.eid.resize(net.ne);
+  net.dk.resize(net.ne);
+  net.db.resize(net.ne);
+  for (int e = 0; e < net.ne; ++e) {
+    if (ket_dims[e] < 1 || bra_dims[e] < 1) return tn_fail(TN_ERR_ARG, "tn_merge_search: dims must be >= 1");
+    net.eid[e] = e;
+    net.dk[e] = ket_dims[e];
+    net.db[e] = bra_dims[e];
+  }
+  net.rep.resize(net.n);
+  net.owner.resize(net.n);
+  net.phys.assign(net.n, 2);
+  net.ket_off.assign(net.n, 0);
+  net.bra_off.assign(net.n, 0);
+  for (int q = 0; q < net.n; ++q) net.rep[q] = net.owner[q] = q;
+  tn_path_opts o = opts ? *opts : tn_default_opts();
+  std::vector<char> keep(net.ne, 0);
+  for (int j = 0; j < o.n_cut_edges; ++j) {
+    const int e = o.cut_edges ? o.cut_edges[j] : -1;
+    if (e < 0 || e >= net.ne) return tn_fail(TN_ERR_ARG, "tn_merge_search: bad cut edge %d", e);
+    keep[e] = 1;
+  }
+  if (!o.no_merge) merge_nodes(net, keep);
+  std::vector<double> d(net.ne);
+  for (int e = 0; e < net.ne; ++e) d[e] = (double)net.dc(e);
+  const double limit = o.max_intermediate > 0 ? (double)o.max_intermediate : (double)(1LL << 24);
+  std::vector<int> ord, cut;
+  double score = 0;
+  int64_t pops = 0;
+  int ru = 0;
+  PathGraph pg = make_pg(net.n, net.eu, net.ev, d);
+  if ((s = path_auto(pg, o, ord, score, pops, ru)) != TN_OK) return s;
+  if (o.n_cut_edges > 0) {
+    for (int e = 0; e < net.ne; ++e)
+      if (keep[net.eid[e]]) { cut.push_back(e); d[e] = 1; }
+    PathGraph pg2 = make_pg(net.n, net.eu, net.ev, d);
+    if ((s = path_auto(pg2, o, ord, score, pops, ru)) != TN_OK) return s;
+  } else if ((s = choose_cuts(net, o, d, o.n_cuts, limit, cut, ord, score, pops, ru)) != TN_OK) {
+    return s;
+  }
+  double slices = 1;
+  for (int e : cut) slices *= (double)net.dc(e);
+  for (int q = 0; q < g->n_qubits; ++q) owner[q] = net.rep[net.owner[q]];
+  *n_nodes = net.n;
+  for (int j = 0; j < net.n; ++j) order[j] = net.rep[ord[j]];
+  if (n_cuts) *n_cuts = (int32_t)cut.size();
+  if (total_cmacs) *total_cmacs = slices * score;
+  return TN_OK;
 }
 
 // Every device index a compiled plan can produce, checked on the host before any launch: node

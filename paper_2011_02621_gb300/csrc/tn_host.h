@@ -78,6 +78,7 @@ struct Net {
   std::vector<int> eu, ev, eid;
   std::vector<std::vector<int>> legs;             // per node, network edge ids in tensor order
   std::vector<int> rep;                           // representative qubit per node
+  std::vector<int> owner;                         // per qubit: the node it belongs to
   std::vector<int> phys;                          // physical values per node
   std::vector<int64_t> dk, db;                    // ket / bra dim per network edge
   std::vector<int64_t> ket_off, bra_off;          // node offsets in the ket / bra item

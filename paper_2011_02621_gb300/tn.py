@@ -105,6 +105,8 @@ def _load():
                                  C.POINTER(dbl), C.POINTER(i64)]),
         "tn_cut_search": (i32, [C.POINTER(tn_graph), C.POINTER(dbl), C.POINTER(tn_path_opts), C.POINTER(i32),
                                 C.POINTER(i32), C.POINTER(i32), C.POINTER(dbl)]),
+        "tn_merge_search": (i32, [C.POINTER(tn_graph), C.POINTER(i32), C.POINTER(i32), C.POINTER(tn_path_opts),
+                                  C.POINTER(i32), C.POINTER(i32), C.POINTER(i32), C.POINTER(i32), C.POINTER(dbl)]),
         "tn_server_create": (i32, [C.POINTER(tn_server_cfg), C.POINTER(vp)]),
         "tn_server_submit": (i32, [vp, vp, vp, i64, i32, vp, C.POINTER(C.c_uint64)]),
         "tn_server_wait": (i32, [vp, C.c_uint64, i64]),
@@ -427,6 +429,24 @@ def tn_path_search(n_qubits: int, edges, dims, **opts):
     _check(LIB.tn_path_search(C.byref(g), d.ctypes.data_as(C.POINTER(C.c_double)), C.byref(o),
                               order.ctypes.data_as(C.POINTER(C.c_int32)), C.byref(score), C.byref(states)))
     return order, float(score.value), int(states.value)
+
+
+def tn_merge_search(n_qubits: int, edges, ket_dims, bra_dims, **opts):
+    """The network tn_path contracts for these bond dimensions: (owner per qubit, contraction order
+    of the nodes, number of cuts, total complex MACs)."""
+    g, e = _graph_struct(n_qubits, edges)
+    kd = np.ascontiguousarray(np.asarray(ket_dims, dtype=np.int32))
+    bd = np.ascontiguousarray(np.asarray(bra_dims, dtype=np.int32))
+    o, keep = _opts(**opts)
+    owner = np.zeros(n_qubits, dtype=np.int32)
+    order = np.zeros(n_qubits, dtype=np.int32)
+    nn, nc, tot = C.c_int32(), C.c_int32(), C.c_double()
+    _check(LIB.tn_merge_search(C.byref(g), kd.ctypes.data_as(C.POINTER(C.c_int32)),
+                               bd.ctypes.data_as(C.POINTER(C.c_int32)), C.byref(o),
+                               owner.ctypes.data_as(C.POINTER(C.c_int32)), C.byref(nn),
+                               order.ctypes.data_as(C.POINTER(C.c_int32)), C.byref(nc), C.byref(tot)))
+    del e, keep
+    return owner, order[: nn.value], nc.value, tot.value
 
 
 def tn_cut_search(n_qubits: int, edges, dims, **opts):

@@ -197,3 +197,54 @@ def test_cut_search_respects_limit_and_reports_cost(tn):
     assert len(cuts) == 0 and total == pytest.approx(score0, rel=1e-12)
     order, cuts, total = tn.tn_cut_search(g.n, g.edges, dims, cut_edges=[3, 7])
     assert list(cuts) == [3, 7]
+
+
+def _oracle_dims(name):
+    w = gen.workload(name, n_bits=1)
+    g1, g2 = otns.split_gates(w.gates, w.split)
+    ket = otns.evolve_ket(w.graph.n, w.graph.edges, g1, w.chi, w.cutoff)
+    bra = otns.evolve_bra(w.graph.n, w.graph.edges, g2, w.bits[0], w.chi, w.cutoff)
+    return w, [ket.bond(e) for e in range(len(w.graph.edges))], [bra.bond(e) for e in range(len(w.graph.edges))]
+
+
+def test_merge_search_groups_and_cost(tn):
+    """Boundary-node merging on the 53-qubit workload's overlap network (the oracle's bond
+    dimensions): every qubit belongs to one node, each node is a connected group of at most three
+    qubits (physical index <= 8 values) named by one of its members, every node is in the
+    contraction order once, and the merged network costs no more than the unmerged one."""
+    w, kd, bd = _oracle_dims("syc53")
+    n, edges = w.graph.n, w.graph.edges
+    owner, order, n_cuts, cost = tn.tn_merge_search(n, edges, kd, bd)
+    owner_u, order_u, _, cost_u = tn.tn_merge_search(n, edges, kd, bd, merge=False)
+    assert list(owner_u) == list(range(n)) and len(order_u) == n
+    reps = sorted(set(owner))
+    assert len(reps) == len(order) < n and sorted(order) == reps
+    adj = {q: set() for q in range(n)}
+    for u, v in edges:
+        adj[u].add(v)
+        adj[v].add(u)
+    for r in reps:
+        members = [q for q in range(n) if owner[q] == r]
+        assert owner[r] == r and 1 <= len(members) <= 3
+        seen, todo = {members[0]}, [members[0]]          # connected inside the group
+        while todo:
+            x = todo.pop()
+            for y in adj[x]:
+                if owner[y] == r and y not in seen:
+                    seen.add(y)
+                    todo.append(y)
+        assert seen == set(members)
+    assert n_cuts == 0 and cost <= cost_u * (1 + 1e-12)
+
+
+def test_merge_search_leaf_and_kept_cut_edges(tn):
+    """A path graph 0-1-2-3 with equal bonds: nodes are merged in index order while at least two
+    remain (the leaf 0 into 1, then 2 into that node: physical index 8); an explicit cut edge is
+    never merged away (its endpoints stay in different nodes)."""
+    edges = [(0, 1), (1, 2), (2, 3)]
+    owner, order, _, _ = tn.tn_merge_search(4, edges, [2, 2, 2], [2, 2, 2])
+    assert list(owner) == [1, 1, 1, 3] and sorted(order) == [1, 3]
+    owner, order, n_cuts, _ = tn.tn_merge_search(4, edges, [2, 2, 2], [2, 2, 2], cut_edges=[0])
+    assert owner[0] != owner[1] and n_cuts == 1
+    with pytest.raises(tn.TNError):
+        tn.tn_merge_search(4, edges, [2, 0, 2], [2, 2, 2])
