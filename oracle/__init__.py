@@ -12,7 +12,8 @@ Modules:
 * ``statevector``  brute-force Schroedinger simulation: the definition
   a(s) = <s|U|0...0> that the untruncated method reaches exactly.
 * ``tns``          the method step by step: gate split (Eq. gatesplit), gate
-  application (Eqs. result1/result2), SVD compression (Eqs. svd/svd2),
+  application (Eqs. result1/result2), SVD compression (Eqs. svd/svd2, and a
+  two-sided QR + SVD variant of them),
   two-sided evolution (Fig. 2a), overlap network (Eq. overlap), cutting and
   a contraction by the oracle's own greedy pairwise order.
 * ``path``         the path score of the supplement (score recursion and

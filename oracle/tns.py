@@ -29,6 +29,11 @@ Conventions (readings where the paper is silent):
   amplitude is then sum_sigma psi_bar[sigma] phi[sigma] with no complex
   conjugation (Eq. overlap). This equals applying the group "inversely" to
   <s| (Fig. 2a).
+* ``compress="two_sided"`` selects a variant of Eqs. svd/svd2 that the paper does not use: thin QR
+  of both endpoints, SVD of the small bond matrix R_k R_l^T, isometry to the same endpoint and
+  S to the other. It keeps the singular values of the local product A^k A^l itself, so its
+  truncation is the best one of that rank for the pair (Eckart-Young) and its bond is the rank of
+  the product. Same keep rule and endpoint rule; untruncated it gives the same amplitudes.
 * Single-qubit gates are applied to the physical index directly (no fusion).
 * Overlap legs merge (a, b) as a * dim(b) + b (Eq. overlap).
 * Cutting fixes the merged index of the cut edges; the slices' scalars are
@@ -107,7 +112,9 @@ class TNS:
         return out.reshape(shape)
 
     def apply_2q(self, q0: int, q1: int, m: np.ndarray, chi: int = 0, cutoff: float = 1e-12,
-                 svd_node: Optional[int] = None) -> None:
+                 svd_node: Optional[int] = None, compress: str = "one_sided") -> None:
+        """Eqs. result1/result2, then the bond compression: Eqs. svd/svd2 (``one_sided``) or the
+        two-sided variant (``two_sided``, see ``_compress_two_sided``)."""
         k, l = q0, q1
         e = self.edge_id.get(tuple(sorted((k, l))))
         if e is None:
@@ -124,6 +131,15 @@ class TNS:
             Asv, psv, Aot, pot, sv = Ak, pk, Al, pl, k
         else:
             Asv, psv, Aot, pot, sv = Al, pl, Ak, pk, l
+        if compress == "two_sided":
+            Asv, Aot = self._compress_two_sided(Asv, psv, Aot, pot, chi, cutoff, e, sv)
+            if sv == k:
+                self.A[k], self.A[l] = Asv, Aot
+            else:
+                self.A[k], self.A[l] = Aot, Asv
+            return
+        if compress != "one_sided":
+            raise ValueError(f"unknown compression {compress!r}")
         X = np.moveaxis(Asv, psv, -1)
         shp = X.shape
         X = X.reshape(-1, shp[-1])
@@ -141,13 +157,44 @@ class TNS:
             self.A[k], self.A[l] = Aot, Asv
         self.log.append(dict(edge=e, svd_node=sv, m=X.shape[0], n=X.shape[1], s=S, keep=keep))
 
+    def _compress_two_sided(self, Asv, psv, Aot, pot, chi, cutoff, e, sv):
+        """Two-sided bond compression, a variant of Eqs. svd/svd2 that the paper does not use.
+
+        With X = A^sv and Y = A^other matricised as (physical and other legs) x (bond), the two
+        tensors meet in the local product X Y^T. Thin QR factorisations X = Q_x R_x and
+        Y = Q_y R_y reduce it to the small bond matrix R_x R_y^T, whose SVD U S V^H has the
+        singular values of X Y^T itself (Q_x, Q_y have orthonormal columns). The kept part gives
+        A^sv <- Q_x U (an isometry, as in Eq. svd2) and A^other <- Q_y conj(V) S, so
+        X' Y'^T = Q_x U S V^H Q_y^T: the best approximation of X Y^T of that rank (Eckart-Young),
+        and a bond no larger than the rank of X Y^T. Same keep rule as the one-sided form."""
+        X = np.moveaxis(Asv, psv, -1)
+        shx = X.shape
+        X = X.reshape(-1, shx[-1])
+        Y = np.moveaxis(Aot, pot, -1)
+        shy = Y.shape
+        Y = Y.reshape(-1, shy[-1])
+        Qx, Rx = np.linalg.qr(X)
+        Qy, Ry = np.linalg.qr(Y)
+        Mb = Rx @ Ry.T
+        U, S, Vh = np.linalg.svd(Mb, full_matrices=False)
+        keep = int(np.sum(S > cutoff * S[0])) if S[0] > 0 else 1
+        if chi and chi > 0:
+            keep = min(keep, chi)
+        keep = max(keep, 1)
+        Xn = Qx @ U[:, :keep]
+        Yn = Qy @ (S[:keep, None] * Vh[:keep, :]).T
+        self.log.append(dict(edge=e, svd_node=sv, m=Mb.shape[0], n=Mb.shape[1], s=S, keep=keep,
+                             two_sided=True))
+        return (np.moveaxis(Xn.reshape(shx[:-1] + (keep,)), -1, psv),
+                np.moveaxis(Yn.reshape(shy[:-1] + (keep,)), -1, pot))
+
     def apply(self, gate, chi: int = 0, cutoff: float = 1e-12, transpose: bool = False,
-              svd_node: Optional[int] = None) -> None:
+              svd_node: Optional[int] = None, compress: str = "one_sided") -> None:
         m = gate.m.T if transpose else gate.m
         if len(gate.qubits) == 1:
             self.apply_1q(gate.qubits[0], m)
         else:
-            self.apply_2q(gate.qubits[0], gate.qubits[1], m, chi, cutoff, svd_node)
+            self.apply_2q(gate.qubits[0], gate.qubits[1], m, chi, cutoff, svd_node, compress)
 
 
 def structural_svd_nodes(n, edges, gates, chi=0, return_dims: bool = False):
@@ -155,7 +202,9 @@ def structural_svd_nodes(n, edges, gates, chi=0, return_dims: bool = False):
     whose matrix has fewer rows 2 * prod(other legs) in the structural shapes, ties to the gate's
     first qubit. Structural shapes: bonds start at 1; a gate multiplies its bond by its chi_o
     (Eq. gatesplit); the compression bounds it by the rows of the compressed matrix and by chi
-    (Eqs. svd, shouwei). Independent of the state."""
+    (Eqs. svd, shouwei). The same shapes bound the two-sided compression: the rank of the local
+    product is at most the smaller endpoint's rows, which is the endpoint named here. Independent
+    of the state."""
     es = [tuple(sorted(e)) for e in edges]
     eid = {e: i for i, e in enumerate(es)}
     legs: List[List[int]] = [[] for _ in range(n)]
@@ -190,21 +239,22 @@ def split_gates(gates, split_cycle: int):
     return g1, g2
 
 
-def _evolve(t: TNS, seq, chi, cutoff, transpose) -> TNS:
+def _evolve(t: TNS, seq, chi, cutoff, transpose, compress="one_sided") -> TNS:
     nodes = iter(structural_svd_nodes(t.n, t.edges, seq, chi))
     for g in seq:
-        t.apply(g, chi, cutoff, transpose=transpose, svd_node=None if len(g.qubits) == 1 else next(nodes))
+        t.apply(g, chi, cutoff, transpose=transpose,
+                svd_node=None if len(g.qubits) == 1 else next(nodes), compress=compress)
     return t
 
 
-def evolve_ket(n, edges, gates1, chi=0, cutoff=1e-12) -> TNS:
+def evolve_ket(n, edges, gates1, chi=0, cutoff=1e-12, compress="one_sided") -> TNS:
     """|phi> = (group 1) |0...0>."""
-    return _evolve(TNS(n, edges), list(gates1), chi, cutoff, False)
+    return _evolve(TNS(n, edges), list(gates1), chi, cutoff, False, compress)
 
 
-def evolve_bra(n, edges, gates2, bits, chi=0, cutoff=1e-12) -> TNS:
+def evolve_bra(n, edges, gates2, bits, chi=0, cutoff=1e-12, compress="one_sided") -> TNS:
     """Coefficients of <psi| = <s| (group 2): the transposed gates, last to first, on |s>."""
-    return _evolve(TNS(n, edges, bits), list(reversed(list(gates2))), chi, cutoff, True)
+    return _evolve(TNS(n, edges, bits), list(reversed(list(gates2))), chi, cutoff, True, compress)
 
 
 # --------------------------------------------------------------------------
@@ -313,14 +363,16 @@ def to_dense(t: TNS) -> np.ndarray:
     return np.transpose(out, [lab.index(("p", q)) for q in range(t.n)])
 
 
-def amplitudes(n, edges, gates, bits_batch, split_cycle, chi=0, cutoff=1e-12, cuts=(), ket=None, slices=None):
+def amplitudes(n, edges, gates, bits_batch, split_cycle, chi=0, cutoff=1e-12, cuts=(), ket=None, slices=None,
+               compress="one_sided"):
     """The full method for each row of ``bits_batch``; returns (amplitudes, ket). ``slices``: only
-    these slices of the cut network enter each sum (see overlap_amplitude)."""
+    these slices of the cut network enter each sum (see overlap_amplitude). ``compress``: the bond
+    compression of both halves, ``one_sided`` (Eqs. svd/svd2) or ``two_sided``."""
     g1, g2 = split_gates(gates, split_cycle)
     if ket is None:
-        ket = evolve_ket(n, edges, g1, chi, cutoff)
+        ket = evolve_ket(n, edges, g1, chi, cutoff, compress)
     out = np.empty(len(bits_batch), dtype=np.complex128)
     for i, bits in enumerate(bits_batch):
-        bra = evolve_bra(n, edges, g2, bits, chi, cutoff)
+        bra = evolve_bra(n, edges, g2, bits, chi, cutoff, compress)
         out[i] = overlap_amplitude(ket, bra, cuts, slices)
     return out, ket

@@ -34,8 +34,8 @@ def test_unpatched_oracle_passes():
 def test_bra_without_transpose_is_caught(monkeypatch):
     orig = tns.TNS.apply
 
-    def no_transpose(self, gate, chi=0, cutoff=1e-12, transpose=False, svd_node=None):
-        return orig(self, gate, chi, cutoff, transpose=False, svd_node=svd_node)
+    def no_transpose(self, gate, chi=0, cutoff=1e-12, transpose=False, svd_node=None, compress="one_sided"):
+        return orig(self, gate, chi, cutoff, transpose=False, svd_node=svd_node, compress=compress)
     monkeypatch.setattr(tns.TNS, "apply", no_transpose)
     assert _err_vs_statevector() > 1e-3
 
