@@ -1,0 +1,16 @@
+// Persistent form of the TMA-fed tcgen05 step (BF16x6): one CTA per SM walks the output tiles,
+// the operand ring runs across tile boundaries and the accumulators are handed between the MMA
+// issuer and the epilogue by mbarriers (two TMEM accumulator sets at 64-column tiles).
+#pragma once
+
+#include "tn_internal.h"
+
+// Same contract as launch_step_tma for the loaded-B (cbuf == nullptr: B pieces by TMA) and
+// complex64-B (cbuf: the overlap tensor [N][K] per item, c_stride elements apart) modes. At
+// 128-column tiles it issues the same MMAs and sums the accumulators in the same order as
+// launch_step_tma (R = 3); at 64-column tiles it uses R = 3 (launch_step_tma: 7). bn: 128 or
+// 64 real output columns per tile (0 picks by shape). Returns cudaErrorInvalidValue for
+// unsupported shapes or arguments.
+cudaError_t launch_step_tma_persistent(const StepParams &s, const ContractArgs &a, const Pieces &A, const Pieces &B,
+                                       const OutDesc &out, int *err, cudaStream_t st, int bn, const float2 *cbuf,
+                                       int64_t c_stride);
