@@ -15,7 +15,8 @@ Modules:
   application (Eqs. result1/result2), SVD compression (Eqs. svd/svd2, and a
   two-sided QR + SVD variant of them),
   two-sided evolution (Fig. 2a), overlap network (Eq. overlap), cutting and
-  a contraction by the oracle's own greedy pairwise order.
+  a contraction by the oracle's own greedy pairwise order; the same sums
+  grouped as the double-layer network (ket and bra tensors as separate nodes).
 * ``path``         the path score of the supplement (score recursion and
   Eq. optscore) by brute force over orders and by subset dynamic programming.
 """

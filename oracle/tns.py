@@ -314,6 +314,21 @@ def contract_network(tensors: List[np.ndarray], labels: List[List[int]]) -> comp
     return complex(ts[0].reshape(()) if ts[0].ndim == 0 else ts[0].sum())
 
 
+def double_layer_amplitude(ket: TNS, bra: TNS) -> complex:
+    """<psi|phi> from the double-layer network: every ket tensor A^q and every bra tensor B^q is a
+    node of its own, A^q and B^q share the physical index sigma_q, the A's share the ket bonds
+    and the B's the bra bonds. These are the sums of Eq. overlap without first forming the node
+    tensors C^q = sum_sigma A^q B^q, so the value equals overlap_amplitude; only the grouping of
+    the sums differs (here: the oracle's greedy pairwise order over 2N tensors)."""
+    ts, ls = [], []
+    for q in range(ket.n):
+        ts.append(ket.A[q])
+        ls.append([("s", q)] + [("a", e) for e in ket.legs[q]])
+        ts.append(bra.A[q])
+        ls.append([("s", q)] + [("b", e) for e in bra.legs[q]])
+    return contract_network(ts, ls)
+
+
 def overlap_amplitude(ket: TNS, bra: TNS, cuts: Sequence[int] = (), slices=None) -> complex:
     """<psi|phi> by Eq. overlap; with ``cuts`` the sum over all slices of the cut edges.
 

@@ -248,3 +248,23 @@ def test_merge_search_leaf_and_kept_cut_edges(tn):
     assert owner[0] != owner[1] and n_cuts == 1
     with pytest.raises(tn.TNError):
         tn.tn_merge_search(4, edges, [2, 0, 2], [2, 2, 2])
+
+
+def test_planner_on_the_double_layer_network(tn):
+    """Algorithm 1 on the double-layer network of the 53-qubit workload (ket and bra tensors as
+    separate nodes, joined by a dimension-2 physical edge; structural bond dims): its cost is the
+    oracle's path score of the order it returns, and about ten times below the cost of the
+    overlap network (one node per qubit, edge dims dk * db) on the same bonds."""
+    w = gen.workload("syc53", n_bits=1)
+    n, edges = w.graph.n, [tuple(sorted(e)) for e in w.graph.edges]
+    g1, g2 = otns.split_gates(w.gates, w.split)
+    kd = otns.structural_svd_nodes(n, edges, g1, w.chi, return_dims=True)[1]
+    bd = otns.structural_svd_nodes(n, edges, list(reversed(g2)), w.chi, return_dims=True)[1]
+    _, cuts1, total1 = tn.tn_cut_search(n, edges, [a * b for a, b in zip(kd, bd)])
+    e2 = edges + [(n + u, n + v) for u, v in edges] + [(q, n + q) for q in range(n)]
+    d2 = [float(x) for x in list(kd) + list(bd) + [2] * n]
+    order2, cuts2, total2 = tn.tn_cut_search(2 * n, e2, d2)
+    assert len(cuts1) == 0 and len(cuts2) == 0
+    assert sorted(int(v) for v in order2) == list(range(2 * n))
+    assert total2 == pytest.approx(opath.score([int(v) for v in order2], e2, d2), rel=1e-12)
+    assert total2 < 0.2 * total1
