@@ -116,6 +116,8 @@ typedef struct {
   double mem_budget_bytes;  /* workspace budget of tn_amplitudes; 0 = 8 GiB */
   int32_t no_merge;         /* 1 = one network node per qubit; 0 = merge boundary nodes of degree
                                <= 2 into a neighbour first (exact; see tn_path) */
+  int32_t layers;           /* 0 or 1 = the overlap network of Eq. overlap (one node per qubit);
+                               2 = the double-layer network (see tn_path) */
 } tn_path_opts;
 
 /* Summary of a plan. All counts are per amplitude unless stated. */
@@ -170,12 +172,30 @@ tn_status tn_circuit_bond_dims(const tn_circuit *c, int32_t side, int32_t *out);
  * every bitstring's bra, giving one node with a physical index of 4 (or 8)
  * values; the overlap network and the amplitudes are unchanged, the path
  * search and the contraction see fewer, no larger nodes.
- * Errors: TN_ERR_STATE, TN_ERR_NO_PATH, TN_ERR_ARG, TN_ERR_CUDA, TN_ERR_OOM. */
+ * With opts->layers == 2 the network is the double-layer one: node q is qubit q's ket tensor,
+ * node n_qubits + q its bra tensor, the two joined by an edge of dimension 2 (the physical
+ * index), ket bonds between ket nodes and bra bonds between bra nodes; network edge ids are
+ * e (ket bond of circuit edge e), n_edges + e (its bra bond) and 2 n_edges + q (qubit q's
+ * physical index). The sums are those of Eq. overlap without forming the per-qubit overlap
+ * tensors first, so the amplitudes are the same; each step absorbs one ket tensor (the same for
+ * every bitstring) or one bra tensor. No merging; explicit cut_edges are not accepted
+ * (TN_ERR_UNSUPPORTED); automatic cuts are.
+ * Errors: TN_ERR_STATE, TN_ERR_NO_PATH, TN_ERR_ARG, TN_ERR_CUDA, TN_ERR_OOM, TN_ERR_UNSUPPORTED. */
 tn_status tn_path(tn_circuit *c, const tn_path_opts *opts, tn_plan **out, tn_plan_info *info);
 
-/* Plan details: order[n_qubits] (contraction order of the network's nodes,
- * each named by its representative qubit, then -1 for the merged qubits),
- * cuts[n_cuts] (edge ids), steps[3*n_steps] = (M, K, N) per step per slice.
+/* Host-only estimate of the plan tn_path(opts) would make after
+ * tn_evolve_two_sided(c, split_cycle, chi_max, cutoff_rel): the same gate programs with their
+ * structural bond bounds (no device work and no rank probe, so a bond can be wider than an
+ * evolved circuit's), the same network, path, cuts and compiled steps, every table checked
+ * against the node tensors and the item strides as tn_path does. Fills `info`; c is not
+ * modified and needs no evolution. Errors: TN_ERR_ARG, TN_ERR_NO_PATH, TN_ERR_UNSUPPORTED. */
+tn_status tn_plan_estimate(const tn_circuit *c, int32_t split_cycle, int32_t chi_max, double cutoff_rel,
+                           const tn_path_opts *opts, tn_plan_info *info);
+
+/* Plan details: order[max(n_qubits, n_nodes)] (contraction order of the network's nodes,
+ * each named by its representative qubit, then -1 for the merged qubits; for a double-layer
+ * plan the 2 n_qubits node ids), cuts[n_cuts] (circuit edge ids; network edge ids for a
+ * double-layer plan), steps[3*n_steps] = (M, K, N) per step per slice.
  * Any pointer may be NULL. */
 tn_status tn_plan_details(const tn_plan *p, int32_t *order, int32_t *cuts, int64_t *steps);
 

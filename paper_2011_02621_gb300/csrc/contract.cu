@@ -428,7 +428,9 @@ cudaError_t launch_form_c(const StepParams &s, const ContractArgs &a, const floa
   const int64_t kn = s.K * s.N;
   if (kn <= 0 || a.items <= 0) return cudaSuccess;
   const int64_t tk = s.phys * s.ket_sig, tb = s.phys * s.bra_sig;   // the node's tensors
-  if ((tk + tb) * (int64_t)sizeof(float2) <= 48 * 1024 && kn >= 1024) {
+  // staged only when both operands are node tensors of that size (a double-layer step's own
+  // tensor has physical stride 0 and is read in place)
+  if (s.ket_sig > 0 && s.bra_sig > 0 && (tk + tb) * (int64_t)sizeof(float2) <= 48 * 1024 && kn >= 1024) {
     const int64_t gx = (kn + 256 * FORM_E - 1) / (256 * FORM_E);
     for (int64_t i0 = 0; i0 < a.items; i0 += 65535) {
       const int64_t ni = a.items - i0 < 65535 ? a.items - i0 : 65535;
@@ -521,7 +523,7 @@ cudaError_t launch_step(const StepParams &s, const ContractArgs &a, const void *
     case SIMT_SMALL: {
       if (a.items > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
       const size_t node_bytes = (size_t)(s.phys * s.ket_sig + s.phys * s.bra_sig) * sizeof(V);
-      const int staged = node_bytes <= 32 * 1024 ? 1 : 0;
+      const int staged = (s.ket_sig > 0 && s.bra_sig > 0 && node_bytes <= 32 * 1024) ? 1 : 0;
       step_small_kernel<R><<<(unsigned)a.items, 256, staged ? node_bytes : 0, st>>>(
           s, a, (const V *)ket, (const V *)bra, (const V *)t_in, t_out, staged);
       tn_count_launch(1);

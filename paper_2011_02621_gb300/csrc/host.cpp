@@ -1091,6 +1091,70 @@ static Net identity_net(const tn_circuit *c) {
   return g;
 }
 
+// The double-layer network: qubit q's ket tensor is node q and its bra tensor node n + q, joined
+// by an edge of dimension 2 (the physical index sigma_q, id 2 ne + q); ket bond e joins ket nodes
+// (id e, dims dk = ket bond, db = 1), its bra bond joins bra nodes (id ne + e, dk = 1, db = bra
+// bond). Each node's tensor is the half's node tensor as stored, [sigma, legs in increasing edge
+// id], so its legs are [sigma edge, bonds]. These are the sums of Eq. overlap without the
+// per-qubit tensors C^q formed first.
+static Net double_layer_net(const tn_circuit *c) {
+  Net g;
+  const int n = c->n, ne = c->ne;
+  g.n = 2 * n;
+  g.ne = 2 * ne + n;
+  g.eu.resize(g.ne);
+  g.ev.resize(g.ne);
+  g.eid.resize(g.ne);
+  g.dk.resize(g.ne);
+  g.db.resize(g.ne);
+  for (int e = 0; e < ne; ++e) {
+    g.eu[e] = c->eu[e];
+    g.ev[e] = c->ev[e];
+    g.eid[e] = e;
+    g.dk[e] = c->ket.dims[e];
+    g.db[e] = 1;
+    g.eu[ne + e] = n + c->eu[e];
+    g.ev[ne + e] = n + c->ev[e];
+    g.eid[ne + e] = ne + e;
+    g.dk[ne + e] = 1;
+    g.db[ne + e] = c->bra.dims[e];
+  }
+  for (int q = 0; q < n; ++q) {
+    const int e = 2 * ne + q;
+    g.eu[e] = q;
+    g.ev[e] = n + q;
+    g.eid[e] = e;
+    g.dk[e] = 2;
+    g.db[e] = 1;
+  }
+  g.legs.assign(g.n, {});
+  g.rep.resize(g.n);
+  g.owner.resize(n);
+  g.phys.assign(g.n, 2);              // the unit operand's two values
+  g.layer.resize(g.n);
+  g.ket_off.resize(g.n);
+  g.bra_off.resize(g.n);
+  for (int q = 0; q < n; ++q) {
+    g.legs[q].push_back(2 * ne + q);
+    g.legs[n + q].push_back(2 * ne + q);
+    for (int e : c->legs[q]) {
+      g.legs[q].push_back(e);
+      g.legs[n + q].push_back(ne + e);
+    }
+    g.rep[q] = g.rep[n + q] = q;
+    g.owner[q] = q;
+    g.layer[q] = 1;
+    g.layer[n + q] = 2;
+    g.ket_off[q] = c->ket.node_off[q];
+    g.bra_off[q] = 0;                 // unit operand
+    g.ket_off[n + q] = 0;             // unit operand
+    g.bra_off[n + q] = c->bra.node_off[q];
+  }
+  g.ket_elems = c->ket.item_elems;
+  g.bra_elems = c->bra.item_elems;
+  return g;
+}
+
 // Merge node v into u through edge a on both halves: U's tensor becomes
 // [p_u, p_v, legs_u \ a, legs_v \ a] = sum_a U V, a new slot past the items' current ends.
 static void apply_merge(Net &g, int v, int a) {
@@ -1298,11 +1362,22 @@ static tn_status validate_plan(const tn_plan *p) {
     for (int64_t i = 0; i < n; ++i) m = std::max<int64_t>(m, tab[off + i]);
     return m;
   };
+  const auto layer_of = [&](int i) { return g.layer.empty() ? 0 : g.layer[i]; };
+  // a double-layer node's own tensor (its legs' dims dc) in its half's item; the unit operand
+  // (two values) in the other slot
+  auto own_size = [&](int i) {
+    int64_t t = 1;
+    for (int e : g.legs[i]) t *= g.dc(e);
+    return t;
+  };
   for (int i = 0; i < g.n; ++i) {
     int64_t sk = g.phys[i], sb = g.phys[i];
-    for (int e : g.legs[i]) { sk *= g.dk[e]; sb *= g.db[e]; }
-    if (g.ket_off[i] + sk > g.ket_elems) return bad("ket node tensor outside the item", i, g.ket_off[i] + sk, g.ket_elems);
-    if (g.bra_off[i] + sb > g.bra_elems) return bad("bra node tensor outside the item", i, g.bra_off[i] + sb, g.bra_elems);
+    if (layer_of(i) == 1) { sk = own_size(i); sb = 2; }
+    else if (layer_of(i) == 2) { sk = 2; sb = own_size(i); }
+    else for (int e : g.legs[i]) { sk *= g.dk[e]; sb *= g.db[e]; }
+    const int64_t klim = layer_of(i) == 2 ? 2 : g.ket_elems, blim = layer_of(i) == 1 ? 2 : g.bra_elems;
+    if (g.ket_off[i] + sk > klim) return bad("ket node tensor outside the item", i, g.ket_off[i] + sk, klim);
+    if (g.bra_off[i] + sb > blim) return bad("bra node tensor outside the item", i, g.bra_off[i] + sb, blim);
   }
   for (int h = 0; h < 2; ++h) {
     const std::vector<MergeParams> &ms = h ? g.mb : g.mk;
@@ -1322,6 +1397,8 @@ static tn_status validate_plan(const tn_plan *p) {
     const StepParams &s = p->steps[j];
     const int i = p->order[j];
     int64_t tk = s.phys * s.ket_sig, tb = s.phys * s.bra_sig;   // the node's tensor sizes
+    if (layer_of(i) == 1) { tk = own_size(i); tb = 2; }
+    else if (layer_of(i) == 2) { tk = 2; tb = own_size(i); }
     const int64_t ka = tmax(s.t_sa, p->n_slices) + tmax(s.t_bna, s.N) + (j ? tmax(s.t_bka, s.K) : 0) +
                        (s.phys - 1) * s.ket_sig;
     const int64_t kb = tmax(s.t_sb, p->n_slices) + tmax(s.t_bnb, s.N) + (j ? tmax(s.t_bkb, s.K) : 0) +
@@ -1366,8 +1443,33 @@ static tn_status compile_plan(tn_plan *p) {
     for (int j = (int)L.size() - 1; j >= 0; --j) { st[j] = s; s *= dims[L[j]]; }
     return s;
   };
+  // double-layer nodes: one tensor with leg dims dc in the node's own slot (1 ket, 2 bra)
+  const auto layer_of = [&](int i) { return c.layer.empty() ? 0 : c.layer[i]; };
+  std::vector<int64_t> dcv(c.ne);
+  for (int e = 0; e < c.ne; ++e) dcv[e] = c.dc(e);
   // tables over a list of legs of node i: offsets into ket / bra for each multi-index
   auto leg_tables = [&](int i, const std::vector<int> &legs, std::vector<int64_t> &ta, std::vector<int64_t> &tb) {
+    if (layer_of(i) != 0) {
+      std::vector<int64_t> sd;
+      leg_strides(i, dcv, sd);
+      int64_t total = 1;
+      for (int e : legs) total *= c.dc(e);
+      ta.assign(total, 0);
+      tb.assign(total, 0);
+      std::vector<int64_t> &own = layer_of(i) == 1 ? ta : tb;
+      for (int64_t idx = 0; idx < total; ++idx) {
+        int64_t r = idx, o = 0;
+        for (int j = (int)legs.size() - 1; j >= 0; --j) {
+          const int e = legs[j];
+          const int64_t d = c.dc(e);
+          const int li = (int)(std::find(c.legs[i].begin(), c.legs[i].end(), e) - c.legs[i].begin());
+          o += (r % d) * sd[li];
+          r /= d;
+        }
+        own[idx] = o;
+      }
+      return;
+    }
     std::vector<int64_t> sk, sb;
     leg_strides(i, c.dk, sk);
     leg_strides(i, c.db, sb);
@@ -1396,6 +1498,19 @@ static tn_status compile_plan(tn_plan *p) {
     leg_strides(i, c.db, sb);
     sa.assign(p->n_slices, 0);
     sbv.assign(p->n_slices, 0);
+    if (layer_of(i) != 0) {
+      std::vector<int64_t> sd;
+      leg_strides(i, dcv, sd);
+      std::vector<int64_t> &own = layer_of(i) == 1 ? sa : sbv;
+      for (int64_t s = 0; s < p->n_slices; ++s)
+        for (size_t j = 0; j < p->cuts.size(); ++j) {
+          const int e = p->cuts[j];
+          auto it = std::find(c.legs[i].begin(), c.legs[i].end(), e);
+          if (it == c.legs[i].end()) continue;
+          own[s] += ((s / cut_stride[j]) % c.dc(e)) * sd[(int)(it - c.legs[i].begin())];
+        }
+      return;
+    }
     for (int64_t s = 0; s < p->n_slices; ++s) {
       for (size_t j = 0; j < p->cuts.size(); ++j) {
         int e = p->cuts[j];
@@ -1423,6 +1538,7 @@ static tn_status compile_plan(tn_plan *p) {
   };
   p->steps.clear();
   p->step_mkn.clear();
+  p->step_layer.clear();
   // pass 1: per step the rest, shared and new legs; the input layout of step j is
   // [rest_j, shared_j], both in the order the legs were created
   std::vector<std::vector<int>> R(n), Sh(n), Nw(n);
@@ -1503,9 +1619,16 @@ static tn_status compile_plan(tn_plan *p) {
     s.ket_sig = leg_strides(i, c.dk, skk);
     s.bra_sig = leg_strides(i, c.db, sbb);
     s.phys = c.phys[i];
+    if (layer_of(i) != 0) {
+      // sum over the unit operand's two values: own[x] * 1 + own[x] * 0 (own stride 0, unit stride 1)
+      s.phys = 2;
+      s.ket_sig = layer_of(i) == 1 ? 0 : 1;
+      s.bra_sig = layer_of(i) == 1 ? 1 : 0;
+    }
     s.ket_off = c.ket_off[i];
     s.bra_off = c.bra_off[i];
     p->steps.push_back(s);
+    p->step_layer.push_back(layer_of(i));
     p->step_mkn.push_back({M, K, N});
     if (j > 0) {
       cmacs += (double)M * K * N;
@@ -1562,24 +1685,29 @@ int64_t plan_ws_bytes(const tn_plan *p, int kind, int64_t chunk, int64_t slices)
   return b;
 }
 
-extern "C" tn_status tn_path(tn_circuit *c, const tn_path_opts *opts, tn_plan **out, tn_plan_info *info) {
-  if (!c || !out) return tn_fail(TN_ERR_ARG, "tn_path: NULL argument");
-  *out = nullptr;
-  if (!c->evolved) return tn_fail(TN_ERR_STATE, "tn_path: call tn_evolve_two_sided first");
-  tn_path_opts o = opts ? *opts : tn_default_opts();
+// The host part of a plan of circuit c (its programs built): network, path, cuts, compiled and
+// checked steps, batch sizes. No device work; on failure p is left for the caller to delete.
+static tn_status plan_host(tn_circuit *c, const tn_path_opts &o, tn_plan *p) {
   const double limit = o.max_intermediate > 0 ? (double)o.max_intermediate : (double)(1LL << 24);
   if (o.n_cut_edges > 0 && !o.cut_edges) return tn_fail(TN_ERR_ARG, "tn_path: cut_edges is NULL");
+  if (o.layers < 0 || o.layers > 2) return tn_fail(TN_ERR_ARG, "tn_path: layers must be 1 or 2");
+  const bool two_layers = o.layers == 2;
+  if (two_layers && o.n_cut_edges > 0)
+    return tn_fail(TN_ERR_UNSUPPORTED, "tn_path: explicit cut edges are not accepted with the double-layer network");
   std::vector<char> keep(c->ne, 0);   // explicit cut edges stay edges of the network
   for (int j = 0; j < o.n_cut_edges; ++j) {
     const int e = o.cut_edges[j];
     if (e < 0 || e >= c->ne || keep[e]) return tn_fail(TN_ERR_ARG, "tn_path: bad or repeated cut edge %d", e);
     keep[e] = 1;
   }
-  tn_plan *p = new tn_plan();
   p->c = c;
   p->generation = c->generation;
-  p->net = identity_net(c);
-  if (!o.no_merge) merge_nodes(p->net, keep);
+  if (two_layers) {
+    p->net = double_layer_net(c);
+  } else {
+    p->net = identity_net(c);
+    if (!o.no_merge) merge_nodes(p->net, keep);
+  }
   const Net &g = p->net;
   std::vector<double> dims(g.ne);
   for (int e = 0; e < g.ne; ++e) dims[e] = (double)g.dc(e);
@@ -1587,7 +1715,7 @@ extern "C" tn_status tn_path(tn_circuit *c, const tn_path_opts *opts, tn_plan **
   int64_t pops = 0;
   tn_status s = path_auto(pg, o, p->order, p->score, pops, p->rank_used);
   p->pops = pops;
-  if (s != TN_OK) { delete p; return s; }
+  if (s != TN_OK) return s;
   // cuts: explicit, counted or automatic (thinnest frontier first), then the path of the cut network
   if (o.n_cut_edges > 0) {
     for (int j = 0; j < o.n_cut_edges; ++j)
@@ -1598,13 +1726,13 @@ extern "C" tn_status tn_path(tn_circuit *c, const tn_path_opts *opts, tn_plan **
     PathGraph pg2 = make_pg(g.n, g.eu, g.ev, cd2);
     s = path_auto(pg2, o, p->order, p->score, pops, p->rank_used);
     p->pops += pops;
-    if (s != TN_OK) { delete p; return s; }
+    if (s != TN_OK) return s;
   } else {
     s = choose_cuts(g, o, dims, o.n_cuts, limit, p->cuts, p->order, p->score, p->pops, p->rank_used);
-    if (s != TN_OK) { delete p; return s; }
+    if (s != TN_OK) return s;
   }
   s = compile_plan(p);
-  if (s != TN_OK) { delete p; return s; }
+  if (s != TN_OK) return s;
   const double budget = o.mem_budget_bytes > 0 ? o.mem_budget_bytes : 8.0 * (1ull << 30);
   for (int kind = 0; kind < 2; ++kind) {
     // as many whole bitstrings (all slices) as fit; else one bitstring and groups of its slices
@@ -1625,6 +1753,18 @@ extern "C" tn_status tn_path(tn_circuit *c, const tn_path_opts *opts, tn_plan **
     p->slice_chunk[kind] = sc;
     p->ws_bytes[kind] = plan_ws_bytes(p, kind, ch, sc);
   }
+  return TN_OK;
+}
+
+extern "C" tn_status tn_path(tn_circuit *c, const tn_path_opts *opts, tn_plan **out, tn_plan_info *info) {
+  if (!c || !out) return tn_fail(TN_ERR_ARG, "tn_path: NULL argument");
+  *out = nullptr;
+  if (!c->evolved) return tn_fail(TN_ERR_STATE, "tn_path: call tn_evolve_two_sided first");
+  const tn_path_opts o = opts ? *opts : tn_default_opts();
+  tn_plan *p = new tn_plan();
+  tn_status s = plan_host(c, o, p);
+  if (s != TN_OK) { delete p; return s; }
+  const bool two_layers = o.layers == 2;
   // upload tables
   cudaStream_t st = 0;
   s = c->mem.ensure(p->tab_dev, std::max<size_t>(p->tab_host.size(), 1) * sizeof(int32_t), st);
@@ -1636,15 +1776,69 @@ extern "C" tn_status tn_path(tn_circuit *c, const tn_path_opts *opts, tn_plan **
     delete p;
     return tn_fail(TN_ERR_CUDA, "table upload: %s", cudaGetErrorString(ce));
   }
+  if (two_layers) {   // the unit operand [1, 0]: complex128 at byte 0, complex64 at byte 32
+    s = c->mem.ensure(p->unit_dev, 64, st);
+    if (s != TN_OK) {
+      c->mem.release(p->tab_dev);
+      delete p;
+      return s;
+    }
+    uint8_t u[64] = {0};
+    const double one = 1.0;
+    const float onef = 1.0f;
+    std::memcpy(u, &one, sizeof one);
+    std::memcpy(u + 32, &onef, sizeof onef);
+    ce = cudaMemcpy(p->unit_dev.p, u, sizeof u, cudaMemcpyHostToDevice);
+    if (ce != cudaSuccess) {
+      c->mem.release(p->unit_dev);
+      c->mem.release(p->tab_dev);
+      delete p;
+      return tn_fail(TN_ERR_CUDA, "unit operand upload: %s", cudaGetErrorString(ce));
+    }
+  }
   fill_info(p, info);
   *out = p;
   return TN_OK;
 }
 
+extern "C" tn_status tn_plan_estimate(const tn_circuit *c, int32_t split_cycle, int32_t chi_max, double cutoff_rel,
+                                      const tn_path_opts *opts, tn_plan_info *info) {
+  if (!c || !info) return tn_fail(TN_ERR_ARG, "tn_plan_estimate: NULL argument");
+  if (split_cycle < 0 || chi_max < 0 || !(cutoff_rel >= 0) || cutoff_rel >= 1)
+    return tn_fail(TN_ERR_ARG, "tn_plan_estimate: bad split/chi/cutoff");
+  tn_circuit h;   // a host copy: graph, gates and the structural programs only
+  h.n = c->n;
+  h.ne = c->ne;
+  h.max_deg = c->max_deg;
+  h.eu = c->eu;
+  h.ev = c->ev;
+  h.legs = c->legs;
+  h.gates = c->gates;
+  std::vector<const tn_gate *> g1, g2;
+  for (const auto &g : h.gates) (g.cycle <= split_cycle ? g1 : g2).push_back(&g);
+  std::reverse(g2.begin(), g2.end());
+  build_half(&h, g1, false, chi_max, cutoff_rel, h.ket);
+  build_half(&h, g2, true, chi_max, cutoff_rel, h.bra);
+  h.split = split_cycle;
+  h.chi = chi_max;
+  h.cutoff = cutoff_rel;
+  h.evolved = true;
+  const tn_path_opts o = opts ? *opts : tn_default_opts();
+  tn_plan p;
+  const tn_status s = plan_host(&h, o, &p);
+  if (s != TN_OK) return s;
+  fill_info(&p, info);
+  return TN_OK;
+}
+
 extern "C" tn_status tn_plan_details(const tn_plan *p, int32_t *order, int32_t *cuts, int64_t *steps) {
   if (!p) return tn_fail(TN_ERR_ARG, "tn_plan_details: NULL plan");
-  if (order)
-    for (int j = 0; j < p->c->n; ++j) order[j] = j < p->net.n ? p->net.rep[p->order[j]] : -1;
+  if (order) {
+    if (!p->net.layer.empty())
+      for (int j = 0; j < p->net.n; ++j) order[j] = p->order[j];
+    else
+      for (int j = 0; j < p->c->n; ++j) order[j] = j < p->net.n ? p->net.rep[p->order[j]] : -1;
+  }
   if (cuts)
     for (size_t j = 0; j < p->cuts.size(); ++j) cuts[j] = p->net.eid[p->cuts[j]];
   if (steps)
@@ -1726,6 +1920,9 @@ tn_status ws_ensure(tn_plan *p, Workspace &w, int kind, cudaStream_t st) {
 }
 
 bool step_kernel_ok(const StepParams &s, tn_precision prec, int k) {
+  // a double-layer step (one tensor and the unit operand, a zero physical stride) never uses a
+  // kernel that builds the operand from node tensors staged in shared memory
+  if ((s.ket_sig == 0 || s.bra_sig == 0) && sk_is_tma(k) && sk_tma_bmode(k) == 1) return false;
   if (k < SK_TC) return simt_variant_ok(s, k);
   if (k == SK_TC) return prec != TN_FP64 && prec != TN_FP32 && prec != TN_BF16X6 && tc_step_supported(s);
   if (!sk_is_tma(k)) return false;
@@ -1874,6 +2071,20 @@ tn_status enqueue_chunk(tn_plan *p, Workspace &w, const uint64_t *bits_dev, int6
   }
   const size_t nsteps = p->steps.size();
   const int64_t cap = (int64_t)w.chunk * w.slice_chunk;     // items the buffers hold
+  // double-layer steps: the slot that is not the absorbed tensor's reads the unit operand
+  const void *unit = p->unit_dev.p ? (const void *)((const uint8_t *)p->unit_dev.p + (kind ? 32 : 0)) : nullptr;
+  auto operands = [&](size_t j, const ContractArgs &a, const void *&kj, const void *&bj, ContractArgs &aj) {
+    kj = ket;
+    bj = bra;
+    aj = a;
+    const int lay = j < p->step_layer.size() ? p->step_layer[j] : 0;
+    if (lay == 1) {
+      bj = unit;
+      aj.bra_stride = 0;
+    } else if (lay == 2) {
+      kj = unit;
+    }
+  };
   for (int64_t s0 = S0; s0 < S; s0 += w.slice_chunk) {
     const int64_t sg = std::min<int64_t>(w.slice_chunk, S - s0);
     ContractArgs a;
@@ -1885,14 +2096,18 @@ tn_status enqueue_chunk(tn_plan *p, Workspace &w, const uint64_t *bits_dev, int6
     a.bra_stride = g.bra_elems;
     void *tin = w.t0.p, *tout = w.t1.p;
     const double el = kind ? 8.0 : 16.0;
+    const void *kj, *bj;
+    ContractArgs aj;
     {
       ProfScope ps(kind ? "overlap_form_c64" : "overlap_form_c128", st, el * a.items * p->steps[0].N, 0);
       const OutDesc od = out_desc(tin, ks, 1, cap * p->maxT);
-      if (kind) CUDA_TRY(launch_form<float>(p->steps[0], a, ket, bra, od, st));
-      else CUDA_TRY(launch_form<double>(p->steps[0], a, ket, bra, od, st));
+      operands(0, a, kj, bj, aj);
+      if (kind) CUDA_TRY(launch_form<float>(p->steps[0], aj, kj, bj, od, st));
+      else CUDA_TRY(launch_form<double>(p->steps[0], aj, kj, bj, od, st));
     }
     for (size_t j = 1; j < nsteps; ++j) {
-      CUDA_TRY(enqueue_step(p, w, j, ks[j], prec, a, ket, bra, tin, tout,
+      operands(j, a, kj, bj, aj);
+      CUDA_TRY(enqueue_step(p, w, j, ks[j], prec, aj, kj, bj, tin, tout,
                             out_desc(tout, ks, j + 1, cap * p->maxT), st));
       std::swap(tin, tout);
     }
@@ -1964,5 +2179,6 @@ extern "C" void tn_plan_free(tn_plan *p) {
   cudaDeviceSynchronize();
   ws_release(p->c->mem, p->ws);
   p->c->mem.release(p->tab_dev);
+  p->c->mem.release(p->unit_dev);
   delete p;
 }

@@ -84,6 +84,10 @@ struct Net {
   std::vector<int64_t> ket_off, bra_off;          // node offsets in the ket / bra item
   int64_t ket_elems = 0, bra_elems = 0;           // item sizes including merged nodes
   std::vector<MergeParams> mk, mb;                // merge program of the ket / bra, in order
+  // Double-layer networks only (empty otherwise): 1 = the node is a ket tensor, 2 = a bra tensor.
+  // Such a node has one tensor, [legs in order] with leg dims dc, in its own half's item; the
+  // other operand slot of its steps reads the plan's two-value unit tensor [1, 0].
+  std::vector<int> layer;
   int64_t dc(int e) const { return dk[e] * db[e]; }
   bool merged() const { return !mk.empty(); }
 };
@@ -108,6 +112,8 @@ struct tn_plan {
   int64_t ws_bytes[2] = {0, 0};
   Workspace ws;
   Net net;                                        // nodes, legs and layouts the steps address
+  std::vector<int> step_layer;                    // per step: 0, or the absorbed node's layer (1 ket, 2 bra)
+  Buf unit_dev;                                   // double-layer plans: [1, 0] as complex128, then as complex64
   std::vector<int> tune[TN_TF32X6 + 1];           // per precision: a StepKernel per step (empty: heuristic)
 };
 

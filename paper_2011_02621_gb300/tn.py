@@ -57,7 +57,7 @@ class tn_path_opts(C.Structure):
     _fields_ = [("max_rank", C.c_int32), ("boundary_only", C.c_int32), ("connected", C.c_int32),
                 ("max_states", C.c_int64), ("n_cuts", C.c_int32), ("cut_edges", C.POINTER(C.c_int32)),
                 ("n_cut_edges", C.c_int32), ("max_intermediate", C.c_int64), ("mem_budget_bytes", C.c_double),
-                ("no_merge", C.c_int32)]
+                ("no_merge", C.c_int32), ("layers", C.c_int32)]
 
 
 class tn_plan_info(C.Structure):
@@ -90,6 +90,7 @@ def _load():
         "tn_circuit_bond_dims": (i32, [vp, i32, C.POINTER(i32)]),
         "tn_path": (i32, [vp, C.POINTER(tn_path_opts), C.POINTER(vp), C.POINTER(tn_plan_info)]),
         "tn_plan_details": (i32, [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i64)]),
+        "tn_plan_estimate": (i32, [vp, i32, i32, dbl, C.POINTER(tn_path_opts), C.POINTER(tn_plan_info)]),
         "tn_amplitudes": (i32, [vp, vp, i64, i32, vp, vp]),
         "tn_amplitudes_static": (i32, [vp, vp, i64, i32, vp, vp]),
         "tn_amplitudes_slices": (i32, [vp, vp, i64, i32, i64, i64, vp, vp]),
@@ -276,7 +277,7 @@ def tn_circuit_bond_dims(c: Circuit, side: int) -> np.ndarray:
 
 
 def _opts(max_rank=0, boundary_only=True, connected=True, max_states=0, n_cuts=-1, cut_edges=None,
-          max_intermediate=0, mem_budget_bytes=0.0, merge=True):
+          max_intermediate=0, mem_budget_bytes=0.0, merge=True, layers=1):
     o = tn_path_opts()
     o.max_rank = int(max_rank)
     o.boundary_only = 1 if boundary_only else 0
@@ -291,6 +292,7 @@ def _opts(max_rank=0, boundary_only=True, connected=True, max_states=0, n_cuts=-
     o.max_intermediate = int(max_intermediate)
     o.mem_budget_bytes = float(mem_budget_bytes)
     o.no_merge = 0 if merge else 1
+    o.layers = int(layers)
     return o, keep
 
 
@@ -306,8 +308,18 @@ def tn_path(c: Circuit, **opts) -> Plan:
     return Plan(out, c, _info_dict(info))
 
 
+def tn_plan_estimate(c: Circuit, split_cycle: int, chi: int = 0, cutoff: float = 1e-12, **opts) -> dict:
+    """The summary of the plan tn_path(**opts) would make after tn_evolve_two_sided(split_cycle,
+    chi, cutoff), from the structural bond bounds, on the host (no device needed)."""
+    o, keep = _opts(**opts)
+    info = tn_plan_info()
+    _check(LIB.tn_plan_estimate(c.ptr, int(split_cycle), int(chi), float(cutoff), C.byref(o), C.byref(info)))
+    del keep
+    return _info_dict(info)
+
+
 def tn_plan_details(p: Plan):
-    n = p.info["n_qubits"]
+    n = max(p.info["n_qubits"], p.info["n_nodes"])
     order = np.zeros(n, dtype=np.int32)
     cuts = np.zeros(max(p.info["n_cuts"], 1), dtype=np.int32)
     steps = np.zeros((max(p.info["n_steps"], 1), 3), dtype=np.int64)

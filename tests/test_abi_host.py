@@ -268,3 +268,59 @@ def test_planner_on_the_double_layer_network(tn):
     assert sorted(int(v) for v in order2) == list(range(2 * n))
     assert total2 == pytest.approx(opath.score([int(v) for v in order2], e2, d2), rel=1e-12)
     assert total2 < 0.2 * total1
+
+
+def _structural_dims(w, chi=None):
+    n, edges = w.graph.n, [tuple(sorted(e)) for e in w.graph.edges]
+    g1, g2 = otns.split_gates(w.gates, w.split)
+    chi = w.chi if chi is None else chi
+    kd = otns.structural_svd_nodes(n, edges, g1, chi, return_dims=True)[1]
+    bd = otns.structural_svd_nodes(n, edges, list(reversed(g2)), chi, return_dims=True)[1]
+    return n, edges, kd, bd
+
+
+@pytest.mark.parametrize("name", ["grid12", "syc53"])
+def test_plan_estimate_matches_the_oracle_structure(tn, name):
+    """The host-only plan estimate (no device) builds the gate programs with the library's own
+    structural recursion; its contraction cost equals the planner's cost on the oracle's
+    structural bonds, for the merged overlap network, the unmerged one and the double-layer one,
+    so both recursions give the same bonds. Every compiled table passed the plan's index check."""
+    w = gen.workload(name, n_bits=1)
+    n, edges, kd, bd = _structural_dims(w)
+    c = tn.tn_build(w.graph.n, w.graph.edges, w.gates, allocator=None)
+    merged = tn.tn_plan_estimate(c, w.split, w.chi, w.cutoff)
+    owner, order, ncut, total = tn.tn_merge_search(n, edges, kd, bd)
+    assert merged["n_nodes"] == len(order) and merged["n_steps"] == len(order) - 1
+    assert merged["n_cuts"] == ncut == 0
+    assert merged["cmacs"] == pytest.approx(total, rel=1e-12)
+    flat = tn.tn_plan_estimate(c, w.split, w.chi, w.cutoff, merge=False)
+    _, cuts1, total1 = tn.tn_cut_search(n, edges, [a * b for a, b in zip(kd, bd)])
+    assert flat["n_nodes"] == n and flat["cmacs"] == pytest.approx(total1, rel=1e-12)
+    dl = tn.tn_plan_estimate(c, w.split, w.chi, w.cutoff, layers=2)
+    e2 = edges + [(n + u, n + v) for u, v in edges] + [(q, n + q) for q in range(n)]
+    d2 = [float(x) for x in list(kd) + list(bd) + [2] * n]
+    _, cuts2, total2 = tn.tn_cut_search(2 * n, e2, d2)
+    assert dl["n_nodes"] == 2 * n and dl["n_steps"] == 2 * n - 1 and dl["n_cuts"] == len(cuts2)
+    assert dl["cmacs"] == pytest.approx(total2, rel=1e-12)
+    assert dl["cmacs"] < merged["cmacs"]
+
+
+def test_double_layer_plans_with_cuts_and_every_split(tn):
+    """Double-layer plans compile and pass the index check at every split of the 3x4 grid and
+    with cuts forced by a small intermediate limit (slice tables of ket-only and bra-only nodes)."""
+    w = gen.workload("grid12", n_bits=1)
+    c = tn.tn_build(w.graph.n, w.graph.edges, w.gates, allocator=None)
+    for split in range(0, w.depth + 1):
+        info = tn.tn_plan_estimate(c, split, 0, 1e-12, layers=2)
+        assert info["n_steps"] == 2 * w.graph.n - 1
+    cut = tn.tn_plan_estimate(c, 4, 0, 1e-12, layers=2, max_intermediate=64)
+    assert cut["n_cuts"] > 0 and cut["n_slices"] > 1 and cut["max_intermediate"] <= 64
+    with pytest.raises(tn.TNError) as e:
+        tn.tn_plan_estimate(c, 4, 0, 1e-12, layers=2, cut_edges=[0])
+    assert e.value.status == tn.TN_ERR_UNSUPPORTED
+    with pytest.raises(tn.TNError) as e:
+        tn.tn_plan_estimate(c, 4, 0, 1e-12, layers=3)
+    assert e.value.status == tn.TN_ERR_ARG
+    with pytest.raises(tn.TNError) as e:
+        tn.tn_plan_estimate(c, -1, 0, 1e-12)
+    assert e.value.status == tn.TN_ERR_ARG
