@@ -2028,6 +2028,23 @@ cudaError_t enqueue_step(const tn_plan *p, const Workspace &w, size_t j, int k, 
   return launch_step_tma(sp, a, A, B, od, (int *)w.err.p + 1, st, sk_tma_bn(k));
 }
 
+void step_operands(const tn_plan *p, size_t j, int kind, const void *ket, const void *bra, const ContractArgs &a,
+                   const void *&kj, const void *&bj, ContractArgs &aj) {
+  kj = ket;
+  bj = bra;
+  aj = a;
+  const int lay = j < p->step_layer.size() ? p->step_layer[j] : 0;
+  if (lay == 0) return;
+  // double-layer step: the slot that is not the absorbed tensor's reads the unit operand
+  const void *unit = (const uint8_t *)p->unit_dev.p + (kind ? 32 : 0);
+  if (lay == 1) {
+    bj = unit;
+    aj.bra_stride = 0;
+  } else {
+    kj = unit;
+  }
+}
+
 // Bra evolution and contraction of nb <= w.chunk bitstrings already on the device, amplitudes to
 // res_dev (nb complex128 on the device). Stream-ordered work only (no allocation, no host
 // synchronisation), so it can also be captured into a CUDA graph. The error words in w.err are
@@ -2071,19 +2088,8 @@ tn_status enqueue_chunk(tn_plan *p, Workspace &w, const uint64_t *bits_dev, int6
   }
   const size_t nsteps = p->steps.size();
   const int64_t cap = (int64_t)w.chunk * w.slice_chunk;     // items the buffers hold
-  // double-layer steps: the slot that is not the absorbed tensor's reads the unit operand
-  const void *unit = p->unit_dev.p ? (const void *)((const uint8_t *)p->unit_dev.p + (kind ? 32 : 0)) : nullptr;
   auto operands = [&](size_t j, const ContractArgs &a, const void *&kj, const void *&bj, ContractArgs &aj) {
-    kj = ket;
-    bj = bra;
-    aj = a;
-    const int lay = j < p->step_layer.size() ? p->step_layer[j] : 0;
-    if (lay == 1) {
-      bj = unit;
-      aj.bra_stride = 0;
-    } else if (lay == 2) {
-      kj = unit;
-    }
+    step_operands(p, j, kind, ket, bra, a, kj, bj, aj);
   };
   for (int64_t s0 = S0; s0 < S; s0 += w.slice_chunk) {
     const int64_t sg = std::min<int64_t>(w.slice_chunk, S - s0);

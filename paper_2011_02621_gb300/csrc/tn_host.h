@@ -145,6 +145,10 @@ struct WsSizes {
 WsSizes ws_sizes(const tn_plan *p, int kind, int64_t chunk, int64_t slices);
 void ws_carve(Workspace &w, void *base, const WsSizes &z, int64_t chunk, int64_t slices, cudaStream_t st);
 bool is_device_ptr(const void *p);
+// the operands of step j: the plan's ket and bra buffers, or for a double-layer step the absorbed
+// tensor's buffer and the unit operand (kind 0: complex128, 1: complex64) with its arguments
+void step_operands(const tn_plan *p, size_t j, int kind, const void *ket, const void *bra, const ContractArgs &a,
+                   const void *&kj, const void *&bj, ContractArgs &aj);
 // one contraction step j with kernel k (with the overlap formation that kernel needs); no host sync
 cudaError_t enqueue_step(const tn_plan *p, const Workspace &w, size_t j, int k, tn_precision prec,
                          const ContractArgs &a, const void *ket, const void *bra, const void *tin, void *tout,

@@ -92,8 +92,11 @@ extern "C" tn_status tn_autotune(tn_plan *p, tn_precision prec, int64_t n_bits, 
       cudaError_t e = cudaSuccess;
       for (int rep = 0, r = 1; rep < 2; ++rep) {
         CUDA_TRY(cudaEventRecord(ev.a, st));
+        const void *kj, *bj;
+        ContractArgs aj;
+        step_operands(p, j, kind, ket, bra, a, kj, bj, aj);
         for (int i = 0; i < r && e == cudaSuccess; ++i)
-          e = enqueue_step(p, w, j, k, prec, a, ket, bra, w.t0.p, w.t1.p, od, st);
+          e = enqueue_step(p, w, j, k, prec, aj, kj, bj, w.t0.p, w.t1.p, od, st);
         if (e != cudaSuccess) {
           cudaStreamSynchronize(st);
           return tn_fail(TN_ERR_CUDA, "step %zu kernel %d: %s", j, k, cudaGetErrorString(e));
