@@ -192,6 +192,31 @@ tn_status tn_path(tn_circuit *c, const tn_path_opts *opts, tn_plan **out, tn_pla
 tn_status tn_plan_estimate(const tn_circuit *c, int32_t split_cycle, int32_t chi_max, double cutoff_rel,
                            const tn_path_opts *opts, tn_plan_info *info);
 
+/* Host-only inspection of the compiled steps of the plan tn_plan_estimate describes (same
+ * arguments), for CPU models of the contraction and checks of the plan compiler. Call once with
+ * NULL layout/steps/tables to get *n_steps and *n_tables, then with buffers of these sizes:
+ *   layout[8 + 2*n_qubits + 2*n_edges]: max intermediate (item stride), slices, steps, ket and
+ *     bra item elements of the network (with merged nodes), 1 if nodes were merged, ket and bra
+ *     item elements of the halves; per qubit its ket and bra node offsets; per edge its ket and
+ *     bra bond. A node tensor is [sigma, legs in increasing edge id], complex, row-major.
+ *   steps[n_steps * TN_STEP_DESC_LEN]: per step M, K, N, layer (0 overlap node, 1 ket tensor,
+ *     2 bra tensor of a double-layer plan), n_rest, ket_off, ket_sig, bra_off, bra_sig, phys,
+ *     the table offsets of ocol, bka, bkb, bna, bnb, sa, sb, then TN_PLAN_MAXREST rest dims
+ *     (slowest first) and TN_PLAN_MAXREST rest output strides.
+ *   tables[n_tables]: the int32 tables.
+ * A step computes, per item (bitstring b, slice l): with x = ket + ket_off + sa[l] and
+ * y = bra_b + bra_off + sb[l], C[k][n] = sum_{s < phys} x[bka[k] + bna[n] + s*ket_sig] *
+ * y[bkb[k] + bnb[n] + s*bra_sig]; out[orow(m) + ocol[n]] = sum_k in[m*K + k] C[k][n], orow(m)
+ * the mixed-radix digits of m over the rest dims times their strides. Step 0 writes C[0][n] at
+ * ocol[n]. For layer 1 (2) steps y (x) is the unit operand [1, 0]. The amplitude is the sum over
+ * slices of the last step's out[0].
+ * Errors: TN_ERR_ARG, TN_ERR_NO_PATH, TN_ERR_UNSUPPORTED. */
+#define TN_PLAN_MAXREST 32
+#define TN_STEP_DESC_LEN (17 + 2 * TN_PLAN_MAXREST)
+tn_status tn_plan_inspect(const tn_circuit *c, int32_t split_cycle, int32_t chi_max, double cutoff_rel,
+                          const tn_path_opts *opts, int64_t *layout, int64_t *steps, int32_t *tables,
+                          int64_t *n_steps, int64_t *n_tables);
+
 /* Plan details: order[max(n_qubits, n_nodes)] (contraction order of the network's nodes,
  * each named by its representative qubit, then -1 for the merged qubits; for a double-layer
  * plan the 2 n_qubits node ids), cuts[n_cuts] (circuit edge ids; network edge ids for a

@@ -1801,12 +1801,12 @@ extern "C" tn_status tn_path(tn_circuit *c, const tn_path_opts *opts, tn_plan **
   return TN_OK;
 }
 
-extern "C" tn_status tn_plan_estimate(const tn_circuit *c, int32_t split_cycle, int32_t chi_max, double cutoff_rel,
-                                      const tn_path_opts *opts, tn_plan_info *info) {
-  if (!c || !info) return tn_fail(TN_ERR_ARG, "tn_plan_estimate: NULL argument");
+// A host copy of circuit c with the structural gate programs of (split, chi, cutoff) and no
+// device state: what tn_path compiles, without the rank probe and the ket evolution.
+static tn_status host_programs(const tn_circuit *c, int32_t split_cycle, int32_t chi_max, double cutoff_rel,
+                               tn_circuit &h) {
   if (split_cycle < 0 || chi_max < 0 || !(cutoff_rel >= 0) || cutoff_rel >= 1)
-    return tn_fail(TN_ERR_ARG, "tn_plan_estimate: bad split/chi/cutoff");
-  tn_circuit h;   // a host copy: graph, gates and the structural programs only
+    return tn_fail(TN_ERR_ARG, "bad split/chi/cutoff");
   h.n = c->n;
   h.ne = c->ne;
   h.max_deg = c->max_deg;
@@ -1823,11 +1823,68 @@ extern "C" tn_status tn_plan_estimate(const tn_circuit *c, int32_t split_cycle, 
   h.chi = chi_max;
   h.cutoff = cutoff_rel;
   h.evolved = true;
+  return TN_OK;
+}
+
+extern "C" tn_status tn_plan_estimate(const tn_circuit *c, int32_t split_cycle, int32_t chi_max, double cutoff_rel,
+                                      const tn_path_opts *opts, tn_plan_info *info) {
+  if (!c || !info) return tn_fail(TN_ERR_ARG, "tn_plan_estimate: NULL argument");
+  tn_circuit h;
+  tn_status s = host_programs(c, split_cycle, chi_max, cutoff_rel, h);
+  if (s != TN_OK) return s;
   const tn_path_opts o = opts ? *opts : tn_default_opts();
   tn_plan p;
-  const tn_status s = plan_host(&h, o, &p);
-  if (s != TN_OK) return s;
+  if ((s = plan_host(&h, o, &p)) != TN_OK) return s;
   fill_info(&p, info);
+  return TN_OK;
+}
+
+static_assert(TN_PLAN_MAXREST == TN_MAXREST, "rest-leg limit of the inspection layout");
+
+extern "C" tn_status tn_plan_inspect(const tn_circuit *c, int32_t split_cycle, int32_t chi_max, double cutoff_rel,
+                                     const tn_path_opts *opts, int64_t *layout, int64_t *steps, int32_t *tables,
+                                     int64_t *n_steps, int64_t *n_tables) {
+  if (!c || !n_steps || !n_tables) return tn_fail(TN_ERR_ARG, "tn_plan_inspect: NULL argument");
+  tn_circuit h;
+  tn_status s = host_programs(c, split_cycle, chi_max, cutoff_rel, h);
+  if (s != TN_OK) return s;
+  const tn_path_opts o = opts ? *opts : tn_default_opts();
+  tn_plan p;
+  if ((s = plan_host(&h, o, &p)) != TN_OK) return s;
+  *n_steps = (int64_t)p.steps.size();
+  *n_tables = (int64_t)p.tab_host.size();
+  if (layout) {
+    layout[0] = p.maxT;
+    layout[1] = p.n_slices;
+    layout[2] = (int64_t)p.steps.size();
+    layout[3] = p.net.ket_elems;
+    layout[4] = p.net.bra_elems;
+    layout[5] = p.net.merged() ? 1 : 0;
+    layout[6] = h.ket.item_elems;
+    layout[7] = h.bra.item_elems;
+    for (int q = 0; q < h.n; ++q) {
+      layout[8 + 2 * q] = h.ket.node_off[q];
+      layout[9 + 2 * q] = h.bra.node_off[q];
+    }
+    const int64_t b = 8 + 2 * (int64_t)h.n;
+    for (int e = 0; e < h.ne; ++e) {
+      layout[b + 2 * e] = h.ket.dims[e];
+      layout[b + 2 * e + 1] = h.bra.dims[e];
+    }
+  }
+  if (steps)
+    for (size_t j = 0; j < p.steps.size(); ++j) {
+      const StepParams &q = p.steps[j];
+      int64_t *d = steps + (int64_t)j * TN_STEP_DESC_LEN;
+      const int64_t head[17] = {q.M, q.K, q.N, p.step_layer[j], q.n_rest, q.ket_off, q.ket_sig, q.bra_off,
+                                q.bra_sig, q.phys, q.t_ocol, q.t_bka, q.t_bkb, q.t_bna, q.t_bnb, q.t_sa, q.t_sb};
+      for (int t = 0; t < 17; ++t) d[t] = head[t];
+      for (int r = 0; r < TN_MAXREST; ++r) {
+        d[17 + r] = r < q.n_rest ? q.rest_dim[r] : 0;
+        d[17 + TN_MAXREST + r] = r < q.n_rest ? q.rest_ostride[r] : 0;
+      }
+    }
+  if (tables) std::memcpy(tables, p.tab_host.data(), p.tab_host.size() * sizeof(int32_t));
   return TN_OK;
 }
 

@@ -91,6 +91,8 @@ def _load():
         "tn_path": (i32, [vp, C.POINTER(tn_path_opts), C.POINTER(vp), C.POINTER(tn_plan_info)]),
         "tn_plan_details": (i32, [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i64)]),
         "tn_plan_estimate": (i32, [vp, i32, i32, dbl, C.POINTER(tn_path_opts), C.POINTER(tn_plan_info)]),
+        "tn_plan_inspect": (i32, [vp, i32, i32, dbl, C.POINTER(tn_path_opts), C.POINTER(i64), C.POINTER(i64),
+                                  C.POINTER(i32), C.POINTER(i64), C.POINTER(i64)]),
         "tn_amplitudes": (i32, [vp, vp, i64, i32, vp, vp]),
         "tn_amplitudes_static": (i32, [vp, vp, i64, i32, vp, vp]),
         "tn_amplitudes_slices": (i32, [vp, vp, i64, i32, i64, i64, vp, vp]),
@@ -316,6 +318,40 @@ def tn_plan_estimate(c: Circuit, split_cycle: int, chi: int = 0, cutoff: float =
     _check(LIB.tn_plan_estimate(c.ptr, int(split_cycle), int(chi), float(cutoff), C.byref(o), C.byref(info)))
     del keep
     return _info_dict(info)
+
+
+STEP_DESC_LEN = 17 + 2 * 32
+STEP_FIELDS = ("M", "K", "N", "layer", "n_rest", "ket_off", "ket_sig", "bra_off", "bra_sig", "phys", "t_ocol",
+               "t_bka", "t_bkb", "t_bna", "t_bnb", "t_sa", "t_sb")
+
+
+def tn_plan_inspect(c: Circuit, split_cycle: int, chi: int = 0, cutoff: float = 1e-12, **opts):
+    """(layout, steps, tables) of the plan tn_plan_estimate describes, on the host: layout a dict
+    (item stride, slices, item sizes, per-qubit node offsets, per-edge bonds), steps a list of
+    dicts (the fields of STEP_FIELDS, rest_dim, rest_ostride), tables an int32 array."""
+    o, keep = _opts(**opts)
+    ns, nt = C.c_int64(), C.c_int64()
+    _check(LIB.tn_plan_inspect(c.ptr, int(split_cycle), int(chi), float(cutoff), C.byref(o), None, None, None,
+                               C.byref(ns), C.byref(nt)))
+    lay = np.zeros(8 + 2 * c.n_qubits + 2 * c.n_edges, dtype=np.int64)
+    st = np.zeros((max(ns.value, 1), STEP_DESC_LEN), dtype=np.int64)
+    tab = np.zeros(max(nt.value, 1), dtype=np.int32)
+    _check(LIB.tn_plan_inspect(c.ptr, int(split_cycle), int(chi), float(cutoff), C.byref(o),
+                               lay.ctypes.data_as(C.POINTER(C.c_int64)), st.ctypes.data_as(C.POINTER(C.c_int64)),
+                               tab.ctypes.data_as(C.POINTER(C.c_int32)), C.byref(ns), C.byref(nt)))
+    del keep
+    n, ne = c.n_qubits, c.n_edges
+    layout = dict(max_t=int(lay[0]), n_slices=int(lay[1]), n_steps=int(lay[2]), ket_elems=int(lay[3]),
+                  bra_elems=int(lay[4]), merged=bool(lay[5]), ket_half_elems=int(lay[6]), bra_half_elems=int(lay[7]),
+                  ket_off=lay[8:8 + 2 * n:2].copy(), bra_off=lay[9:8 + 2 * n:2].copy(),
+                  ket_dims=lay[8 + 2 * n::2][:ne].copy(), bra_dims=lay[9 + 2 * n::2][:ne].copy())
+    steps = []
+    for row in st[: ns.value]:
+        d = {f: int(v) for f, v in zip(STEP_FIELDS, row[:17])}
+        d["rest_dim"] = [int(x) for x in row[17:17 + d["n_rest"]]]
+        d["rest_ostride"] = [int(x) for x in row[17 + 32:17 + 32 + d["n_rest"]]]
+        steps.append(d)
+    return layout, steps, tab[: nt.value].copy()
 
 
 def tn_plan_details(p: Plan):
