@@ -179,7 +179,8 @@ tn_status tn_circuit_bond_dims(const tn_circuit *c, int32_t side, int32_t *out);
  * physical index). The sums are those of Eq. overlap without forming the per-qubit overlap
  * tensors first, so the amplitudes are the same; each step absorbs one ket tensor (the same for
  * every bitstring) or one bra tensor. No merging; explicit cut_edges are not accepted
- * (TN_ERR_UNSUPPORTED); automatic cuts are.
+ * (TN_ERR_UNSUPPORTED); automatic cuts are. The path search holds at most 128 nodes, so the
+ * double-layer network takes circuits of at most 64 qubits (TN_ERR_UNSUPPORTED above).
  * Errors: TN_ERR_STATE, TN_ERR_NO_PATH, TN_ERR_ARG, TN_ERR_CUDA, TN_ERR_OOM, TN_ERR_UNSUPPORTED. */
 tn_status tn_path(tn_circuit *c, const tn_path_opts *opts, tn_plan **out, tn_plan_info *info);
 

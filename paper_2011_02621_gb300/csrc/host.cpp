@@ -776,6 +776,7 @@ static PathGraph make_pg(int n, const std::vector<int> &eu, const std::vector<in
 static tn_status alg1(const PathGraph &pg, int max_rank, bool boundary_only, bool connected, int64_t max_states,
                       std::vector<int> &order, double &score, int64_t &pops) {
   const int n = pg.n;
+  if (n > 128) return tn_fail(TN_ERR_UNSUPPORTED, "Algorithm 1: at most 128 network nodes (got %d)", n);
   std::vector<PEntry> arena;
   arena.reserve(1 << 16);
   std::priority_queue<HeapKey> pq;
@@ -1700,6 +1701,8 @@ static tn_status plan_host(tn_circuit *c, const tn_path_opts &o, tn_plan *p) {
     if (e < 0 || e >= c->ne || keep[e]) return tn_fail(TN_ERR_ARG, "tn_path: bad or repeated cut edge %d", e);
     keep[e] = 1;
   }
+  if (two_layers && 2 * c->n > 128)
+    return tn_fail(TN_ERR_UNSUPPORTED, "tn_path: the double-layer network of %d qubits has more than 128 nodes", c->n);
   p->c = c;
   p->generation = c->generation;
   if (two_layers) {

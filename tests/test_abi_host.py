@@ -324,3 +324,14 @@ def test_double_layer_plans_with_cuts_and_every_split(tn):
     with pytest.raises(tn.TNError) as e:
         tn.tn_plan_estimate(c, -1, 0, 1e-12)
     assert e.value.status == tn.TN_ERR_ARG
+
+
+def test_double_layer_network_node_limit(tn):
+    """The path search holds at most 128 nodes: a double-layer network of more than 64 qubits
+    is refused with TN_ERR_UNSUPPORTED (the 104-qubit grid), its overlap network is planned."""
+    w = gen.workload("syc104", n_bits=1)
+    c = tn.tn_build(w.graph.n, w.graph.edges, w.gates, allocator=None)
+    with pytest.raises(tn.TNError) as e:
+        tn.tn_plan_estimate(c, w.split, w.chi, w.cutoff, layers=2)
+    assert e.value.status == tn.TN_ERR_UNSUPPORTED
+    assert tn.tn_plan_estimate(c, w.split, w.chi, w.cutoff)["n_nodes"] <= w.graph.n
