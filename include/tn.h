@@ -118,6 +118,9 @@ typedef struct {
                                <= 2 into a neighbour first (exact; see tn_path) */
   int32_t layers;           /* 0 or 1 = the overlap network of Eq. overlap (one node per qubit);
                                2 = the double-layer network (see tn_path) */
+  double byte_weight;       /* 0 = Algorithm 1's score (complex MACs); w > 0 adds w x (input +
+                               output elements) per step, for steps bound by memory traffic
+                               (w ~ compute rate / bandwidth in complex MACs per element) */
 } tn_path_opts;
 
 /* Summary of a plan. All counts are per amplitude unless stated. */

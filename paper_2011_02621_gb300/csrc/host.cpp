@@ -46,6 +46,19 @@ extern "C" int64_t tn_launch_count(int32_t reset) {
 
 extern "C" const char *tn_last_error(void) { return g_err.c_str(); }
 
+// Runs f (returning tn_status) so that no C++ exception crosses the C ABI: host memory
+// exhaustion becomes TN_ERR_OOM, anything else TN_ERR_UNSUPPORTED with its message.
+template <typename F>
+static tn_status no_throw(const char *what, F &&f) {
+  try {
+    return f();
+  } catch (const std::bad_alloc &) {
+    return tn_fail(TN_ERR_OOM, "%s: host memory exhausted", what);
+  } catch (const std::exception &e) {
+    return tn_fail(TN_ERR_UNSUPPORTED, "%s: %s", what, e.what());
+  }
+}
+
 // ---------------------------------------------------------------------------
 // tracing
 // ---------------------------------------------------------------------------
@@ -774,7 +787,7 @@ static PathGraph make_pg(int n, const std::vector<int> &eu, const std::vector<in
 }
 
 static tn_status alg1(const PathGraph &pg, int max_rank, bool boundary_only, bool connected, int64_t max_states,
-                      std::vector<int> &order, double &score, int64_t &pops) {
+                      std::vector<int> &order, double &score, int64_t &pops, double byte_weight = 0) {
   const int n = pg.n;
   if (n > 128) return tn_fail(TN_ERR_UNSUPPORTED, "Algorithm 1: at most 128 network nodes (got %d)", n);
   std::vector<PEntry> arena;
@@ -850,8 +863,9 @@ static tn_status alg1(const PathGraph &pg, int max_rank, bool boundary_only, boo
       PEntry e;
       e.mask = cur.mask;
       e.mask.set(i);
-      e.score = cur.score + cur.prod_open * fresh;     // Cost = prod of dims over legs of C^S and C^i
       e.prod_open = cur.prod_open / shared * fresh;
+      // Cost = prod of dims over legs of C^S and C^i (+ byte_weight x the step's input and output)
+      e.score = cur.score + cur.prod_open * fresh + (byte_weight > 0 ? byte_weight * (cur.prod_open + e.prod_open) : 0.0);
       e.parent = hk.idx;
       e.last = (uint8_t)i;
       e.m = (uint8_t)(cur.m + 1);
@@ -871,7 +885,7 @@ static tn_status path_auto(const PathGraph &pg, const tn_path_opts &o, std::vect
   const int64_t cap = o.max_states > 0 ? o.max_states : 4000000;
   if (o.max_rank > 0 || !o.connected) {
     rank_used = o.max_rank;
-    return alg1(pg, o.max_rank, o.boundary_only != 0, o.connected != 0, cap, order, score, pops);
+    return alg1(pg, o.max_rank, o.boundary_only != 0, o.connected != 0, cap, order, score, pops, o.byte_weight);
   }
   int maxdeg = 0;
   for (int q = 0; q < pg.n; ++q) maxdeg = std::max(maxdeg, (int)pg.adj[q].size());
@@ -887,7 +901,7 @@ static tn_status path_auto(const PathGraph &pg, const tn_path_opts &o, std::vect
     int64_t p = 0;
     std::vector<int> ord;
     double sc = 0;
-    tn_status r = alg1(pg, M, o.boundary_only != 0, true, cap, ord, sc, p);
+    tn_status r = alg1(pg, M, o.boundary_only != 0, true, cap, ord, sc, p, o.byte_weight);
     total += p;
     if (r != TN_OK) {
       if (first >= 0) break;   // a larger M ran out of states: keep what was found
@@ -909,7 +923,7 @@ static tn_status path_auto(const PathGraph &pg, const tn_path_opts &o, std::vect
   return s;
 }
 
-extern "C" tn_status tn_path_search(const tn_graph *g, const double *dims, const tn_path_opts *opts, int32_t *order,
+static tn_status tn_path_search_impl(const tn_graph *g, const double *dims, const tn_path_opts *opts, int32_t *order,
                                     double *score, int64_t *states_expanded) {
   if (!g || !dims || !order) return tn_fail(TN_ERR_ARG, "tn_path_search: NULL argument");
   std::vector<int> eu, ev;
@@ -932,6 +946,11 @@ extern "C" tn_status tn_path_search(const tn_graph *g, const double *dims, const
   for (int i = 0; i < g->n_qubits; ++i) order[i] = ord[i];
   if (score) *score = sc;
   return TN_OK;
+}
+
+extern "C" tn_status tn_path_search(const tn_graph *g, const double *dims, const tn_path_opts *opts, int32_t *order,
+                                      double *score, int64_t *states_expanded) {
+  return no_throw("tn_path_search", [&] { return tn_path_search_impl(g, dims, opts, order, score, states_expanded); });
 }
 
 tn_path_opts tn_default_opts() {
@@ -1019,7 +1038,7 @@ static tn_status choose_cuts(const Net &c, const tn_path_opts &o, std::vector<do
   return TN_OK;
 }
 
-extern "C" tn_status tn_cut_search(const tn_graph *g, const double *dims, const tn_path_opts *opts, int32_t *order,
+static tn_status tn_cut_search_impl(const tn_graph *g, const double *dims, const tn_path_opts *opts, int32_t *order,
                                    int32_t *cuts, int32_t *n_cuts, double *total_cmacs) {
   if (!g || !dims || !order || !n_cuts) return tn_fail(TN_ERR_ARG, "tn_cut_search: NULL argument");
   Net tmp;
@@ -1059,6 +1078,11 @@ extern "C" tn_status tn_cut_search(const tn_graph *g, const double *dims, const 
   *n_cuts = (int32_t)cut.size();
   if (total_cmacs) *total_cmacs = slices * score;
   return TN_OK;
+}
+
+extern "C" tn_status tn_cut_search(const tn_graph *g, const double *dims, const tn_path_opts *opts, int32_t *order,
+                                     int32_t *cuts, int32_t *n_cuts, double *total_cmacs) {
+  return no_throw("tn_cut_search", [&] { return tn_cut_search_impl(g, dims, opts, order, cuts, n_cuts, total_cmacs); });
 }
 
 static int64_t dc_of(const tn_circuit *c, int e) { return (int64_t)c->ket.dims[e] * c->bra.dims[e]; }
@@ -1288,7 +1312,7 @@ static void merge_nodes(Net &g, const std::vector<char> &keep_edge) {
   g = h;
 }
 
-extern "C" tn_status tn_merge_search(const tn_graph *g, const int32_t *ket_dims, const int32_t *bra_dims,
+static tn_status tn_merge_search_impl(const tn_graph *g, const int32_t *ket_dims, const int32_t *bra_dims,
                                      const tn_path_opts *opts, int32_t *owner, int32_t *n_nodes, int32_t *order,
                                      int32_t *n_cuts, double *total_cmacs) {
   if (!g || !ket_dims || !bra_dims || !owner || !n_nodes || !order)
@@ -1346,6 +1370,12 @@ extern "C" tn_status tn_merge_search(const tn_graph *g, const int32_t *ket_dims,
   if (n_cuts) *n_cuts = (int32_t)cut.size();
   if (total_cmacs) *total_cmacs = slices * score;
   return TN_OK;
+}
+
+extern "C" tn_status tn_merge_search(const tn_graph *g, const int32_t *ket_dims, const int32_t *bra_dims,
+                                       const tn_path_opts *opts, int32_t *owner, int32_t *n_nodes, int32_t *order,
+                                       int32_t *n_cuts, double *total_cmacs) {
+  return no_throw("tn_merge_search", [&] { return tn_merge_search_impl(g, ket_dims, bra_dims, opts, owner, n_nodes, order, n_cuts, total_cmacs); });
 }
 
 // Every device index a compiled plan can produce, checked on the host before any launch: node
@@ -1425,6 +1455,13 @@ static tn_status compile_plan(tn_plan *p) {
   for (int e : p->cuts) is_cut[e] = 1;
   std::vector<int64_t> cut_stride(p->cuts.size());
   {
+    double sd = 1;   // checked in floating point first: the product can overflow int64
+    for (int e : p->cuts) sd *= (double)c.dc(e);
+    // every step holds two int32 offset tables over the slices
+    if (sd * 2.0 * n >= (double)(1LL << 31))
+      return tn_fail(TN_ERR_UNSUPPORTED,
+                     "%.3g slices: their offset tables exceed the plan's table limit; allow larger intermediates "
+                     "(max_intermediate) or cap the bonds (chi)", sd);
     int64_t s = 1;
     for (int j = (int)p->cuts.size() - 1; j >= 0; --j) { cut_stride[j] = s; s *= c.dc(p->cuts[j]); }
     p->n_slices = s;
@@ -1765,7 +1802,7 @@ extern "C" tn_status tn_path(tn_circuit *c, const tn_path_opts *opts, tn_plan **
   if (!c->evolved) return tn_fail(TN_ERR_STATE, "tn_path: call tn_evolve_two_sided first");
   const tn_path_opts o = opts ? *opts : tn_default_opts();
   tn_plan *p = new tn_plan();
-  tn_status s = plan_host(c, o, p);
+  tn_status s = no_throw("tn_path", [&] { return plan_host(c, o, p); });
   if (s != TN_OK) { delete p; return s; }
   const bool two_layers = o.layers == 2;
   // upload tables
@@ -1829,9 +1866,8 @@ static tn_status host_programs(const tn_circuit *c, int32_t split_cycle, int32_t
   return TN_OK;
 }
 
-extern "C" tn_status tn_plan_estimate(const tn_circuit *c, int32_t split_cycle, int32_t chi_max, double cutoff_rel,
-                                      const tn_path_opts *opts, tn_plan_info *info) {
-  if (!c || !info) return tn_fail(TN_ERR_ARG, "tn_plan_estimate: NULL argument");
+static tn_status plan_estimate_impl(const tn_circuit *c, int32_t split_cycle, int32_t chi_max, double cutoff_rel,
+                                    const tn_path_opts *opts, tn_plan_info *info) {
   tn_circuit h;
   tn_status s = host_programs(c, split_cycle, chi_max, cutoff_rel, h);
   if (s != TN_OK) return s;
@@ -1842,12 +1878,17 @@ extern "C" tn_status tn_plan_estimate(const tn_circuit *c, int32_t split_cycle, 
   return TN_OK;
 }
 
+extern "C" tn_status tn_plan_estimate(const tn_circuit *c, int32_t split_cycle, int32_t chi_max, double cutoff_rel,
+                                      const tn_path_opts *opts, tn_plan_info *info) {
+  if (!c || !info) return tn_fail(TN_ERR_ARG, "tn_plan_estimate: NULL argument");
+  return no_throw("tn_plan_estimate", [&] { return plan_estimate_impl(c, split_cycle, chi_max, cutoff_rel, opts, info); });
+}
+
 static_assert(TN_PLAN_MAXREST == TN_MAXREST, "rest-leg limit of the inspection layout");
 
-extern "C" tn_status tn_plan_inspect(const tn_circuit *c, int32_t split_cycle, int32_t chi_max, double cutoff_rel,
-                                     const tn_path_opts *opts, int64_t *layout, int64_t *steps, int32_t *tables,
-                                     int64_t *n_steps, int64_t *n_tables) {
-  if (!c || !n_steps || !n_tables) return tn_fail(TN_ERR_ARG, "tn_plan_inspect: NULL argument");
+static tn_status plan_inspect_impl(const tn_circuit *c, int32_t split_cycle, int32_t chi_max, double cutoff_rel,
+                                   const tn_path_opts *opts, int64_t *layout, int64_t *steps, int32_t *tables,
+                                   int64_t *n_steps, int64_t *n_tables) {
   tn_circuit h;
   tn_status s = host_programs(c, split_cycle, chi_max, cutoff_rel, h);
   if (s != TN_OK) return s;
@@ -1889,6 +1930,15 @@ extern "C" tn_status tn_plan_inspect(const tn_circuit *c, int32_t split_cycle, i
     }
   if (tables) std::memcpy(tables, p.tab_host.data(), p.tab_host.size() * sizeof(int32_t));
   return TN_OK;
+}
+
+extern "C" tn_status tn_plan_inspect(const tn_circuit *c, int32_t split_cycle, int32_t chi_max, double cutoff_rel,
+                                     const tn_path_opts *opts, int64_t *layout, int64_t *steps, int32_t *tables,
+                                     int64_t *n_steps, int64_t *n_tables) {
+  if (!c || !n_steps || !n_tables) return tn_fail(TN_ERR_ARG, "tn_plan_inspect: NULL argument");
+  return no_throw("tn_plan_inspect", [&] {
+    return plan_inspect_impl(c, split_cycle, chi_max, cutoff_rel, opts, layout, steps, tables, n_steps, n_tables);
+  });
 }
 
 extern "C" tn_status tn_plan_details(const tn_plan *p, int32_t *order, int32_t *cuts, int64_t *steps) {

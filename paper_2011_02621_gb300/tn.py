@@ -57,7 +57,7 @@ class tn_path_opts(C.Structure):
     _fields_ = [("max_rank", C.c_int32), ("boundary_only", C.c_int32), ("connected", C.c_int32),
                 ("max_states", C.c_int64), ("n_cuts", C.c_int32), ("cut_edges", C.POINTER(C.c_int32)),
                 ("n_cut_edges", C.c_int32), ("max_intermediate", C.c_int64), ("mem_budget_bytes", C.c_double),
-                ("no_merge", C.c_int32), ("layers", C.c_int32)]
+                ("no_merge", C.c_int32), ("layers", C.c_int32), ("byte_weight", C.c_double)]
 
 
 class tn_plan_info(C.Structure):
@@ -279,7 +279,7 @@ def tn_circuit_bond_dims(c: Circuit, side: int) -> np.ndarray:
 
 
 def _opts(max_rank=0, boundary_only=True, connected=True, max_states=0, n_cuts=-1, cut_edges=None,
-          max_intermediate=0, mem_budget_bytes=0.0, merge=True, layers=1):
+          max_intermediate=0, mem_budget_bytes=0.0, merge=True, layers=1, byte_weight=0.0):
     o = tn_path_opts()
     o.max_rank = int(max_rank)
     o.boundary_only = 1 if boundary_only else 0
@@ -295,6 +295,7 @@ def _opts(max_rank=0, boundary_only=True, connected=True, max_states=0, n_cuts=-
     o.mem_budget_bytes = float(mem_budget_bytes)
     o.no_merge = 0 if merge else 1
     o.layers = int(layers)
+    o.byte_weight = float(byte_weight)
     return o, keep
 
 

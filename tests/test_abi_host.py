@@ -335,3 +335,15 @@ def test_double_layer_network_node_limit(tn):
         tn.tn_plan_estimate(c, w.split, w.chi, w.cutoff, layers=2)
     assert e.value.status == tn.TN_ERR_UNSUPPORTED
     assert tn.tn_plan_estimate(c, w.split, w.chi, w.cutoff)["n_nodes"] <= w.graph.n
+
+
+def test_planning_failures_are_statuses_not_exceptions(tn):
+    """Untruncated 12-cycle circuit on 40 qubits (random 3-regular graph): the overlap network
+    needs about 1e9 slices, whose offset tables the plan cannot hold. The host-only call returns
+    TN_ERR_UNSUPPORTED; no C++ exception (an allocation failure) crosses the C ABI."""
+    w = gen.regular3_family(count=32, n_bits=1)[31]
+    assert w.graph.n == 40
+    c = tn.tn_build(w.graph.n, w.graph.edges, w.gates, allocator=None)
+    with pytest.raises(tn.TNError) as e:
+        tn.tn_plan_estimate(c, w.split, 0, 1e-12)
+    assert e.value.status == tn.TN_ERR_UNSUPPORTED and "slices" in str(e.value)
