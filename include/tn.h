@@ -162,6 +162,48 @@ tn_status tn_build(const tn_graph *g, const tn_gate *gates, int64_t n_gates,
 tn_status tn_evolve_two_sided(tn_circuit *c, int32_t split_cycle, int32_t chi_max,
                               double cutoff_rel, void *cuda_stream);
 
+/* Bond compression of both halves (the SVD step after every two-qubit gate).
+ *   TN_COMPRESS_ONE_SIDED (default): Eqs. svd/svd2 as the paper states them. The endpoint
+ *     with fewer rows 2*prod(other legs) (ties: q[0]) is decomposed, A^sv <- U, and S V^H is
+ *     absorbed into the other endpoint; the kept singular values are those of A^sv alone.
+ *   TN_COMPRESS_TWO_SIDED: a variant the paper does not use. The kept singular values are
+ *     those of the local product A^sv A^other^T, which is what a thin QR of both endpoints
+ *     followed by an SVD of R_sv R_other^T yields. A truncated bond is then the best
+ *     approximation of that rank of the pair (Eckart-Young), and its rank is that of the
+ *     product. The device runs it as two entries of the same gate kernel per two-qubit gate.
+ *     The first applies the gate and decomposes the other endpoint exactly (cutoff 0, no chi
+ *     cap), so that endpoint becomes an isometry. The second is an identity gate that
+ *     decomposes A^sv with the keep rule. Same endpoint rule and the same structural bond
+ *     shapes as the one-sided form. Untruncated, both give the same amplitudes.
+ * Host only. Takes effect at the next tn_evolve_two_sided, which rebuilds the programs when
+ * the mode changed (plans made before are then invalid). Errors: TN_ERR_ARG. */
+typedef enum { TN_COMPRESS_ONE_SIDED = 0, TN_COMPRESS_TWO_SIDED = 1 } tn_compress;
+tn_status tn_set_compression(tn_circuit *c, int32_t mode);
+
+/* Host-only inspection of the gate program of one half (side 0 = ket, 1 = bra) that
+ * tn_evolve_two_sided(c, split_cycle, chi_max, cutoff_rel) builds with the circuit's
+ * compression mode, from the structural bond bounds (no rank probe, no device work), for CPU
+ * models of the evolution kernels. Call once with NULL entries/mats to get *n_entries, then
+ * with entries[n_entries * TN_PROG_ENTRY_LEN] and mats[n_entries * TN_PROG_MAT_LEN]. Entry i,
+ * in processing order, is
+ *   a two-qubit entry (op 2): op, k, l, edge, sv_is_k, din, chi_o, n = din*chi_o, dout, m_k,
+ *     m_l, pk, pl (positions of the edge among k's and l's legs), off_k, off_l, id; mats: P and
+ *     Q as 16 complex each (re, im; P[(s'*2 + s)*4 + a], s' the output and s the input value of
+ *     the physical index, a the term of Eq. gatesplit), then the cutoff. On the node tensors
+ *     [sigma, legs in increasing edge id] it forms X_k = P A^k and X_l = Q A^l, the shared leg
+ *     becoming (a_old, a) at index a_old*chi_o + a (Eqs. result1/result2). It takes the SVD of
+ *     the endpoint named by sv_is_k, matricised as (sigma, other legs) x (bond). It keeps
+ *     keep = min(#{s_j > cutoff * s_0}, dout) singular values, largest first, and zero-pads to
+ *     dout. Then A^sv <- U and A^other <- X_other (S V^H)^T (Eqs. svd/svd2).
+ *   a single-qubit entry (op 1, the tail of single-qubit gates with no later two-qubit gate):
+ *     op, q, -1, ..., off at [13]; mats: the 2x2 matrix as 4 complex, applied to sigma.
+ * The ket starts from |0...0>, the bra from the bitstring's basis state.
+ * Errors: TN_ERR_ARG. */
+#define TN_PROG_ENTRY_LEN 16
+#define TN_PROG_MAT_LEN 66
+tn_status tn_program_inspect(const tn_circuit *c, int32_t split_cycle, int32_t chi_max, double cutoff_rel,
+                             int32_t side, int64_t *entries, double *mats, int64_t *n_entries);
+
 /* Structural bond dimensions after evolution: side 0 = ket, 1 = bra;
  * out[n_edges]. Errors: TN_ERR_STATE before tn_evolve_two_sided. */
 tn_status tn_circuit_bond_dims(const tn_circuit *c, int32_t side, int32_t *out);

@@ -397,11 +397,13 @@ static M2 mul2(const M2 &a, const M2 &b) {
 // endpoint with fewer rows 2 * prod(other legs) (ties: q[0]) and the bond becomes
 // min(dim * chi_o, those rows, chi): the structural program, independent of the state. With
 // `force_sv` (the structural program's endpoints) and `caps` (probed ranks), the same endpoints
-// are kept and each bond is also capped by its probed rank.
+// are kept and each bond is also capped by its probed rank. With the two-sided compression every
+// two-qubit gate is two entries (see below); force_sv and caps are per entry.
 static void build_half(const tn_circuit *c, const std::vector<const tn_gate *> &seq, bool transpose, int chi,
                        double cutoff, Half &h, const std::vector<int> *caps = nullptr,
                        const std::vector<int> *force_sv = nullptr) {
   const int n = c->n;
+  const bool two_sided = c->compress == TN_COMPRESS_TWO_SIDED;
   h = Half();
   h.dims.assign(c->ne, 1);
   std::vector<M2> pend(n, M2{1, 0, 0, 1});
@@ -444,46 +446,73 @@ static void build_half(const tn_circuit *c, const std::vector<const tn_gate *> &
     cd P[16], Q[16];
     int chi_o = gate_split(F, P, Q);
     const int e = find_edge(c, k, l);
-    GateParams gp;
-    std::memset(&gp, 0, sizeof gp);
-    gp.nk = (int)c->legs[k].size();
-    gp.nl = (int)c->legs[l].size();
-    int64_t ok = 1, ol = 1;
-    for (int j = 0; j < gp.nk; ++j) {
-      int ej = c->legs[k][j];
-      gp.dk[j] = h.dims[ej];
-      if (ej == e) gp.pk = j; else ok *= h.dims[ej];
+    // One entry of the program: gate (Pm, Qm) with chi_o_ terms on (k, l) at the current bonds,
+    // SVD of endpoint k (sv_rule 1) or l (0) unless force_sv names it, bond bound dout (capped
+    // by chi unless `whole`, and by the probed rank), keep rule s_j > cut * s_0.
+    auto entry = [&](const cd *Pm, const cd *Qm, int chi_o_, int sv_rule, bool whole, double cut) {
+      GateParams gp;
+      std::memset(&gp, 0, sizeof gp);
+      gp.nk = (int)c->legs[k].size();
+      gp.nl = (int)c->legs[l].size();
+      int64_t ok = 1, ol = 1;
+      for (int j = 0; j < gp.nk; ++j) {
+        int ej = c->legs[k][j];
+        gp.dk[j] = h.dims[ej];
+        if (ej == e) gp.pk = j; else ok *= h.dims[ej];
+      }
+      for (int j = 0; j < gp.nl; ++j) {
+        int ej = c->legs[l][j];
+        gp.dl[j] = h.dims[ej];
+        if (ej == e) gp.pl = j; else ol *= h.dims[ej];
+      }
+      gp.din = h.dims[e];
+      gp.chi_o = chi_o_;
+      gp.n = gp.din * chi_o_;
+      gp.m_k = (int)(2 * ok);
+      gp.m_l = (int)(2 * ol);
+      const size_t gi = h.gp.size();
+      gp.sv_is_k = sv_rule;
+      if (force_sv && gi < force_sv->size()) gp.sv_is_k = (*force_sv)[gi];
+      int dout = std::min(gp.n, gp.sv_is_k ? gp.m_k : gp.m_l);
+      if (chi > 0 && !whole) dout = std::min(dout, chi);
+      if (caps && gi < caps->size() && (*caps)[gi] > 0) dout = std::min(dout, (*caps)[gi]);   // probed rank
+      gp.dout = dout;
+      gp.id = (int)gi;
+      gp.cutoff = cut;
+      for (int i = 0; i < 16; ++i) {
+        gp.P[i] = make_double2(Pm[i].real(), Pm[i].imag());
+        gp.Q[i] = make_double2(Qm[i].real(), Qm[i].imag());
+      }
+      h.dims[e] = dout;
+      cap[k] = std::max(cap[k], node_size(k));
+      cap[l] = std::max(cap[l], node_size(l));
+      h.gp.push_back(gp);
+      h.gate_nodes.push_back({k, l});
+      h.seq.push_back({2, (int)h.gp.size() - 1});
+      h.max_gate_mn = std::max<int64_t>(h.max_gate_mn, (int64_t)std::max(gp.m_k, gp.m_l) * gp.n);
+    };
+    // the endpoint with fewer rows 2 * prod(other legs) is compressed (ties: q[0]); the other
+    // legs' dims do not change within one gate
+    int64_t rows_k = 2, rows_l = 2;
+    for (int ej : c->legs[k]) if (ej != e) rows_k *= h.dims[ej];
+    for (int ej : c->legs[l]) if (ej != e) rows_l *= h.dims[ej];
+    const int sv = rows_k <= rows_l ? 1 : 0;
+    if (!two_sided) {
+      entry(P, Q, chi_o, sv, false, cutoff);
+      continue;
     }
-    for (int j = 0; j < gp.nl; ++j) {
-      int ej = c->legs[l][j];
-      gp.dl[j] = h.dims[ej];
-      if (ej == e) gp.pl = j; else ol *= h.dims[ej];
-    }
-    gp.din = h.dims[e];
-    gp.chi_o = chi_o;
-    gp.n = gp.din * chi_o;
-    gp.m_k = (int)(2 * ok);
-    gp.m_l = (int)(2 * ol);
+    // Two-sided: first the gate with the other endpoint decomposed whole (cutoff 0, no chi cap),
+    // which leaves that endpoint an isometry U_o and moves S_o V_o^H into A^sv; then an identity
+    // gate (one term) decomposing A^sv with the keep rule. A^sv A^o^T = A^sv' U_o^T with U_o's
+    // columns orthonormal, so the second SVD has the singular values of the local product.
     const size_t gi = h.gp.size();
-    gp.sv_is_k = gp.m_k <= gp.m_l ? 1 : 0;     // SVD the endpoint with fewer rows (ties: q[0])
-    if (force_sv && gi < force_sv->size()) gp.sv_is_k = (*force_sv)[gi];
-    int dout = std::min(gp.n, gp.sv_is_k ? gp.m_k : gp.m_l);
-    if (chi > 0) dout = std::min(dout, chi);
-    if (caps && gi < caps->size() && (*caps)[gi] > 0) dout = std::min(dout, (*caps)[gi]);   // probed rank
-    gp.dout = dout;
-    gp.id = (int)gi;
-    gp.cutoff = cutoff;
-    for (int i = 0; i < 16; ++i) {
-      gp.P[i] = make_double2(P[i].real(), P[i].imag());
-      gp.Q[i] = make_double2(Q[i].real(), Q[i].imag());
-    }
-    h.dims[e] = dout;
-    cap[k] = std::max(cap[k], node_size(k));
-    cap[l] = std::max(cap[l], node_size(l));
-    h.gp.push_back(gp);
-    h.gate_nodes.push_back({k, l});
-    h.seq.push_back({2, (int)h.gp.size() - 1});
-    h.max_gate_mn = std::max<int64_t>(h.max_gate_mn, (int64_t)std::max(gp.m_k, gp.m_l) * gp.n);
+    const int sv2 = (force_sv && gi + 1 < force_sv->size()) ? (*force_sv)[gi + 1] : sv;
+    entry(P, Q, chi_o, 1 - sv2, true, 0.0);
+    cd I[16];
+    for (int i = 0; i < 16; ++i) I[i] = 0;
+    I[(0 * 2 + 0) * 4 + 0] = 1;     // [s'][s][a]: delta(s', s), one term
+    I[(1 * 2 + 1) * 4 + 0] = 1;
+    entry(I, I, 1, sv2, false, cutoff);
   }
   for (int q = 0; q < n; ++q) {
     if (!has[q]) continue;
@@ -632,7 +661,8 @@ extern "C" tn_status tn_evolve_two_sided(tn_circuit *c, int32_t split_cycle, int
   if (s != TN_OK) return s;
   cudaStream_t st = (cudaStream_t)cuda_stream;
   // the same program again keeps plans valid (same static shapes); anything else rebuilds it
-  const bool same = c->evolved && c->split == split_cycle && c->chi == chi_max && c->cutoff == cutoff_rel;
+  const bool same = c->evolved && c->split == split_cycle && c->chi == chi_max && c->cutoff == cutoff_rel &&
+                    c->built_compress == c->compress;
   DevMem &mem = c->mem;
   if (!same) {
     std::vector<const tn_gate *> g1, g2;
@@ -643,6 +673,7 @@ extern "C" tn_status tn_evolve_two_sided(tn_circuit *c, int32_t split_cycle, int
     c->split = split_cycle;
     c->chi = chi_max;
     c->cutoff = cutoff_rel;
+    c->built_compress = c->compress;
     // Rank probe. The static bounds can exceed the true bond ranks. The ket is a single state:
     // its ranks are exact. For the bra, the ranks reached from one random (generic) product state
     // bound those reached from every basis state (a rank can only drop on special inputs), so
@@ -1854,6 +1885,7 @@ static tn_status host_programs(const tn_circuit *c, int32_t split_cycle, int32_t
   h.ev = c->ev;
   h.legs = c->legs;
   h.gates = c->gates;
+  h.compress = h.built_compress = c->compress;
   std::vector<const tn_gate *> g1, g2;
   for (const auto &g : h.gates) (g.cycle <= split_cycle ? g1 : g2).push_back(&g);
   std::reverse(g2.begin(), g2.end());
@@ -1939,6 +1971,65 @@ extern "C" tn_status tn_plan_inspect(const tn_circuit *c, int32_t split_cycle, i
   return no_throw("tn_plan_inspect", [&] {
     return plan_inspect_impl(c, split_cycle, chi_max, cutoff_rel, opts, layout, steps, tables, n_steps, n_tables);
   });
+}
+
+static_assert(TN_PROG_ENTRY_LEN == 16 && TN_PROG_MAT_LEN == 66, "gate program inspection layout");
+
+static tn_status program_inspect_impl(const tn_circuit *c, int32_t split_cycle, int32_t chi_max, double cutoff_rel,
+                                      int32_t side, int64_t *entries, double *mats, int64_t *n_entries) {
+  tn_circuit h;
+  tn_status s = host_programs(c, split_cycle, chi_max, cutoff_rel, h);
+  if (s != TN_OK) return s;
+  const Half &hf = side ? h.bra : h.ket;
+  *n_entries = (int64_t)hf.seq.size();
+  if (!entries || !mats) return TN_OK;
+  for (size_t j = 0; j < hf.seq.size(); ++j) {
+    int64_t *e = entries + j * TN_PROG_ENTRY_LEN;
+    double *m = mats + j * TN_PROG_MAT_LEN;
+    for (int i = 0; i < TN_PROG_ENTRY_LEN; ++i) e[i] = -1;
+    for (int i = 0; i < TN_PROG_MAT_LEN; ++i) m[i] = 0;
+    const int op = hf.seq[j].first, idx = hf.seq[j].second;
+    e[0] = op;
+    if (op == 2) {
+      const GateParams &g = hf.gp[idx];
+      const int k = hf.gate_nodes[idx].first, l = hf.gate_nodes[idx].second;
+      const int64_t v[16] = {2, k, l, h.legs[k][g.pk], g.sv_is_k, g.din, g.chi_o, g.n, g.dout, g.m_k, g.m_l,
+                             g.pk, g.pl, g.off_k, g.off_l, g.id};
+      for (int i = 0; i < 16; ++i) e[i] = v[i];
+      for (int i = 0; i < 16; ++i) {
+        m[2 * i] = g.P[i].x;
+        m[2 * i + 1] = g.P[i].y;
+        m[32 + 2 * i] = g.Q[i].x;
+        m[32 + 2 * i + 1] = g.Q[i].y;
+      }
+      m[64] = g.cutoff;
+    } else {
+      const Apply1Params &a = hf.ap[idx];
+      e[1] = hf.ap_node[idx];
+      e[13] = a.off;
+      for (int i = 0; i < 4; ++i) {
+        m[2 * i] = a.u[i].x;
+        m[2 * i + 1] = a.u[i].y;
+      }
+    }
+  }
+  return TN_OK;
+}
+
+extern "C" tn_status tn_program_inspect(const tn_circuit *c, int32_t split_cycle, int32_t chi_max, double cutoff_rel,
+                                        int32_t side, int64_t *entries, double *mats, int64_t *n_entries) {
+  if (!c || !n_entries || (side != 0 && side != 1)) return tn_fail(TN_ERR_ARG, "tn_program_inspect: bad argument");
+  return no_throw("tn_program_inspect", [&] {
+    return program_inspect_impl(c, split_cycle, chi_max, cutoff_rel, side, entries, mats, n_entries);
+  });
+}
+
+extern "C" tn_status tn_set_compression(tn_circuit *c, int32_t mode) {
+  if (!c) return tn_fail(TN_ERR_ARG, "tn_set_compression: NULL circuit");
+  if (mode != TN_COMPRESS_ONE_SIDED && mode != TN_COMPRESS_TWO_SIDED)
+    return tn_fail(TN_ERR_ARG, "tn_set_compression: unknown mode %d", (int)mode);
+  c->compress = mode;
+  return TN_OK;
 }
 
 extern "C" tn_status tn_plan_details(const tn_plan *p, int32_t *order, int32_t *cuts, int64_t *steps) {

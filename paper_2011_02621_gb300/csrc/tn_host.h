@@ -56,6 +56,8 @@ struct tn_circuit {
   int64_t generation = 0;
   int split = 0, chi = 0;
   double cutoff = 1e-12;
+  int compress = 0;                               // bond compression for the next programs (tn_compress)
+  int built_compress = 0;                         // the compression of the current programs
   int device = 0;
   Half ket, bra;
   Buf ket_dev, ket_c64, ket_off_dev, bra_off_dev, err_dev, ket_work;

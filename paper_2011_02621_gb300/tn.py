@@ -88,6 +88,8 @@ def _load():
         "tn_build": (i32, [C.POINTER(tn_graph), C.POINTER(tn_gate), i64, C.POINTER(tn_allocator), C.POINTER(vp)]),
         "tn_evolve_two_sided": (i32, [vp, i32, i32, dbl, vp]),
         "tn_circuit_bond_dims": (i32, [vp, i32, C.POINTER(i32)]),
+        "tn_set_compression": (i32, [vp, i32]),
+        "tn_program_inspect": (i32, [vp, i32, i32, dbl, i32, C.POINTER(i64), C.POINTER(dbl), C.POINTER(i64)]),
         "tn_path": (i32, [vp, C.POINTER(tn_path_opts), C.POINTER(vp), C.POINTER(tn_plan_info)]),
         "tn_plan_details": (i32, [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i64)]),
         "tn_plan_estimate": (i32, [vp, i32, i32, dbl, C.POINTER(tn_path_opts), C.POINTER(tn_plan_info)]),
@@ -268,7 +270,22 @@ def tn_build(n_qubits: int, edges, gates, allocator="torch") -> Circuit:
     return Circuit(out, int(n_qubits), int(e.shape[0]), (alloc,))
 
 
-def tn_evolve_two_sided(c: Circuit, split_cycle: int, chi_max: int = 0, cutoff_rel: float = 1e-12, stream=None):
+COMPRESSIONS = {"one_sided": 0, "two_sided": 1}
+
+
+def tn_set_compression(c: Circuit, mode: str = "one_sided"):
+    """Bond compression of both halves for the next tn_evolve_two_sided: "one_sided" (Eqs. svd/
+    svd2) or "two_sided" (the singular values of the local product of the two endpoints)."""
+    if mode not in COMPRESSIONS:
+        raise ValueError(f"unknown compression {mode!r}")
+    _check(LIB.tn_set_compression(c.ptr, COMPRESSIONS[mode]))
+
+
+def tn_evolve_two_sided(c: Circuit, split_cycle: int, chi_max: int = 0, cutoff_rel: float = 1e-12, stream=None,
+                        compress=None):
+    """compress: None keeps the circuit's mode (tn_set_compression), else sets it first."""
+    if compress is not None:
+        tn_set_compression(c, compress)
     _check(LIB.tn_evolve_two_sided(c.ptr, int(split_cycle), int(chi_max), float(cutoff_rel), _stream_handle(stream)))
 
 
@@ -353,6 +370,38 @@ def tn_plan_inspect(c: Circuit, split_cycle: int, chi: int = 0, cutoff: float = 
         d["rest_ostride"] = [int(x) for x in row[17 + 32:17 + 32 + d["n_rest"]]]
         steps.append(d)
     return layout, steps, tab[: nt.value].copy()
+
+
+PROG_ENTRY_LEN = 16
+PROG_MAT_LEN = 66
+PROG_FIELDS = ("op", "k", "l", "edge", "sv_is_k", "din", "chi_o", "n", "dout", "m_k", "m_l", "pk", "pl", "off_k",
+               "off_l", "id")
+
+
+def tn_program_inspect(c: Circuit, split_cycle: int, chi: int = 0, cutoff: float = 1e-12, side: int = 0):
+    """The gate program of one half (0 ket, 1 bra) tn_evolve_two_sided builds with the circuit's
+    compression mode, from the structural bond bounds, on the host: a list of dicts, one per
+    entry in processing order (fields PROG_FIELDS; two-qubit entries carry P and Q as [s'][s][a]
+    complex arrays and the cutoff, single-qubit entries (op 1, node k) the 2x2 matrix u)."""
+    n = C.c_int64()
+    _check(LIB.tn_program_inspect(c.ptr, int(split_cycle), int(chi), float(cutoff), int(side), None, None,
+                                  C.byref(n)))
+    e = np.zeros((max(n.value, 1), PROG_ENTRY_LEN), dtype=np.int64)
+    m = np.zeros((max(n.value, 1), PROG_MAT_LEN), dtype=np.float64)
+    _check(LIB.tn_program_inspect(c.ptr, int(split_cycle), int(chi), float(cutoff), int(side),
+                                  e.ctypes.data_as(C.POINTER(C.c_int64)), m.ctypes.data_as(C.POINTER(C.c_double)),
+                                  C.byref(n)))
+    out = []
+    for row, mat in zip(e[: n.value], m[: n.value]):
+        d = {f: int(v) for f, v in zip(PROG_FIELDS, row)}
+        if d["op"] == 2:
+            d["P"] = (mat[0:32:2] + 1j * mat[1:32:2]).reshape(2, 2, 4)
+            d["Q"] = (mat[32:64:2] + 1j * mat[33:64:2]).reshape(2, 2, 4)
+            d["cutoff"] = float(mat[64])
+        else:
+            d["u"] = (mat[0:8:2] + 1j * mat[1:8:2]).reshape(2, 2)
+        out.append(d)
+    return out
 
 
 def tn_plan_details(p: Plan):
