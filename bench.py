@@ -61,13 +61,14 @@ def _oracle_worker(payload):
     import numpy as np  # noqa: F401
     import gen
     from oracle import tns
-    name, idx, n_bits, seed_off = payload
+    name, idx, n_bits, seed_off, compress = payload
     w = gen.workload(name, n_bits=n_bits)
     bits = _rank_bits(w, seed_off)[list(idx)]
     g1, g2 = tns.split_gates(w.gates, w.split)
-    ket = tns.evolve_ket(w.graph.n, w.graph.edges, g1, w.chi, w.cutoff)
+    ket = tns.evolve_ket(w.graph.n, w.graph.edges, g1, w.chi, w.cutoff, compress)
     t0 = time.perf_counter()
-    a, _ = tns.amplitudes(w.graph.n, w.graph.edges, w.gates, bits, w.split, w.chi, w.cutoff, ket=ket)
+    a, _ = tns.amplitudes(w.graph.n, w.graph.edges, w.gates, bits, w.split, w.chi, w.cutoff, ket=ket,
+                          compress=compress)
     return list(idx), [complex(x) for x in a], time.perf_counter() - t0
 
 
@@ -78,18 +79,20 @@ def _rank_bits(w, seed_off):
     return gen.bitstrings(w.graph.n, len(w.bits), gen.rng(gen.BASE_SEED + 3 + 7919 * seed_off, 2))
 
 
-def cpu_oracle(name, n_bits, sample, seed_off=0, cores=None):
-    """Time the oracle (as it stands) on `sample` bitstrings over a spawned process pool."""
+def cpu_oracle(name, n_bits, sample, seed_off=0, cores=None, compress="one_sided"):
+    """Time the oracle (as it stands) on `sample` bitstrings over a spawned process pool
+    (compress: the bond compression of both halves, as in the oracle)."""
     import multiprocessing as mp
     import numpy as np
     cores = cores or os.cpu_count() or 1
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         os.environ[k] = "1"
     per = max(1, math.ceil(sample / cores))
-    chunks = [(name, tuple(range(i, min(i + per, sample))), n_bits, seed_off) for i in range(0, sample, per)]
+    chunks = [(name, tuple(range(i, min(i + per, sample))), n_bits, seed_off, compress)
+              for i in range(0, sample, per)]
     ctx = mp.get_context("spawn")
     with ctx.Pool(min(cores, len(chunks))) as pool:
-        pool.map(_oracle_worker, [(name, (0,), n_bits, seed_off)] * min(cores, len(chunks)))   # warm imports
+        pool.map(_oracle_worker, [(name, (0,), n_bits, seed_off, compress)] * min(cores, len(chunks)))   # warm imports
         t0 = time.perf_counter()
         res = pool.map(_oracle_worker, chunks)
         wall = time.perf_counter() - t0
@@ -464,6 +467,81 @@ def double_layer_run(tn, np, torch, c, w, packed, a64, steps, warmup, flush, mem
     return res
 
 
+def two_sided_run(tn, np, torch, w, packed, a64, prec, steps, warmup, flush, mem_gib, pk):
+    """The two-sided bond compression (the singular values of the local product of a gate's two
+    endpoints, a variant of Eqs. svd/svd2 the paper does not use) on the device:
+    (1) the same workload with both halves compressed two-sided: FP64 on the first len(a64)
+        bitstrings against the one-sided FP64 amplitudes a64, then the `prec` form timed like the
+        main step and checked against its own FP64 amplitudes;
+    (2) a capped case where the forms differ: a 3x4 grid, 8 cycles of Haar-random two-qubit
+        gates, every gate in the ket (split 8), bonds capped at chi = 4. All 4096 amplitudes of
+        each form against the untruncated FP64 amplitudes (exact), as the fidelity
+        |<exact|approx>|^2 / <approx|approx> and the largest error relative to rms |exact|.
+    Returns the section and the two-sided FP64 amplitudes of (1)."""
+    import gen
+    stream = torch.cuda.current_stream()
+    B = len(packed)
+    nchk = len(a64)
+    c2 = tn.tn_build(w.graph.n, w.graph.edges, w.gates)
+    tn.tn_evolve_two_sided(c2, w.split, w.chi, w.cutoff, stream, compress="two_sided")
+    p2 = tn.tn_path(c2, mem_budget_bytes=mem_gib * 2 ** 30)
+    rms = float(np.sqrt(np.mean(np.abs(a64) ** 2)))
+    d64 = tn.tn_amplitudes(p2, packed[:nchk], "fp64")
+    res = {"compression": "two-sided: two gate-kernel entries per gate (the other endpoint decomposed "
+                          "whole, then the kept endpoint under the keep rule)",
+           "plan": {k: p2.info[k] for k in ("n_steps", "cmacs", "max_intermediate", "chunk_bitstrings")},
+           "fp64_vs_one_sided_fp64": {"checked": nchk, "max_rel_err": float(np.max(np.abs(d64 - a64)) / rms)}}
+    tuned = tn.tn_autotune(p2, prec, B, stream=stream)
+    bits_dev = torch.from_numpy(packed.view(np.int64).copy()).cuda()
+    out = torch.empty(B, dtype=torch.complex128, device="cuda")
+
+    def step():
+        tn.tn_evolve_two_sided(c2, w.split, w.chi, w.cutoff, stream)
+        tn.tn_amplitudes(p2, bits_dev, prec, out=out, stream=stream)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    tn.tn_profile_enable(True)
+    total = 0.0
+    for _ in range(steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        total += e0.elapsed_time(e1) / 1000.0
+    prof = tn.tn_profile_read()
+    tn.tn_profile_enable(False)
+    rel = np.abs(out[:nchk].cpu().numpy() - d64) / float(np.sqrt(np.mean(np.abs(d64) ** 2)))
+    ok = float(np.mean(rel <= TOL))
+    res[prec] = {"value": B * steps / total * ok, "unit": UNIT, "ms_per_step": 1000 * total / steps,
+                 "accuracy": {"checked": nchk, "within_1e-5": ok, "max_rel_err_vs_fp64": float(rel.max())},
+                 "kernels": kernel_table(prof, steps),
+                 "step_kernels": {k: tuned.count(k) for k in sorted(set(tuned))}}
+    del p2
+    # (2) a capped case: exact amplitudes from the untruncated FP64 path on the same device
+    g = gen.grid(3, 4)
+    gates = gen.rqc(g, 8, gen.rng(43, 1), twoq="haar", oneq="haar")
+    allbits = gen.all_bitstrings(12)
+    amps = {}
+    for label, chi, comp in (("exact", 0, "one_sided"), ("one_sided", 4, "one_sided"), ("two_sided", 4, "two_sided")):
+        cc = tn.tn_build(12, g.edges, gates)
+        tn.tn_evolve_two_sided(cc, 8, chi, 1e-12, stream, compress=comp)
+        amps[label] = tn.tn_amplitudes(tn.tn_path(cc), allbits, "fp64")
+    ex = amps["exact"]
+    capped = {"workload": "3x4 grid, 8 cycles of Haar-random two-qubit gates and Haar SU(2), split 8, chi 4, "
+                          "all 4096 bitstrings", "norm_exact": float(np.sum(np.abs(ex) ** 2))}
+    for label in ("one_sided", "two_sided"):
+        a = amps[label]
+        capped[label] = {"fidelity": float(abs(np.vdot(ex, a)) ** 2 / (np.vdot(a, a).real * np.vdot(ex, ex).real)),
+                         "max_rel_err_vs_exact": float(np.max(np.abs(a - ex)) / np.sqrt(np.mean(np.abs(ex) ** 2)))}
+    res["capped_3x4_haar_chi4"] = capped
+    return res, d64
+
+
 def kernel_table(prof, steps):
     return {k: {"ms_per_step": v["ms"] / steps, "launches_per_step": v["launches"] / steps,
                 "GB/s": v["bytes"] / max(v["ms"], 1e-9) / 1e6, "TFLOP/s": v["flops"] / max(v["ms"], 1e-9) / 1e9}
@@ -489,6 +567,7 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="keep the shape heuristic's step kernels")
     ap.add_argument("--mem-gib", type=float, default=32.0, help="device memory budget of the plan's batches")
     ap.add_argument("--no-batch", action="store_true", help="skip the 32-circuit batched-graph measurement")
+    ap.add_argument("--no-two-sided", action="store_true", help="skip the two-sided compression section")
     ap.add_argument("--no-double-layer", action="store_true",
                     help="skip the double-layer network section (ket and bra tensors as separate nodes)")
     args = ap.parse_args()
@@ -651,6 +730,13 @@ def main():
                                                     flush, args.mem_gib, pk)
         except Exception as e:  # noqa: BLE001  (recorded in the line, never ends the run)
             line["double_layer"] = {"error": f"{type(e).__name__}: {e}"}
+    d64_two = None
+    if not args.no_two_sided and world == 1:
+        try:
+            line["two_sided"], d64_two = two_sided_run(tn, np, torch, w, packed, a64, args.prec, args.steps,
+                                                       args.warmup, flush, args.mem_gib, pk)
+        except Exception as e:  # noqa: BLE001  (recorded in the line, never ends the run)
+            line["two_sided"] = {"error": f"{type(e).__name__}: {e}"}
     if not args.no_cpu and world == 1:
         cs = min(args.cpu_sample, B)
         r = cpu_oracle("syc53", args.bits, cs)
@@ -659,6 +745,13 @@ def main():
                                 "sample": f"first {cs} of the 65536 bitstrings (ket evolution outside the timing)",
                                 "single_thread_value": r["single_thread_value"], "wall_s": r["wall_s"]}
         line["oracle_check"] = {"bitstrings": cs, "max_rel_err": float(err.max())}
+        if d64_two is not None:
+            # the device's two-sided FP64 amplitudes against the oracle's two-sided compression
+            ct = min(cs, len(d64_two))
+            r2 = cpu_oracle("syc53", args.bits, ct, compress="two_sided")
+            err2 = np.abs(d64_two[:ct] - r2["amps"]) / float(np.sqrt(np.mean(np.abs(r2["amps"]) ** 2)))
+            line["oracle_check_two_sided"] = {"bitstrings": ct, "precision": "fp64", "max_rel_err": float(err2.max()),
+                                              "oracle_value": r2["value"]}
     print(json.dumps(line))
     return 0
 
