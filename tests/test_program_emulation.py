@@ -206,3 +206,31 @@ def test_unknown_compression_mode_is_refused(tn):
     with pytest.raises(ValueError):
         tn.tn_set_compression(c, "three_sided")
     assert tn.LIB.tn_set_compression(c.ptr, 2) == tn.TN_ERR_ARG
+
+
+@pytest.mark.parametrize("compress", ["one_sided", "two_sided"])
+@pytest.mark.parametrize("layers", [1, 2])
+@pytest.mark.parametrize("chi,split", [(0, 4), (4, 8), (4, 0)])
+def test_programs_feed_the_compiled_plan(tn, compress, layers, chi, split):
+    """The two host-side models chained: the node tensors the gate programs leave (at exactly the
+    plan's structural bonds, in the halves' slots) contracted by the compiled plan's steps give
+    the oracle's amplitude for the same compression (the state vector's when nothing is cut)."""
+    from tests.test_plan_emulation import _execute, _place
+    w = _haar_grid_case(44, n_bits=3)
+    c = tn.tn_build(12, w.graph.edges, w.gates)
+    tn.tn_set_compression(c, compress)
+    layout, steps, tab = tn.tn_plan_inspect(c, split, chi, 1e-12, layers=layers, merge=False)
+    ket = _run(tn.tn_program_inspect(c, split, chi, 1e-12, 0), 12, w.graph.edges)
+    assert ket.bonds() == list(layout["ket_dims"])
+    kbuf = _place(ket, layout["ket_dims"], layout["ket_off"], layout["ket_half_elems"])
+    ref, _ = otns.amplitudes(12, w.graph.edges, w.gates, w.bits, split, chi, 1e-12, compress=compress)
+    if chi == 0:
+        assert _rel(ref, sv.amplitudes(sv.run(12, w.gates), w.bits)) < 1e-12
+    bra_prog = tn.tn_program_inspect(c, split, chi, 1e-12, 1)
+    got = []
+    for b in w.bits:
+        bra = _run(bra_prog, 12, w.graph.edges, b)
+        assert bra.bonds() == list(layout["bra_dims"])
+        got.append(_execute(layout, steps, tab, kbuf, _place(bra, layout["bra_dims"], layout["bra_off"],
+                                                             layout["bra_half_elems"])))
+    assert _rel(np.array(got), ref) < 1e-10
