@@ -224,8 +224,8 @@ tn_status tn_circuit_bond_dims(const tn_circuit *c, int32_t side, int32_t *out);
  * physical index). The sums are those of Eq. overlap without forming the per-qubit overlap
  * tensors first, so the amplitudes are the same; each step absorbs one ket tensor (the same for
  * every bitstring) or one bra tensor. No merging; explicit cut_edges are not accepted
- * (TN_ERR_UNSUPPORTED); automatic cuts are. The path search holds at most 128 nodes, so the
- * double-layer network takes circuits of at most 64 qubits (TN_ERR_UNSUPPORTED above).
+ * (TN_ERR_UNSUPPORTED); automatic cuts are. The path search holds at most 256 nodes, so the
+ * double-layer network takes every circuit tn_build accepts (at most 128 qubits).
  * Errors: TN_ERR_STATE, TN_ERR_NO_PATH, TN_ERR_ARG, TN_ERR_CUDA, TN_ERR_OOM, TN_ERR_UNSUPPORTED. */
 tn_status tn_path(tn_circuit *c, const tn_path_opts *opts, tn_plan **out, tn_plan_info *info);
 
@@ -402,8 +402,9 @@ tn_status tn_gate_split(const tn_c128 *m, tn_c128 *P, tn_c128 *Q, int32_t *chi_o
 
 /* Algorithm 1 on an arbitrary graph with per-edge dimensions `dims`
  * (n_edges entries, >= 1). order[n_qubits] receives the path, *score its
- * score (Cost = product of the dims of all legs of both tensors).
- * Errors: TN_ERR_ARG, TN_ERR_GRAPH, TN_ERR_NO_PATH. */
+ * score (Cost = product of the dims of all legs of both tensors). Graphs of
+ * up to 256 nodes (tn_cut_search likewise; circuits hold at most 128 qubits).
+ * Errors: TN_ERR_ARG, TN_ERR_GRAPH, TN_ERR_NO_PATH, TN_ERR_UNSUPPORTED. */
 tn_status tn_path_search(const tn_graph *g, const double *dims, const tn_path_opts *opts,
                          int32_t *order, double *score, int64_t *states_expanded);
 

@@ -15,6 +15,7 @@
 #include <mutex>
 #include <queue>
 #include <string>
+#include <type_traits>
 #include <unordered_set>
 #include <vector>
 
@@ -296,12 +297,14 @@ extern "C" tn_status tn_gate_split(const tn_c128 *m, tn_c128 *P, tn_c128 *Q, int
 // ---------------------------------------------------------------------------
 // graph checks
 // ---------------------------------------------------------------------------
+// max_nodes: 128 for qubit graphs of circuits, 256 for the graphs of the host-only path and cut
+// searches (Algorithm 1's subset masks hold up to 256 nodes)
 static tn_status check_graph(const tn_graph *g, std::vector<int> &eu, std::vector<int> &ev,
-                             std::vector<std::vector<int>> &legs) {
+                             std::vector<std::vector<int>> &legs, int max_nodes = 128) {
   if (!g || g->n_qubits <= 0 || g->n_edges < 0 || (g->n_edges > 0 && !g->edges))
     return tn_fail(TN_ERR_ARG, "graph: bad sizes or NULL edges");
   const int n = g->n_qubits, ne = g->n_edges;
-  if (n > 128) return tn_fail(TN_ERR_UNSUPPORTED, "graph: at most 128 qubits are supported (got %d)", n);
+  if (n > max_nodes) return tn_fail(TN_ERR_UNSUPPORTED, "graph: at most %d nodes are supported (got %d)", max_nodes, n);
   eu.resize(ne);
   ev.resize(ne);
   legs.assign(n, {});
@@ -760,27 +763,43 @@ extern "C" void tn_circuit_free(tn_circuit *c) {
 // Algorithm 1 (supplement): best-first search over qubit subsets
 // ---------------------------------------------------------------------------
 namespace {
-struct Mask {
-  uint64_t w[2] = {0, 0};
+// Node subsets of Algorithm 1 as bit masks of W words: W = 2 for networks of up to 128 nodes,
+// W = 4 (with 16-bit node indices in the states) for up to 256, e.g. the double-layer network of
+// a 104-qubit circuit. The search itself does not depend on W.
+template <int W> struct MaskT {
+  uint64_t w[W] = {};
   bool get(int i) const { return (w[i >> 6] >> (i & 63)) & 1; }
   void set(int i) { w[i >> 6] |= 1ull << (i & 63); }
-  bool operator==(const Mask &o) const { return w[0] == o.w[0] && w[1] == o.w[1]; }
-  bool any_and(const Mask &o) const { return (w[0] & o.w[0]) || (w[1] & o.w[1]); }
+  void clear(int i) { w[i >> 6] &= ~(1ull << (i & 63)); }
+  bool operator==(const MaskT &o) const {
+    for (int j = 0; j < W; ++j)
+      if (w[j] != o.w[j]) return false;
+    return true;
+  }
+  bool any_and(const MaskT &o) const {
+    for (int j = 0; j < W; ++j)
+      if (w[j] & o.w[j]) return true;
+    return false;
+  }
 };
-struct MaskHash {
-  size_t operator()(const Mask &m) const {
+template <int W> struct MaskHashT {
+  size_t operator()(const MaskT<W> &m) const {
     uint64_t h = m.w[0] * 0x9E3779B97F4A7C15ull ^ (m.w[1] + 0x632BE59BD9B4E019ull + (m.w[0] << 6));
+    for (int j = 2; j < W; ++j) h = (h ^ m.w[j]) * 0x9E3779B97F4A7C15ull + (h >> 17);
     h ^= h >> 31;
     h *= 0xBF58476D1CE4E5B9ull;
     return (size_t)(h ^ (h >> 29));
   }
 };
-struct PEntry {
-  Mask mask;
+template <int W> struct PEntryT {
+  using Node = typename std::conditional<W == 2, uint8_t, uint16_t>::type;    // node index / count
+  using Iso = typename std::conditional<W == 2, int8_t, int16_t>::type;       // isolated node, -1: none
+  MaskT<W> mask;
   double score, prod_open;
   int32_t parent;
-  uint8_t last, m, rank;
-  int8_t c;
+  Node last, m;
+  uint8_t rank;
+  Iso c;
 };
 struct HeapKey {
   double score;
@@ -799,28 +818,32 @@ struct PathGraph {
   int n;
   std::vector<std::vector<std::pair<int, int>>> adj;   // (neighbour, edge)
   std::vector<double> dims;
-  std::vector<Mask> nb;                                 // neighbour masks
 };
 
 static PathGraph make_pg(int n, const std::vector<int> &eu, const std::vector<int> &ev, const std::vector<double> &dims) {
   PathGraph pg;
   pg.n = n;
   pg.adj.assign(n, {});
-  pg.nb.assign(n, Mask());
   pg.dims = dims;
   for (size_t e = 0; e < eu.size(); ++e) {
     pg.adj[eu[e]].push_back({ev[e], (int)e});
     pg.adj[ev[e]].push_back({eu[e], (int)e});
-    pg.nb[eu[e]].set(ev[e]);
-    pg.nb[ev[e]].set(eu[e]);
   }
   return pg;
 }
 
-static tn_status alg1(const PathGraph &pg, int max_rank, bool boundary_only, bool connected, int64_t max_states,
-                      std::vector<int> &order, double &score, int64_t &pops, double byte_weight = 0) {
+template <int W>
+static tn_status alg1_masks(const PathGraph &pg, int max_rank, bool boundary_only, bool connected,
+                            int64_t max_states, std::vector<int> &order, double &score, int64_t &pops,
+                            double byte_weight) {
+  using Mask = MaskT<W>;
+  using PEntry = PEntryT<W>;
+  using Node = typename PEntry::Node;
+  using Iso = typename PEntry::Iso;
   const int n = pg.n;
-  if (n > 128) return tn_fail(TN_ERR_UNSUPPORTED, "Algorithm 1: at most 128 network nodes (got %d)", n);
+  std::vector<Mask> nb(n);                             // neighbour masks
+  for (int q = 0; q < n; ++q)
+    for (auto &pr : pg.adj[q]) nb[q].set(pr.first);
   std::vector<PEntry> arena;
   arena.reserve(1 << 16);
   std::priority_queue<HeapKey> pq;
@@ -842,14 +865,14 @@ static tn_status alg1(const PathGraph &pg, int max_rank, bool boundary_only, boo
     for (auto &pr : pg.adj[q]) { po *= pg.dims[pr.second]; rk += pg.dims[pr.second] > 1 ? 1 : 0; }
     e.prod_open = po;
     e.parent = -1;
-    e.last = (uint8_t)q;
+    e.last = (Node)q;
     e.m = 1;
     e.rank = (uint8_t)rk;
     e.c = -1;
     arena.push_back(e);
     pq.push({0.0, 1, seq++, (int32_t)arena.size() - 1});
   }
-  std::unordered_set<Mask, MaskHash> seen;
+  std::unordered_set<Mask, MaskHashT<W>> seen;
   pops = 0;
   while (!pq.empty()) {
     HeapKey hk = pq.top();
@@ -867,20 +890,20 @@ static tn_status alg1(const PathGraph &pg, int max_rank, bool boundary_only, boo
     }
     // members other than the isolated qubit
     Mask main = cur.mask;
-    if (cur.c >= 0) main.w[cur.c >> 6] &= ~(1ull << (cur.c & 63));
+    if (cur.c >= 0) main.clear(cur.c);
     for (int i = 0; i < n; ++i) {
       if (cur.mask.get(i)) continue;
-      const bool adj_s = pg.nb[i].any_and(cur.mask);
-      int8_t c_new = -1;
+      const bool adj_s = nb[i].any_and(cur.mask);
+      Iso c_new = -1;
       if (connected) {
         if (cur.c >= 0) {
-          if (!pg.nb[i].get(cur.c) || !pg.nb[i].any_and(main)) continue;   // must reconnect the isolated qubit
+          if (!nb[i].get(cur.c) || !nb[i].any_and(main)) continue;   // must reconnect the isolated qubit
         } else if (!adj_s) {
           bool dist2 = false;            // an isolated qubit must be reconnectable by the next step
           for (auto &pr : pg.adj[i])
-            if (pg.nb[pr.first].any_and(cur.mask)) { dist2 = true; break; }
+            if (nb[pr.first].any_and(cur.mask)) { dist2 = true; break; }
           if (!dist2) continue;
-          c_new = (int8_t)i;
+          c_new = (Iso)i;
         }
       }
       double shared = 1, fresh = 1;
@@ -898,17 +921,26 @@ static tn_status alg1(const PathGraph &pg, int max_rank, bool boundary_only, boo
       // Cost = prod of dims over legs of C^S and C^i (+ byte_weight x the step's input and output)
       e.score = cur.score + cur.prod_open * fresh + (byte_weight > 0 ? byte_weight * (cur.prod_open + e.prod_open) : 0.0);
       e.parent = hk.idx;
-      e.last = (uint8_t)i;
-      e.m = (uint8_t)(cur.m + 1);
+      e.last = (Node)i;
+      e.m = (Node)(cur.m + 1);
       e.rank = (uint8_t)std::max(rk, 0);
       e.c = c_new;
       if ((int64_t)arena.size() >= arena_cap)
         return tn_fail(TN_ERR_NO_PATH, "Algorithm 1: state arena exceeded %lld entries", (long long)arena_cap);
       arena.push_back(e);
-      pq.push({e.score, e.m, seq++, (int32_t)arena.size() - 1});
+      pq.push({e.score, (int)e.m, seq++, (int32_t)arena.size() - 1});
     }
   }
   return tn_fail(TN_ERR_NO_PATH, "Algorithm 1: no path satisfies the assumptions (max_rank %d)", max_rank);
+}
+
+static tn_status alg1(const PathGraph &pg, int max_rank, bool boundary_only, bool connected, int64_t max_states,
+                      std::vector<int> &order, double &score, int64_t &pops, double byte_weight = 0) {
+  if (pg.n <= 128)
+    return alg1_masks<2>(pg, max_rank, boundary_only, connected, max_states, order, score, pops, byte_weight);
+  if (pg.n <= 256)
+    return alg1_masks<4>(pg, max_rank, boundary_only, connected, max_states, order, score, pops, byte_weight);
+  return tn_fail(TN_ERR_UNSUPPORTED, "Algorithm 1: at most 256 network nodes (got %d)", pg.n);
 }
 
 static tn_status path_auto(const PathGraph &pg, const tn_path_opts &o, std::vector<int> &order, double &score,
@@ -959,7 +991,7 @@ static tn_status tn_path_search_impl(const tn_graph *g, const double *dims, cons
   if (!g || !dims || !order) return tn_fail(TN_ERR_ARG, "tn_path_search: NULL argument");
   std::vector<int> eu, ev;
   std::vector<std::vector<int>> legs;
-  tn_status s = check_graph(g, eu, ev, legs);
+  tn_status s = check_graph(g, eu, ev, legs, 256);
   if (s != TN_OK) return s;
   std::vector<double> d(dims, dims + g->n_edges);
   for (double x : d)
@@ -1073,7 +1105,7 @@ static tn_status tn_cut_search_impl(const tn_graph *g, const double *dims, const
                                    int32_t *cuts, int32_t *n_cuts, double *total_cmacs) {
   if (!g || !dims || !order || !n_cuts) return tn_fail(TN_ERR_ARG, "tn_cut_search: NULL argument");
   Net tmp;
-  tn_status s = check_graph(g, tmp.eu, tmp.ev, tmp.legs);
+  tn_status s = check_graph(g, tmp.eu, tmp.ev, tmp.legs, 256);
   if (s != TN_OK) return s;
   tmp.n = g->n_qubits;
   tmp.ne = g->n_edges;
@@ -1769,8 +1801,8 @@ static tn_status plan_host(tn_circuit *c, const tn_path_opts &o, tn_plan *p) {
     if (e < 0 || e >= c->ne || keep[e]) return tn_fail(TN_ERR_ARG, "tn_path: bad or repeated cut edge %d", e);
     keep[e] = 1;
   }
-  if (two_layers && 2 * c->n > 128)
-    return tn_fail(TN_ERR_UNSUPPORTED, "tn_path: the double-layer network of %d qubits has more than 128 nodes", c->n);
+  if (two_layers && 2 * c->n > 256)
+    return tn_fail(TN_ERR_UNSUPPORTED, "tn_path: the double-layer network of %d qubits has more than 256 nodes", c->n);
   p->c = c;
   p->generation = c->generation;
   if (two_layers) {

@@ -326,15 +326,27 @@ def test_double_layer_plans_with_cuts_and_every_split(tn):
     assert e.value.status == tn.TN_ERR_ARG
 
 
-def test_double_layer_network_node_limit(tn):
-    """The path search holds at most 128 nodes: a double-layer network of more than 64 qubits
-    is refused with TN_ERR_UNSUPPORTED (the 104-qubit grid), its overlap network is planned."""
+def test_double_layer_network_of_the_104_qubit_grid(tn):
+    """Algorithm 1's subset masks hold 256 nodes, so the double-layer network of the 104-qubit
+    grid (208 nodes) is planned: the plan's cost equals the oracle's path score of the order the
+    host-only search returns on the same structural bonds, and a graph of more than 256 nodes is
+    refused with TN_ERR_UNSUPPORTED."""
     w = gen.workload("syc104", n_bits=1)
+    n, edges, kd, bd = _structural_dims(w)
     c = tn.tn_build(w.graph.n, w.graph.edges, w.gates, allocator=None)
+    dl = tn.tn_plan_estimate(c, w.split, w.chi, w.cutoff, layers=2)
+    e2 = edges + [(n + u, n + v) for u, v in edges] + [(q, n + q) for q in range(n)]
+    d2 = [float(x) for x in list(kd) + list(bd) + [2] * n]
+    order2, cuts2, total2 = tn.tn_cut_search(2 * n, e2, d2)
+    assert dl["n_nodes"] == 2 * n == 208 and dl["n_steps"] == 207 and dl["n_cuts"] == len(cuts2) == 0
+    assert sorted(int(v) for v in order2) == list(range(2 * n))
+    assert total2 == pytest.approx(opath.score([int(v) for v in order2], e2, d2), rel=1e-12)
+    assert dl["cmacs"] == pytest.approx(total2, rel=1e-12)
+    assert dl["cmacs"] < tn.tn_plan_estimate(c, w.split, w.chi, w.cutoff)["cmacs"]
+    ring = [(i, (i + 1) % 257) for i in range(257)]
     with pytest.raises(tn.TNError) as e:
-        tn.tn_plan_estimate(c, w.split, w.chi, w.cutoff, layers=2)
+        tn.tn_path_search(257, ring, [2.0] * 257)
     assert e.value.status == tn.TN_ERR_UNSUPPORTED
-    assert tn.tn_plan_estimate(c, w.split, w.chi, w.cutoff)["n_nodes"] <= w.graph.n
 
 
 def test_planning_failures_are_statuses_not_exceptions(tn):
