@@ -408,6 +408,25 @@ def roofline(prof, steps, prec, pk, n_bits):
     return roof
 
 
+def timed_section(torch, stream, step, steps, warmup, flush):
+    """`warmup` untimed calls of step(), then `steps` calls, each after writing the L2-sized flush
+    buffer, timed with CUDA events on `stream`; returns the total seconds of the timed calls."""
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    total = 0.0
+    for _ in range(steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        total += e0.elapsed_time(e1) / 1000.0
+    return total
+
+
 def double_layer_run(tn, np, torch, c, w, packed, a64, steps, warmup, flush, mem_gib, pk):
     """The same amplitudes from the double-layer network: every qubit's ket and bra tensors stay
     two nodes joined by the physical index, and the path Algorithm 1 finds on that network absorbs
@@ -442,16 +461,7 @@ def double_layer_run(tn, np, torch, c, w, packed, a64, steps, warmup, flush, mem
     torch.cuda.synchronize()
     tn.tn_launch_count(reset=True)
     tn.tn_profile_enable(True)
-    total = 0.0
-    for _ in range(steps):
-        flush.zero_()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        step()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        total += e0.elapsed_time(e1) / 1000.0
+    total = timed_section(torch, stream, step, steps, 0, flush)
     prof = tn.tn_profile_read()
     tn.tn_profile_enable(False)
     launches = tn.tn_launch_count() // steps
@@ -503,16 +513,7 @@ def two_sided_run(tn, np, torch, w, packed, a64, prec, steps, warmup, flush, mem
         step()
     torch.cuda.synchronize()
     tn.tn_profile_enable(True)
-    total = 0.0
-    for _ in range(steps):
-        flush.zero_()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        step()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        total += e0.elapsed_time(e1) / 1000.0
+    total = timed_section(torch, stream, step, steps, 0, flush)
     prof = tn.tn_profile_read()
     tn.tn_profile_enable(False)
     rel = np.abs(out[:nchk].cpu().numpy() - d64) / float(np.sqrt(np.mean(np.abs(d64) ** 2)))
