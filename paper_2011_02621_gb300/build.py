@@ -59,7 +59,7 @@ def _run(cmd):
     return r.stdout + r.stderr
 
 
-def build(force: bool = False, verbose: bool = False, debug: bool = False) -> str:
+def build(force: bool = False, verbose: bool = False) -> str:
     """Compile libtn.so if any source is newer than it; returns its path."""
     if not force and not _stale():
         return LIB
@@ -67,15 +67,14 @@ def build(force: bool = False, verbose: bool = False, debug: bool = False) -> st
     nvcc = os.path.join(cuda, "bin", "nvcc")
     os.makedirs(BUILD, exist_ok=True)
     inc = ["-I" + CSRC, "-I" + os.path.join(ROOT, "include"), "-I" + os.path.join(cuda, "include")]
-    dbg = ["-DTN_DEBUG"] if debug else []
     jobs = []
     for f in _sources():
         obj = os.path.join(BUILD, os.path.basename(f) + ".o")
         if f.endswith(".cu"):
             cmd = [nvcc, "-std=c++17", "-O3", ARCH, "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
-                   "-diag-suppress", "550"] + dbg + inc + ["-c", f, "-o", obj]
+                   "-diag-suppress", "550"] + inc + ["-c", f, "-o", obj]
         else:
-            cmd = ["g++", "-std=c++17", "-O2", "-fPIC", "-Wall", "-Wno-unused-function"] + dbg + inc + ["-c", f, "-o", obj]
+            cmd = ["g++", "-std=c++17", "-O2", "-fPIC", "-Wall", "-Wno-unused-function"] + inc + ["-c", f, "-o", obj]
         jobs.append((cmd, obj))
     with cf.ThreadPoolExecutor(max_workers=max(2, min(8, os.cpu_count() or 2))) as ex:
         logs = list(ex.map(lambda j: _run(j[0]), jobs))
@@ -90,4 +89,4 @@ def build(force: bool = False, verbose: bool = False, debug: bool = False) -> st
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True, debug="--debug" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose=True))
