@@ -891,44 +891,70 @@ static tn_status alg1_masks(const PathGraph &pg, int max_rank, bool boundary_onl
     // members other than the isolated qubit
     Mask main = cur.mask;
     if (cur.c >= 0) main.clear(cur.c);
-    for (int i = 0; i < n; ++i) {
-      if (cur.mask.get(i)) continue;
-      const bool adj_s = nb[i].any_and(cur.mask);
-      Iso c_new = -1;
-      if (connected) {
-        if (cur.c >= 0) {
-          if (!nb[i].get(cur.c) || !nb[i].any_and(main)) continue;   // must reconnect the isolated qubit
-        } else if (!adj_s) {
-          bool dist2 = false;            // an isolated qubit must be reconnectable by the next step
-          for (auto &pr : pg.adj[i])
-            if (nb[pr.first].any_and(cur.mask)) { dist2 = true; break; }
-          if (!dist2) continue;
-          c_new = (Iso)i;
+    // The nodes the loop below can accept, in ascending order as before: without Assumption 3
+    // every non-member; with it the neighbours of the set (of the isolated node when there is
+    // one) and, when there is none, the non-members two steps away.
+    Mask cand;
+    if (!connected) {
+      for (int i = 0; i < n; ++i)
+        if (!cur.mask.get(i)) cand.set(i);
+    } else if (cur.c >= 0) {
+      cand = nb[cur.c];
+    } else {
+      Mask front;
+      for (int j = 0; j < W; ++j)
+        for (uint64_t b = cur.mask.w[j]; b; b &= b - 1) {
+          const Mask &m = nb[j * 64 + __builtin_ctzll(b)];
+          for (int t = 0; t < W; ++t) front.w[t] |= m.w[t];
         }
+      cand = front;
+      for (int j = 0; j < W; ++j)
+        for (uint64_t b = front.w[j] & ~cur.mask.w[j]; b; b &= b - 1) {
+          const Mask &m = nb[j * 64 + __builtin_ctzll(b)];
+          for (int t = 0; t < W; ++t) cand.w[t] |= m.w[t];
+        }
+    }
+    for (int t = 0; t < W; ++t) cand.w[t] &= ~cur.mask.w[t];
+    for (int wi = 0; wi < W; ++wi) {
+      for (uint64_t bits = cand.w[wi]; bits; bits &= bits - 1) {
+        const int i = wi * 64 + __builtin_ctzll(bits);
+        const bool adj_s = nb[i].any_and(cur.mask);
+        Iso c_new = -1;
+        if (connected) {
+          if (cur.c >= 0) {
+            if (!nb[i].get(cur.c) || !nb[i].any_and(main)) continue;   // must reconnect the isolated qubit
+          } else if (!adj_s) {
+            bool dist2 = false;            // an isolated qubit must be reconnectable by the next step
+            for (auto &pr : pg.adj[i])
+              if (nb[pr.first].any_and(cur.mask)) { dist2 = true; break; }
+            if (!dist2) continue;
+            c_new = (Iso)i;
+          }
+        }
+        double shared = 1, fresh = 1;
+        int rk = cur.rank;
+        for (auto &pr : pg.adj[i]) {
+          const double d = pg.dims[pr.second];
+          if (cur.mask.get(pr.first)) { shared *= d; rk -= d > 1 ? 1 : 0; }
+          else { fresh *= d; rk += d > 1 ? 1 : 0; }
+        }
+        if (max_rank > 0 && rk > max_rank) continue;
+        PEntry e;
+        e.mask = cur.mask;
+        e.mask.set(i);
+        e.prod_open = cur.prod_open / shared * fresh;
+        // Cost = prod of dims over legs of C^S and C^i (+ byte_weight x the step's input and output)
+        e.score = cur.score + cur.prod_open * fresh + (byte_weight > 0 ? byte_weight * (cur.prod_open + e.prod_open) : 0.0);
+        e.parent = hk.idx;
+        e.last = (Node)i;
+        e.m = (Node)(cur.m + 1);
+        e.rank = (uint8_t)std::max(rk, 0);
+        e.c = c_new;
+        if ((int64_t)arena.size() >= arena_cap)
+          return tn_fail(TN_ERR_NO_PATH, "Algorithm 1: state arena exceeded %lld entries", (long long)arena_cap);
+        arena.push_back(e);
+        pq.push({e.score, (int)e.m, seq++, (int32_t)arena.size() - 1});
       }
-      double shared = 1, fresh = 1;
-      int rk = cur.rank;
-      for (auto &pr : pg.adj[i]) {
-        const double d = pg.dims[pr.second];
-        if (cur.mask.get(pr.first)) { shared *= d; rk -= d > 1 ? 1 : 0; }
-        else { fresh *= d; rk += d > 1 ? 1 : 0; }
-      }
-      if (max_rank > 0 && rk > max_rank) continue;
-      PEntry e;
-      e.mask = cur.mask;
-      e.mask.set(i);
-      e.prod_open = cur.prod_open / shared * fresh;
-      // Cost = prod of dims over legs of C^S and C^i (+ byte_weight x the step's input and output)
-      e.score = cur.score + cur.prod_open * fresh + (byte_weight > 0 ? byte_weight * (cur.prod_open + e.prod_open) : 0.0);
-      e.parent = hk.idx;
-      e.last = (Node)i;
-      e.m = (Node)(cur.m + 1);
-      e.rank = (uint8_t)std::max(rk, 0);
-      e.c = c_new;
-      if ((int64_t)arena.size() >= arena_cap)
-        return tn_fail(TN_ERR_NO_PATH, "Algorithm 1: state arena exceeded %lld entries", (long long)arena_cap);
-      arena.push_back(e);
-      pq.push({e.score, (int)e.m, seq++, (int32_t)arena.size() - 1});
     }
   }
   return tn_fail(TN_ERR_NO_PATH, "Algorithm 1: no path satisfies the assumptions (max_rank %d)", max_rank);
