@@ -234,3 +234,15 @@ def test_programs_feed_the_compiled_plan(tn, compress, layers, chi, split):
         got.append(_execute(layout, steps, tab, kbuf, _place(bra, layout["bra_dims"], layout["bra_off"],
                                                              layout["bra_half_elems"])))
     assert _rel(np.array(got), ref) < 1e-10
+
+
+def test_program_inspection_arguments(tn):
+    w = gen.workload("grid12", n_bits=1)
+    c = tn.tn_build(12, w.graph.edges, w.gates)
+    n = tn.C.c_int64()
+    assert tn.LIB.tn_program_inspect(c.ptr, 4, 0, 1e-12, 2, None, None, tn.C.byref(n)) == tn.TN_ERR_ARG
+    assert tn.LIB.tn_program_inspect(c.ptr, -1, 0, 1e-12, 0, None, None, tn.C.byref(n)) == tn.TN_ERR_ARG
+    assert tn.LIB.tn_program_inspect(None, 4, 0, 1e-12, 0, None, None, tn.C.byref(n)) == tn.TN_ERR_ARG
+    # every gate in the ket: the bra program is empty, the ket holds all 34 two-qubit gates
+    assert tn.tn_program_inspect(c, w.depth, 0, 1e-12, 1) == []
+    assert sum(d["op"] == 2 for d in tn.tn_program_inspect(c, w.depth, 0, 1e-12, 0)) == 34
