@@ -19,7 +19,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtn.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
-CU = ["evolve.cu", "contract.cu", "tc_gemm.cu", "tc_tma.cu", "tc_tma_persist.cu", "static_scratch.cu"]
+CU = ["evolve.cu", "contract.cu", "tc_gemm.cu", "tc_tma.cu", "tc_tma_persist.cu", "static_scratch.cu", "stream.cu"]
 CPP = ["host.cpp", "server.cpp", "tune.cpp", "batch.cpp"]
 
 

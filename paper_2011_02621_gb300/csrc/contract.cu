@@ -479,6 +479,7 @@ bool simt_variant_ok(const StepParams &s, int v) {
     case SIMT_FIXED: return has_fixed(s.K, s.N);
     case SIMT_SMALL: return s.M * s.N <= 256;
     case SIMT_NARROW: return s.M <= 16 && s.M * s.K <= 2048;
+    case SIMT_BOX: return s.box_tm > 0 && s.K * s.N <= TN_BOX_MAXKN && s.N <= TN_BOX_MAXN;
     default: return false;
   }
 }
@@ -497,6 +498,7 @@ cudaError_t launch_step(const StepParams &s, const ContractArgs &a, const void *
     else variant = s.N >= 48 ? SIMT_T64 : s.N >= 12 ? SIMT_T128 : SIMT_T256;
   }
   switch (variant) {
+    case SIMT_BOX: return launch_step_box<R>(s, a, ket, bra, t_in, t_out, st);
     case SIMT_FIXED:
 #define TN_FIXED(k, n) \
   if (s.K == k && s.N == n) return launch_stream_fixed<R, k, n>(s, a, ket, bra, t_in, t_out, st);

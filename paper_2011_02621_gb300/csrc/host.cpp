@@ -1531,6 +1531,26 @@ static tn_status validate_plan(const tn_plan *p) {
     for (int r = 0; r < s.n_rest; ++r) orow += (int64_t)(s.rest_dim[r] - 1) * s.rest_ostride[r];
     const int64_t omax = orow + tmax(s.t_ocol, s.N);
     if (omax >= p->maxT) return bad("step output outside the item stride", (int)j, omax, p->maxT);
+    if (s.box_tm > 0) {
+      // box tiles: box_tm divides M along the digits (trailing digits whole, then one divisor),
+      // and the sorted write table holds every (r, n) of a tile once
+      int64_t q = s.box_tm;
+      for (int r = s.n_rest - 1; r >= 0 && q > 1; --r) {
+        const int64_t d = s.rest_dim[r];
+        if (q % d == 0) { q /= d; continue; }
+        if (d % q != 0) return bad("box tile not aligned to the rest digits", (int)j, s.box_tm, s.M);
+        q = 1;
+      }
+      if (q != 1 || s.M % s.box_tm != 0 || s.box_tm >= 65536)
+        return bad("box tile does not divide the rows", (int)j, s.box_tm, s.M);
+      std::vector<char> seen((size_t)s.box_tm * s.N, 0);
+      for (int64_t e = 0; e < (int64_t)s.box_tm * s.N; ++e) {
+        const uint32_t pr = (uint32_t)tab[s.t_wperm + e];
+        const int64_t r = pr >> 16, nn = pr & 0xffffu;
+        if (r >= s.box_tm || nn >= s.N || seen[r * s.N + nn]) return bad("box write table", (int)j, e, s.box_tm * s.N);
+        seen[r * s.N + nn] = 1;
+      }
+    }
   }
   return TN_OK;
 }
@@ -1742,6 +1762,36 @@ static tn_status compile_plan(tn_plan *p) {
     s.t_bnb = push_tab(nb);
     s.t_sa = push_tab(sa);
     s.t_sb = push_tab(sb);
+    if (j > 0 && K * N <= TN_BOX_MAXKN && N <= TN_BOX_MAXN) {
+      // Row tiles of the box-tiled streaming kernel: the trailing rest digits (fastest first),
+      // the last one taken in part (a divisor of its dim), so that m = t * tm + r splits the
+      // digits of m and orow(m) = orow(t * tm) + orow(r); at most TN_BOX_ROWS_ELEMS / (K + N) rows.
+      const int64_t lim = std::max<int64_t>(1, TN_BOX_ROWS_ELEMS / (K + N));
+      int64_t tm = 1;
+      for (int r = s.n_rest - 1; r >= 0; --r) {
+        const int64_t d = s.rest_dim[r];
+        if (tm * d <= lim) { tm *= d; continue; }
+        int64_t f = lim / tm;
+        while (f > 1 && d % f != 0) --f;
+        tm *= f;
+        break;
+      }
+      // the tile's outputs in increasing output offset (ties in row-major order)
+      std::vector<int64_t> orl(tm);
+      for (int64_t r = 0; r < tm; ++r) {
+        int64_t x = r, off = 0;
+        for (int q = s.n_rest - 1; q >= 0; --q) { off += (x % s.rest_dim[q]) * s.rest_ostride[q]; x /= s.rest_dim[q]; }
+        orl[r] = off;
+      }
+      std::vector<int64_t> perm(tm * N);
+      for (int64_t e = 0; e < tm * N; ++e) perm[e] = e;
+      std::stable_sort(perm.begin(), perm.end(), [&](int64_t x, int64_t y) {
+        return orl[x / N] + ocol[x % N] < orl[y / N] + ocol[y % N];
+      });
+      for (int64_t &e : perm) e = ((e / N) << 16) | (e % N);
+      s.box_tm = (int)tm;
+      s.t_wperm = push_tab(perm);
+    }
     std::vector<int64_t> skk, sbb;
     s.ket_sig = leg_strides(i, c.dk, skk);
     s.bra_sig = leg_strides(i, c.db, sbb);
@@ -2233,11 +2283,13 @@ cudaError_t enqueue_step(const tn_plan *p, const Workspace &w, size_t j, int k, 
   const double fl = 8.0 * items * (double)sp.M * sp.K * sp.N;
   const int64_t cap = (int64_t)w.chunk * w.slice_chunk;
   if (prec == TN_FP64) {
-    ProfScope ps("contract_step_fp64", st, by, fl);
+    ProfScope ps(k == SIMT_BOX ? "contract_step_fp64_box" : "contract_step_fp64", st, by, fl);
     return launch_step<double>(sp, a, ket, bra, tin, od, st, k);
   }
   if (k < SK_TC) {
-    ProfScope ps(prec == TN_FP32 ? "contract_step_fp32" : "contract_step_fp32_tc_fallback", st, by, fl);
+    ProfScope ps(k == SIMT_BOX ? (prec == TN_FP32 ? "contract_step_fp32_box" : "contract_step_fp32_box_tc_fallback")
+                               : (prec == TN_FP32 ? "contract_step_fp32" : "contract_step_fp32_tc_fallback"),
+                 st, by, fl);
     return launch_step<float>(sp, a, ket, bra, tin, od, st, k);
   }
   if (k == SK_TC) {

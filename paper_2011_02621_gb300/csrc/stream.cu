@@ -1,0 +1,222 @@
+// Box-tiled streaming contraction step (SIMT complex FMA) for thin steps: small K and N, many
+// rows, the shape of every step of the double-layer network (ket and bra tensors absorbed one at
+// a time, the sums of Eq. overlap without the per-qubit overlap tensors) and of the thin steps
+// of the overlap network.
+//
+// One step computes, per (bitstring, slice) item, T_out[orow(m) + ocol(n)] = sum_k T_in[m][k]
+// C[k][n] with C[k][n] the absorbed node's operand (Eq. overlap; for a double-layer step one
+// tensor against the unit operand). Such a step moves 8 (M K + M N) bytes per item for 8 M K N
+// flops, at most about 1.6 flops per byte here, so HBM bandwidth bounds it. The kernel is laid
+// out for that roof:
+//  * a CTA works on one item: it builds C in shared memory once, then walks row tiles of box_tm
+//    rows whose input is one contiguous block of box_tm * K complex values, copied with 16-byte
+//    cp.async while the previous tile's outputs are being written;
+//  * each thread computes a row's group of TN consecutive columns from shared memory;
+//  * the tile's outputs go out in increasing output offset (a table the plan compiler sorts), so
+//    that the permuted layout of the next step is written with full, coalesced sectors.
+#include <cuda_runtime.h>
+
+#include "tn_device.h"
+#include "tn_internal.h"
+
+namespace {
+
+template <typename R> struct BoxT;
+template <> struct BoxT<double> { using V = double2; };
+template <> struct BoxT<float> { using V = float2; };
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *g) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *smem, const void *g) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Shared memory of one CTA: C[K][N], the input tile [tm][kp], the output tile [tm][np] (rows
+// padded against bank conflicts), the tile's local output row offsets and the column offsets.
+struct BoxLayout {
+  int kp, np;
+  size_t c_off, in_off, out_off, orow_off, ocol_off, bytes;
+};
+
+__host__ __device__ inline size_t box_align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+template <typename V>
+__host__ __device__ inline BoxLayout box_layout(int tm, int K, int N) {
+  BoxLayout L;
+  if (sizeof(V) == 8) {           // complex64: 16-byte row chunks when K is even
+    L.kp = (K % 2 == 0) ? (K >= 8 ? K + 2 : K) : K;
+    L.np = (N % 2 == 0) ? N + 2 : N + 1;
+  } else {                        // complex128: one element per 16-byte copy
+    L.kp = (K % 2 == 0) ? K + 1 : K;
+    L.np = (N % 2 == 0) ? N + 1 : N;
+  }
+  L.c_off = 0;
+  L.in_off = box_align16(L.c_off + (size_t)K * N * sizeof(V));
+  L.out_off = box_align16(L.in_off + (size_t)tm * L.kp * sizeof(V));
+  L.orow_off = box_align16(L.out_off + (size_t)tm * L.np * sizeof(V));
+  L.ocol_off = L.orow_off + (size_t)tm * sizeof(int);
+  L.bytes = box_align16(L.ocol_off + (size_t)N * sizeof(int));
+  return L;
+}
+
+// TN consecutive entries of one row of C (TN = 4 or 2 complex64: 16-byte loads)
+template <int TN, typename V>
+__device__ __forceinline__ void load_c(const V *p, V c[TN]) {
+  if constexpr (sizeof(V) == 8 && TN % 2 == 0) {
+#pragma unroll
+    for (int j = 0; j < TN; j += 2) {
+      const float4 q = *reinterpret_cast<const float4 *>(p + j);
+      c[j].x = q.x;
+      c[j].y = q.y;
+      c[j + 1].x = q.z;
+      c[j + 1].y = q.w;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < TN; ++j) c[j] = p[j];
+  }
+}
+
+template <typename R, int TN>
+__global__ void __launch_bounds__(256)
+step_box_kernel(StepParams s, ContractArgs a, const typename BoxT<R>::V *ket, const typename BoxT<R>::V *bra,
+                const typename BoxT<R>::V *tin, OutDesc out, int64_t tpc) {
+  using V = typename BoxT<R>::V;
+  extern __shared__ __align__(16) unsigned char box_raw[];
+  const int TM = s.box_tm, K = (int)s.K, N = (int)s.N;
+  const BoxLayout L = box_layout<V>(TM, K, N);
+  V *Cs = reinterpret_cast<V *>(box_raw + L.c_off);
+  V *Ins = reinterpret_cast<V *>(box_raw + L.in_off);
+  V *Outs = reinterpret_cast<V *>(box_raw + L.out_off);
+  int *orow_s = reinterpret_cast<int *>(box_raw + L.orow_off);
+  int *ocol_s = reinterpret_cast<int *>(box_raw + L.ocol_off);
+  const int tid = threadIdx.x;
+  const int64_t T = s.M / TM;                    // row tiles per item
+  const int64_t cpi = (T + tpc - 1) / tpc;       // CTAs per item
+  const int64_t item = (int64_t)blockIdx.x / cpi;
+  const int64_t t_begin = ((int64_t)blockIdx.x % cpi) * tpc;
+  const int64_t t_end = t_begin + tpc < T ? t_begin + tpc : T;
+  const ItemCtx c = item_ctx(a, s, item);
+  const V *tp = tin + item * a.t_stride;
+  const bool k_pow2 = (K & (K - 1)) == 0;
+  const int k_log = __ffs(K) - 1;
+
+  // the input tile t: box_tm rows of K values, contiguous at t * box_tm * K
+  auto load = [&](int64_t t) {
+    const V *src = tp + t * (int64_t)TM * K;
+    if (sizeof(V) == 8 && K % 2 == 0) {
+      const int n2 = TM * K / 2, kh = K / 2;
+      for (int e = tid; e < n2; e += 256) {
+        const int r = k_pow2 ? (e >> (k_log - 1)) : e / kh;
+        cp_async16(Ins + r * L.kp + 2 * (e - r * kh), src + 2 * e);
+      }
+    } else {
+      for (int e = tid; e < TM * K; e += 256) {
+        const int r = k_pow2 ? (e >> k_log) : e / K;
+        if (sizeof(V) == 8) cp_async8(Ins + r * L.kp + (e - r * K), src + e);
+        else cp_async16(Ins + r * L.kp + (e - r * K), src + e);
+      }
+    }
+    cp_async_commit();
+  };
+  if (t_begin < t_end) load(t_begin);
+
+  {   // the absorbed node's operand (Eq. overlap) and the offset tables, once per CTA
+    const V *kp = ket + s.ket_off + c.sa;
+    const V *bp = bra + c.b * a.bra_stride + s.bra_off + c.sb;
+    const int32_t *bka = a.tab + s.t_bka, *bkb = a.tab + s.t_bkb;
+    const int32_t *bna = a.tab + s.t_bna, *bnb = a.tab + s.t_bnb;
+    for (int i = tid; i < K * N; i += 256) {
+      const int k = i / N, n = i - k * N;
+      Cs[i] = overlap_elem(kp, bp, (int64_t)bka[k] + bna[n], (int64_t)bkb[k] + bnb[n], s.ket_sig, s.bra_sig, s.phys);
+    }
+    for (int r = tid; r < TM; r += 256) orow_s[r] = orow_of(s, r);
+    for (int n = tid; n < N; n += 256) ocol_s[n] = a.tab[s.t_ocol + n];
+  }
+
+  const int G = N / TN;                 // threads per row
+  const int RP = 256 / G;               // rows per pass
+  const int g = tid % G, r0 = tid / G;
+  const uint32_t *wperm = reinterpret_cast<const uint32_t *>(a.tab + s.t_wperm);
+  for (int64_t t = t_begin; t < t_end; ++t) {
+    cp_async_wait_all();
+    __syncthreads();                    // input tile t and C in place; the last tile's outputs written
+    if (r0 < RP) {
+      for (int r = r0; r < TM; r += RP) {
+        V acc[TN];
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[j] = cz<V>();
+        const V *xr = Ins + r * L.kp;
+        const V *cc = Cs + g * TN;
+        for (int k = 0; k < K; ++k) {
+          const V x = xr[k];
+          V cv[TN];
+          load_c<TN>(cc + k * N, cv);
+#pragma unroll
+          for (int j = 0; j < TN; ++j) acc[j] = cfma(x, cv[j], acc[j]);
+        }
+        V *o = Outs + r * L.np + g * TN;
+#pragma unroll
+        for (int j = 0; j < TN; ++j) o[j] = acc[j];
+      }
+    }
+    __syncthreads();                    // output tile complete; the input tile may be replaced
+    if (t + 1 < t_end) load(t + 1);
+    const int obase = orow_of(s, t * (int64_t)TM);
+    for (int e = tid; e < TM * N; e += 256) {
+      const uint32_t pr = __ldg(wperm + e);
+      const int r = (int)(pr >> 16), n = (int)(pr & 0xffffu);
+      store_out(out, a.t_stride, item, obase + orow_s[r] + ocol_s[n], Outs[r * L.np + n]);
+    }
+  }
+}
+
+template <typename R, int TN>
+cudaError_t launch_tn(const StepParams &s, const ContractArgs &a, const void *ket, const void *bra, const void *t_in,
+                      const OutDesc &out, cudaStream_t st) {
+  using V = typename BoxT<R>::V;
+  const BoxLayout L = box_layout<V>(s.box_tm, (int)s.K, (int)s.N);
+  if (L.bytes > 48 * 1024) {
+    const int lim = tn_smem_optin<step_box_kernel<R, TN>>();
+    if (lim < 0 || (size_t)lim < L.bytes) return cudaErrorInvalidValue;
+  }
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  // tiles per CTA: whole items when there are enough of them to fill every SM many times over,
+  // else the items' tiles spread over more CTAs
+  const int64_t T = s.M / s.box_tm;
+  int64_t tpc = T * a.items / ((int64_t)sms * 16);
+  tpc = tpc < 1 ? 1 : tpc > T ? T : tpc;
+  const int64_t cpi = (T + tpc - 1) / tpc;
+  const int64_t grid = cpi * a.items;
+  if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  step_box_kernel<R, TN><<<(unsigned)grid, 256, L.bytes, st>>>(s, a, (const V *)ket, (const V *)bra, (const V *)t_in,
+                                                               out, tpc);
+  tn_count_launch(1);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+template <typename R>
+cudaError_t launch_step_box(const StepParams &s, const ContractArgs &a, const void *ket, const void *bra,
+                            const void *t_in, const OutDesc &out, cudaStream_t st) {
+  if (a.items <= 0) return cudaSuccess;
+  if (s.box_tm <= 0 || s.M % s.box_tm != 0 || s.K * s.N > TN_BOX_MAXKN || s.N > TN_BOX_MAXN)
+    return cudaErrorInvalidValue;
+  if (s.N % 4 == 0) return launch_tn<R, 4>(s, a, ket, bra, t_in, out, st);
+  if (s.N % 2 == 0) return launch_tn<R, 2>(s, a, ket, bra, t_in, out, st);
+  return launch_tn<R, 1>(s, a, ket, bra, t_in, out, st);
+}
+
+template cudaError_t launch_step_box<double>(const StepParams &, const ContractArgs &, const void *, const void *,
+                                             const void *, const OutDesc &, cudaStream_t);
+template cudaError_t launch_step_box<float>(const StepParams &, const ContractArgs &, const void *, const void *,
+                                            const void *, const OutDesc &, cudaStream_t);

@@ -89,6 +89,12 @@ struct StepParams {
   int64_t phys;                 // values of the node's physical index (2; 4 or 8 for merged nodes)
   // offsets of the int32 tables in the plan's table buffer
   int64_t t_ocol, t_bka, t_bkb, t_bna, t_bnb, t_sa, t_sb;
+  // Row tiles of the box-tiled streaming kernel (SIMT_BOX; 0 = the step has none): box_tm rows
+  // m = t * box_tm + r, r < box_tm, whose input rows are one contiguous block and whose output
+  // offsets split as orow(t * box_tm) + orow(r) (box_tm is aligned to the rest digits).
+  // t_wperm: box_tm * N entries (r << 16 | n), the tile's outputs in increasing output offset.
+  int box_tm;
+  int64_t t_wperm;
 };
 
 struct ContractArgs {
@@ -126,8 +132,15 @@ cudaError_t launch_step(const StepParams &s, const ContractArgs &a, const void *
                         const void *t_in, const OutDesc &out, cudaStream_t st, int variant = 0);
 // SIMT step kernels: the shape heuristic or one kernel forced (the autotuner's candidates)
 enum SimtVariant { SIMT_AUTO = 0, SIMT_T64 = 1, SIMT_T128 = 2, SIMT_T256 = 3, SIMT_STREAM = 4, SIMT_FIXED = 5,
-                   SIMT_SMALL = 6, SIMT_NARROW = 7 };
+                   SIMT_SMALL = 6, SIMT_NARROW = 7, SIMT_BOX = 8 };
 bool simt_variant_ok(const StepParams &s, int variant);
+// the box-tiled streaming step (stream.cu): thin steps with K * N <= TN_BOX_MAXKN, N <= TN_BOX_MAXN
+#define TN_BOX_MAXKN 2048
+#define TN_BOX_MAXN 256
+#define TN_BOX_ROWS_ELEMS 4096   // box_tm * (K + N) at most (shared memory of one tile)
+template <typename R>
+cudaError_t launch_step_box(const StepParams &s, const ContractArgs &a, const void *ket, const void *bra,
+                            const void *t_in, const OutDesc &out, cudaStream_t st);
 // out[b] (+)= sum over the group's slices, in slice order, in FP64 (accumulate: add to out)
 template <typename R>
 cudaError_t launch_slice_sum(const void *res, int64_t items_stride, int64_t n_bits, int64_t n_slices,

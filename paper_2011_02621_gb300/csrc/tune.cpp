@@ -18,7 +18,7 @@
 
 namespace {
 
-const int kCandidates[] = {SIMT_AUTO, SIMT_T64,  SIMT_T128, SIMT_T256, SIMT_STREAM, SIMT_FIXED, SIMT_SMALL, SIMT_NARROW, SK_TC,
+const int kCandidates[] = {SIMT_AUTO, SIMT_T64,  SIMT_T128, SIMT_T256, SIMT_STREAM, SIMT_FIXED, SIMT_SMALL, SIMT_NARROW, SIMT_BOX, SK_TC,
                            SK_TMA,    SK_TMA128, SK_TMA64,  SK_TMAF,   SK_TMAF128,  SK_TMAF64,  SK_TMAC,    SK_TMAC128,
                            SK_TMAC64};
 

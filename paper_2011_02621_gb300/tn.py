@@ -629,7 +629,8 @@ def tn_server_stats_get(s: Server) -> dict:
 # kernel autotuning and batched circuits
 # ---------------------------------------------------------------------------
 KERNEL_NAMES = {0: "simt_auto", 1: "simt_tile64x64", 2: "simt_tile128x16", 3: "simt_tile256x4",
-                4: "simt_stream", 5: "simt_stream_fixed", 6: "simt_small", 7: "simt_narrow", 16: "tcgen05_split",
+                4: "simt_stream", 5: "simt_stream_fixed", 6: "simt_small", 7: "simt_narrow", 8: "simt_box",
+                16: "tcgen05_split",
                 32: "tcgen05_tma_buildb", 33: "tcgen05_tma_buildb_bn128", 34: "tcgen05_tma_buildb_bn64",
                 40: "tcgen05_tma_loadb", 41: "tcgen05_tma_loadb_bn128", 42: "tcgen05_tma_loadb_bn64",
                 48: "tcgen05_tma", 49: "tcgen05_tma_bn128", 50: "tcgen05_tma_bn64"}
