@@ -1246,6 +1246,8 @@ static Net double_layer_net(const tn_circuit *c) {
   g.owner.resize(n);
   g.phys.assign(g.n, 2);              // the unit operand's two values
   g.layer.resize(g.n);
+  g.dl_id.resize(g.n);
+  for (int v = 0; v < g.n; ++v) g.dl_id[v] = v;
   g.ket_off.resize(g.n);
   g.bra_off.resize(g.n);
   for (int q = 0; q < n; ++q) {
@@ -1267,6 +1269,47 @@ static Net double_layer_net(const tn_circuit *c) {
   g.ket_elems = c->ket.item_elems;
   g.bra_elems = c->bra.item_elems;
   return g;
+}
+
+// Renumber the surviving nodes (alive) and edges (eu >= 0) of g compactly, in increasing order;
+// nid and eidx map the old ids to the new ones (-1: gone).
+static void compact_net(Net &g, const std::vector<char> &alive, std::vector<int> &nid, std::vector<int> &eidx) {
+  nid.assign(g.n, -1);
+  eidx.assign(g.ne, -1);
+  Net h;
+  const bool dl = !g.layer.empty();
+  for (int v = 0; v < g.n; ++v)
+    if (alive[v]) {
+      nid[v] = h.n++;
+      h.rep.push_back(g.rep[v]);
+      h.phys.push_back(g.phys[v]);
+      h.ket_off.push_back(g.ket_off[v]);
+      h.bra_off.push_back(g.bra_off[v]);
+      if (dl) {
+        h.layer.push_back(g.layer[v]);
+        h.dl_id.push_back(g.dl_id[v]);
+      }
+    }
+  for (int e = 0; e < g.ne; ++e)
+    if (g.eu[e] >= 0) {
+      eidx[e] = h.ne++;
+      h.eu.push_back(nid[g.eu[e]]);
+      h.ev.push_back(nid[g.ev[e]]);
+      h.eid.push_back(g.eid[e]);
+      h.dk.push_back(g.dk[e]);
+      h.db.push_back(g.db[e]);
+    }
+  h.legs.resize(h.n);
+  for (int v = 0; v < g.n; ++v)
+    if (alive[v])
+      for (int e : g.legs[v]) h.legs[nid[v]].push_back(eidx[e]);
+  h.owner.resize(g.owner.size());
+  for (size_t q = 0; q < g.owner.size(); ++q) h.owner[q] = nid[g.owner[q]];
+  h.ket_elems = g.ket_elems;
+  h.bra_elems = g.bra_elems;
+  h.mk = g.mk;
+  h.mb = g.mb;
+  g = h;
 }
 
 // Merge node v into u through edge a on both halves: U's tensor becomes
@@ -1368,37 +1411,142 @@ static void merge_nodes(Net &g, const std::vector<char> &keep_edge) {
       did = true;
     }
   }
-  // compact: surviving nodes and edges in increasing order
-  std::vector<int> nid(g.n, -1), eidx(g.ne, -1);
-  Net h;
-  for (int v = 0; v < g.n; ++v)
-    if (alive[v]) {
-      nid[v] = h.n++;
-      h.rep.push_back(g.rep[v]);
-      h.phys.push_back(g.phys[v]);
-      h.ket_off.push_back(g.ket_off[v]);
-      h.bra_off.push_back(g.bra_off[v]);
+  std::vector<int> nid, eidx;
+  compact_net(g, alive, nid, eidx);
+}
+
+// Join two same-layer nodes of a double-layer network, v into u through their edge a, in that
+// layer's half: u's tensor becomes [legs_u \ a, legs_v \ a] = sum_a U V, computed exactly in FP64
+// (once per batch for ket tensors, for every bitstring for bra tensors) in a new slot past the
+// half's item.
+static void apply_layer_merge(Net &g, int u, int v, int a) {
+  const int half = g.layer[u] == 2 ? 1 : 0;
+  auto strides = [&](int node, std::vector<int64_t> &st) -> int64_t {
+    const auto &L = g.legs[node];
+    st.assign(L.size(), 1);
+    int64_t x = 1;
+    for (int j = (int)L.size() - 1; j >= 0; --j) { st[j] = x; x *= g.dc(L[j]); }
+    return x;
+  };
+  MergeParams m;
+  std::memset(&m, 0, sizeof m);
+  std::vector<int64_t> su, sv;
+  m.su_p = strides(u, su);
+  m.sv_p = strides(v, sv);
+  m.pu = m.pv = 1;
+  m.da = (int)g.dc(a);
+  m.u_off = half ? g.bra_off[u] : g.ket_off[u];
+  m.v_off = half ? g.bra_off[v] : g.ket_off[v];
+  int64_t size = 1;
+  for (size_t j = 0; j < g.legs[u].size(); ++j) {
+    const int e = g.legs[u][j];
+    if (e == a) { m.su_a = su[j]; continue; }
+    m.du[m.nu] = (int)g.dc(e);
+    m.su[m.nu++] = su[j];
+    size *= g.dc(e);
+  }
+  for (size_t j = 0; j < g.legs[v].size(); ++j) {
+    const int e = g.legs[v][j];
+    if (e == a) { m.sv_a = sv[j]; continue; }
+    m.dv[m.nv] = (int)g.dc(e);
+    m.sv[m.nv++] = sv[j];
+    size *= g.dc(e);
+  }
+  m.out_size = size;
+  int64_t &ext = half ? g.bra_elems : g.ket_elems;
+  m.out_off = ext;
+  ext += (size + 1) & ~1LL;
+  (half ? g.mb : g.mk).push_back(m);
+  (half ? g.bra_off : g.ket_off)[u] = m.out_off;
+  std::vector<int> L;
+  for (int e : g.legs[u])
+    if (e != a) L.push_back(e);
+  for (int e : g.legs[v]) {
+    if (e == a) continue;
+    L.push_back(e);
+    (g.eu[e] == v ? g.eu[e] : g.ev[e]) = u;
+  }
+  g.legs[u] = L;
+  g.legs[v].clear();
+  g.eu[a] = g.ev[a] = -1;
+  for (int &o : g.owner)
+    if (o == v) o = u;
+}
+
+// Joining partial paths (supplement, the discussion of Assumption 3: partial paths that grow
+// separately and are joined by one pairwise contraction), as a pass over the path Algorithm 1 found
+// on a double-layer network. Where the path absorbs two nodes u, v of the same layer in a row and
+// they share one edge a that is not cut, the pair can be contracted on its own first (a second
+// partial path {u, v}) and joined to the main path in one step. The pass does so when that lowers
+// both the complex multiply-adds (the pair's own contraction counted once per bitstring for bra
+// tensors) and the elements the steps read and write, then tries the joined node with the next one.
+// The amplitude is the same sum in another grouping; the largest intermediate does not grow (the
+// joined step reads step j's input and writes step j + 1's output).
+static void join_paths(tn_plan *p) {
+  Net &g = p->net;
+  std::vector<char> is_cut(g.ne, 0), open(g.ne, 0), alive(g.n, 1);
+  for (int e : p->cuts) is_cut[e] = 1;
+  std::vector<int> ord = p->order;
+  auto other = [&](int e, int x) { return g.eu[e] == x ? g.ev[e] : g.eu[e]; };
+  // K (legs of L open now) and N (legs of L not open and not cut), as products of dims
+  auto split = [&](const std::vector<int> &L, int skip, double &K, double &N) {
+    K = N = 1;
+    for (int e : L) {
+      if (e == skip || is_cut[e]) continue;
+      if (open[e]) K *= (double)g.dc(e);
+      else N *= (double)g.dc(e);
     }
-  for (int e = 0; e < g.ne; ++e)
-    if (g.eu[e] >= 0) {
-      eidx[e] = h.ne++;
-      h.eu.push_back(nid[g.eu[e]]);
-      h.ev.push_back(nid[g.ev[e]]);
-      h.eid.push_back(g.eid[e]);
-      h.dk.push_back(g.dk[e]);
-      h.db.push_back(g.db[e]);
+  };
+  double oprod = 1;   // elements of the current intermediate
+  size_t j = 0;
+  while (j + 1 < ord.size()) {
+    const int u = ord[j], v = ord[j + 1];
+    int a = -1, shared = 0;
+    for (int e : g.legs[u])
+      if (other(e, u) == v) { a = e; ++shared; }
+    bool joined = false;
+    if (g.layer[u] == g.layer[v] && shared == 1 && !is_cut[a] && (int)g.legs[u].size() - 1 <= TN_MERGE_MAXLEGS &&
+        (int)g.legs[v].size() - 1 <= TN_MERGE_MAXLEGS) {
+      double K1, N1, K2, N2, Kw, Nw, Kv, Nv;
+      split(g.legs[u], -1, K1, N1);
+      const double M1 = oprod / K1;
+      // the intermediate after u: u's open legs closed, its new ones (a among them) opened
+      split(g.legs[v], a, Kv, Nv);
+      K2 = Kv * (double)g.dc(a);   // v's legs open after u: a, and those already open before u
+      N2 = Nv;
+      const double M2 = M1 * N1 / K2;
+      Kw = K1 * Kv;
+      Nw = (N1 / (double)g.dc(a)) * Nv;
+      const double Mw = oprod / Kw;
+      const bool first = j == 0;
+      const double seq_mac = (first ? 0 : M1 * K1 * N1) + M2 * K2 * N2;
+      const double seq_el = (first ? 0 : M1 * K1 + M1 * N1) + M2 * K2 + M2 * N2;
+      double pair = 1;   // the pair's own contraction: prod of the dims of all legs of u and v, a once
+      for (int e : g.legs[u]) pair *= (double)g.dc(e);
+      for (int e : g.legs[v])
+        if (e != a) pair *= (double)g.dc(e);
+      const double w_mac = (first ? 0 : Mw * Kw * Nw) + (g.layer[u] == 2 ? pair : 0);
+      const double w_el = first ? 0 : Mw * Kw + Mw * Nw;
+      if (w_mac <= seq_mac && w_el <= seq_el && (w_mac < seq_mac || w_el < seq_el)) {
+        apply_layer_merge(g, u, v, a);
+        alive[v] = 0;
+        ord.erase(ord.begin() + (long)j + 1);
+        joined = true;
+      }
     }
-  h.legs.resize(h.n);
-  for (int v = 0; v < g.n; ++v)
-    if (alive[v])
-      for (int e : g.legs[v]) h.legs[nid[v]].push_back(eidx[e]);
-  h.owner.resize(g.owner.size());
-  for (size_t q = 0; q < g.owner.size(); ++q) h.owner[q] = nid[g.owner[q]];
-  h.ket_elems = g.ket_elems;
-  h.bra_elems = g.bra_elems;
-  h.mk = g.mk;
-  h.mb = g.mb;
-  g = h;
+    if (joined) continue;
+    double K1, N1;
+    split(g.legs[u], -1, K1, N1);
+    oprod = oprod / K1 * N1;
+    for (int e : g.legs[u])
+      if (!is_cut[e]) open[e] = !open[e];
+    ++j;
+  }
+  std::vector<int> nid, eidx;
+  compact_net(g, alive, nid, eidx);
+  for (int &x : ord) x = nid[x];
+  for (int &e : p->cuts) e = eidx[e];
+  p->order = ord;
 }
 
 static tn_status tn_merge_search_impl(const tn_graph *g, const int32_t *ket_dims, const int32_t *bra_dims,
@@ -1910,6 +2058,7 @@ static tn_status plan_host(tn_circuit *c, const tn_path_opts &o, tn_plan *p) {
     s = choose_cuts(g, o, dims, o.n_cuts, limit, p->cuts, p->order, p->score, p->pops, p->rank_used);
     if (s != TN_OK) return s;
   }
+  if (two_layers && !o.no_merge) join_paths(p);
   s = compile_plan(p);
   if (s != TN_OK) return s;
   const double budget = o.mem_budget_bytes > 0 ? o.mem_budget_bytes : 8.0 * (1ull << 30);
@@ -2144,7 +2293,7 @@ extern "C" tn_status tn_plan_details(const tn_plan *p, int32_t *order, int32_t *
   if (!p) return tn_fail(TN_ERR_ARG, "tn_plan_details: NULL plan");
   if (order) {
     if (!p->net.layer.empty())
-      for (int j = 0; j < p->net.n; ++j) order[j] = p->order[j];
+      for (int j = 0; j < p->net.n; ++j) order[j] = p->net.dl_id[p->order[j]];
     else
       for (int j = 0; j < p->c->n; ++j) order[j] = j < p->net.n ? p->net.rep[p->order[j]] : -1;
   }

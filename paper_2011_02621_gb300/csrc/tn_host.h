@@ -90,8 +90,9 @@ struct Net {
   // Such a node has one tensor, [legs in order] with leg dims dc, in its own half's item; the
   // other operand slot of its steps reads the plan's two-value unit tensor [1, 0].
   std::vector<int> layer;
+  std::vector<int> dl_id;                         // double-layer nodes: the original node id (0 .. 2n-1)
   int64_t dc(int e) const { return dk[e] * db[e]; }
-  bool merged() const { return !mk.empty(); }
+  bool merged() const { return !mk.empty() || !mb.empty(); }
 };
 
 struct tn_plan {

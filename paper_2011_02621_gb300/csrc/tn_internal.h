@@ -54,15 +54,16 @@ cudaError_t launch_to_c64(const double2 *src, float2 *dst, int64_t n, cudaStream
 // Merging node v into its neighbour u through their shared edge a, on one half (ket or bra), in
 // FP64 and exactly: out[p_u, p_v, legs_u \ a, legs_v \ a] = sum_a U[p_u, legs_u] V[p_v, legs_v].
 // Element offsets are within one item's region; the rest legs are listed in output order.
-#define TN_MAXMLEGS 8
+#define TN_MAXMLEGS 8          // rest legs of a merged pair in the overlap network's merging policy
+#define TN_MERGE_MAXLEGS 16    // rest legs per operand a merge can describe (joined double-layer nodes)
 struct MergeParams {
   int64_t u_off, v_off, out_off, out_size;
   int64_t su_p, sv_p;                   // physical-index strides in U and V
   int64_t su_a, sv_a;                   // strides of the shared leg a in U and V
   int pu, pv, da;                       // physical values of U and V, dim of a on this half
   int nu, nv;                           // rest legs of U and V
-  int du[TN_MAXMLEGS], dv[TN_MAXMLEGS]; // their dims
-  int64_t su[TN_MAXMLEGS], sv[TN_MAXMLEGS];   // their strides in U and V
+  int du[TN_MERGE_MAXLEGS], dv[TN_MERGE_MAXLEGS];       // their dims
+  int64_t su[TN_MERGE_MAXLEGS], sv[TN_MERGE_MAXLEGS];   // their strides in U and V
 };
 cudaError_t launch_merge(const MergeParams &m, double2 *base, int64_t item_stride, int64_t items, cudaStream_t st);
 cudaError_t launch_pack_bits(const uint64_t *src, uint64_t *dst, int64_t n_words, cudaStream_t st);
@@ -135,7 +136,7 @@ enum SimtVariant { SIMT_AUTO = 0, SIMT_T64 = 1, SIMT_T128 = 2, SIMT_T256 = 3, SI
                    SIMT_SMALL = 6, SIMT_NARROW = 7, SIMT_BOX = 8 };
 bool simt_variant_ok(const StepParams &s, int variant);
 // the box-tiled streaming step (stream.cu): thin steps with K * N <= TN_BOX_MAXKN, N <= TN_BOX_MAXN
-#define TN_BOX_MAXKN 2048
+#define TN_BOX_MAXKN 4096
 #define TN_BOX_MAXN 256
 #define TN_BOX_ROWS_ELEMS 4096   // box_tm * (K + N) at most (shared memory of one tile)
 template <typename R>

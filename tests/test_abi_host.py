@@ -279,6 +279,81 @@ def _structural_dims(w, chi=None):
     return n, edges, kd, bd
 
 
+def _joined_steps(order, edges, dims, layer):
+    """Joining partial paths restated from its definition (no cuts): walking the path, two
+    consecutive nodes u, v of the same layer that share exactly one edge a are contracted with each
+    other first and absorbed as one node when that lowers both the step's complex multiply-adds
+    (the pair's own contraction counted for bra pairs, which are per bitstring) and the elements
+    read and written, neither rising. Returns the (M, K, N) of the steps of the joined path and the
+    pairs' own contraction costs (every pair, both layers)."""
+    legs = {v: set() for v in range(len(layer))}
+    for i, (u, v) in enumerate(edges):
+        legs[u].add(i)
+        legs[v].add(i)
+
+    def D(S):
+        return int(np.prod([dims[e] for e in S])) if S else 1
+
+    order, O, j, pairs = list(order), set(), 0, []
+    while j < len(order) - 1:
+        u, v = order[j], order[j + 1]
+        sh = legs[u] & legs[v]
+        if layer[u] == layer[v] and len(sh) == 1:
+            a = next(iter(sh))
+            K1, N1, R1 = legs[u] & O, legs[u] - O, O - legs[u]
+            O1 = R1 | N1
+            K2, N2, R2 = legs[v] & O1, legs[v] - O1, O1 - legs[v]
+            first = j == 0
+            seq_mac = (0 if first else D(R1) * D(K1) * D(N1)) + D(R2) * D(K2) * D(N2)
+            seq_el = (0 if first else D(R1) * (D(K1) + D(N1))) + D(R2) * (D(K2) + D(N2))
+            Lw = (legs[u] | legs[v]) - {a}
+            Kw, Nw, Rw = Lw & O, Lw - O, O - Lw
+            pair = D(legs[u] | legs[v])
+            w_mac = (0 if first else D(Rw) * D(Kw) * D(Nw)) + (pair if layer[u] == 2 else 0)
+            w_el = 0 if first else D(Rw) * (D(Kw) + D(Nw))
+            if w_mac <= seq_mac and w_el <= seq_el and (w_mac < seq_mac or w_el < seq_el):
+                pairs.append(pair)
+                legs[u], legs[v] = Lw, set()
+                order.pop(j + 1)
+                continue
+        L = legs[order[j]]
+        O = (O - L) | (L - O)
+        j += 1
+    O, steps = set(), []
+    for u in order:
+        L = legs[u]
+        K, N, R = L & O, L - O, O - L
+        steps.append((D(R), D(K), D(N)))
+        O = R | N
+    return steps, pairs
+
+
+def test_joined_paths_beat_the_best_main_path(tn):
+    """Joining partial paths (the relaxation of Assumption 3 in the supplement) on the double-layer
+    network of a 2x4 grid circuit: the joined plan costs fewer complex multiply-adds per amplitude,
+    every pair's own contraction counted in full, than the best single main path over all orders
+    (Eq. optscore, the oracle's subset recursion), which is what Algorithm 1 finds unconstrained.
+    The library's joined plan has the steps of the join restated on its order."""
+    g = gen.grid(2, 4)
+    n = g.n
+    gates = gen.rqc(g, 4, gen.rng(3, 1))
+    w = gen.Workload("g8", g, gates, 4, 2, 0, 1e-12, gen.bitstrings(n, 1, gen.rng(3, 2)))
+    _, edges, kd, bd = _structural_dims(w)
+    e2 = edges + [(n + u, n + v) for u, v in edges] + [(q, n + q) for q in range(n)]
+    d2 = [int(x) for x in list(kd) + list(bd)] + [2] * n
+    order, cuts, plain = tn.tn_cut_search(2 * n, e2, [float(x) for x in d2])
+    assert len(cuts) == 0
+    best_main = opath.subset_dp_optimum(2 * n, e2, d2)
+    assert plain == best_main
+    steps, pairs = _joined_steps([int(v) for v in order], e2, d2, [1] * n + [2] * n)
+    total = sum(m * k * nn for m, k, nn in steps[1:]) + sum(pairs)
+    assert pairs and total < best_main
+    c = tn.tn_build(n, g.edges, gates, allocator=None)
+    info = tn.tn_plan_estimate(c, 2, 0, 1e-12, layers=2)
+    assert info["n_steps"] == len(steps) - 1
+    assert info["cmacs"] == pytest.approx(sum(m * k * nn for m, k, nn in steps[1:]), rel=1e-12)
+
+
 @pytest.mark.parametrize("name", ["grid12", "syc53"])
 def test_plan_estimate_matches_the_oracle_structure(tn, name):
     """The host-only plan estimate (no device) builds the gate programs with the library's own
@@ -296,13 +371,20 @@ def test_plan_estimate_matches_the_oracle_structure(tn, name):
     flat = tn.tn_plan_estimate(c, w.split, w.chi, w.cutoff, merge=False)
     _, cuts1, total1 = tn.tn_cut_search(n, edges, [a * b for a, b in zip(kd, bd)])
     assert flat["n_nodes"] == n and flat["cmacs"] == pytest.approx(total1, rel=1e-12)
-    dl = tn.tn_plan_estimate(c, w.split, w.chi, w.cutoff, layers=2)
+    dl = tn.tn_plan_estimate(c, w.split, w.chi, w.cutoff, layers=2, merge=False)
     e2 = edges + [(n + u, n + v) for u, v in edges] + [(q, n + q) for q in range(n)]
     d2 = [float(x) for x in list(kd) + list(bd) + [2] * n]
-    _, cuts2, total2 = tn.tn_cut_search(2 * n, e2, d2)
+    order2, cuts2, total2 = tn.tn_cut_search(2 * n, e2, d2)
     assert dl["n_nodes"] == 2 * n and dl["n_steps"] == 2 * n - 1 and dl["n_cuts"] == len(cuts2)
     assert dl["cmacs"] == pytest.approx(total2, rel=1e-12)
     assert dl["cmacs"] < merged["cmacs"]
+    # the joined double-layer plan (default): the steps of the join restated on the same order
+    joined = tn.tn_plan_estimate(c, w.split, w.chi, w.cutoff, layers=2)
+    steps, _ = _joined_steps([int(v) for v in order2], e2, [int(x) for x in d2], [1] * n + [2] * n)
+    assert joined["n_steps"] == len(steps) - 1 < dl["n_steps"]
+    assert joined["cmacs"] == pytest.approx(sum(m * k * nn for m, k, nn in steps[1:]), rel=1e-12)
+    assert joined["bytes_c64"] == pytest.approx(sum(8 * (m * k + m * nn) for m, k, nn in steps[1:]), rel=1e-12)
+    assert joined["cmacs"] < dl["cmacs"] and joined["bytes_c64"] < dl["bytes_c64"]
 
 
 def test_double_layer_plans_with_cuts_and_every_split(tn):
@@ -311,10 +393,14 @@ def test_double_layer_plans_with_cuts_and_every_split(tn):
     w = gen.workload("grid12", n_bits=1)
     c = tn.tn_build(w.graph.n, w.graph.edges, w.gates, allocator=None)
     for split in range(0, w.depth + 1):
-        info = tn.tn_plan_estimate(c, split, 0, 1e-12, layers=2)
+        info = tn.tn_plan_estimate(c, split, 0, 1e-12, layers=2, merge=False)
         assert info["n_steps"] == 2 * w.graph.n - 1
-    cut = tn.tn_plan_estimate(c, 4, 0, 1e-12, layers=2, max_intermediate=64)
-    assert cut["n_cuts"] > 0 and cut["n_slices"] > 1 and cut["max_intermediate"] <= 64
+        joined = tn.tn_plan_estimate(c, split, 0, 1e-12, layers=2)
+        assert joined["n_steps"] < info["n_steps"] and joined["cmacs"] <= info["cmacs"]
+        assert joined["max_intermediate"] <= info["max_intermediate"]
+    for merge in (False, True):
+        cut = tn.tn_plan_estimate(c, 4, 0, 1e-12, layers=2, max_intermediate=64, merge=merge)
+        assert cut["n_cuts"] > 0 and cut["n_slices"] > 1 and cut["max_intermediate"] <= 64
     with pytest.raises(tn.TNError) as e:
         tn.tn_plan_estimate(c, 4, 0, 1e-12, layers=2, cut_edges=[0])
     assert e.value.status == tn.TN_ERR_UNSUPPORTED
@@ -334,10 +420,11 @@ def test_double_layer_network_of_the_104_qubit_grid(tn):
     w = gen.workload("syc104", n_bits=1)
     n, edges, kd, bd = _structural_dims(w)
     c = tn.tn_build(w.graph.n, w.graph.edges, w.gates, allocator=None)
-    dl = tn.tn_plan_estimate(c, w.split, w.chi, w.cutoff, layers=2)
+    dl = tn.tn_plan_estimate(c, w.split, w.chi, w.cutoff, layers=2, merge=False)
     e2 = edges + [(n + u, n + v) for u, v in edges] + [(q, n + q) for q in range(n)]
     d2 = [float(x) for x in list(kd) + list(bd) + [2] * n]
     order2, cuts2, total2 = tn.tn_cut_search(2 * n, e2, d2)
+    assert tn.tn_plan_estimate(c, w.split, w.chi, w.cutoff, layers=2)["cmacs"] < dl["cmacs"]
     assert dl["n_nodes"] == 2 * n == 208 and dl["n_steps"] == 207 and dl["n_cuts"] == len(cuts2) == 0
     assert sorted(int(v) for v in order2) == list(range(2 * n))
     assert total2 == pytest.approx(opath.score([int(v) for v in order2], e2, d2), rel=1e-12)

@@ -1,6 +1,6 @@
 """The box-tiled streaming step kernel (SIMT, thin steps) on the device, through the C ABI.
 
-Every step that the kernel supports (K * N <= 2048, N <= 256) is forced onto it, the others keep
+Every step that the kernel supports (K * N <= 4096, N <= 256) is forced onto it, the others keep
 the shape heuristic's kernels, and the amplitudes are compared element by element with what
 does not depend on the CUDA path: the brute-force state vector (untruncated 3x4 and 4x5 grids)
 and the oracle's own contraction of the double-layer network (the 53-qubit workload, truncated).
@@ -16,7 +16,7 @@ from tests.gpu_common import FP64_TOL, TC_TOL, rel_err
 
 pytestmark = pytest.mark.gpu
 
-BOX_MAXKN, BOX_MAXN = 2048, 256
+BOX_MAXKN, BOX_MAXN = 4096, 256
 
 
 @pytest.fixture(scope="module")
@@ -45,9 +45,10 @@ def test_box_grid12_vs_statevector(tn, layers, prec, tol):
     ref = sv.amplitudes(sv.run(12, w.gates), w.bits)
     c = tn.tn_build(12, w.graph.edges, w.gates)
     tn.tn_evolve_two_sided(c, w.split, 0, 1e-12)
-    p = tn.tn_path(c, layers=layers)
-    assert force_box(tn, p, prec) >= (20 if layers == 2 else 1)
-    assert rel_err(tn.tn_amplitudes(p, w.bits, prec), ref) < tol
+    for merge in (False, True):
+        p = tn.tn_path(c, layers=layers, merge=merge)
+        assert force_box(tn, p, prec) >= (20 if layers == 2 and not merge else 1)
+        assert rel_err(tn.tn_amplitudes(p, w.bits, prec), ref) < tol, merge
 
 
 @pytest.mark.parametrize("prec,tol", [("fp64", FP64_TOL), ("fp32", TC_TOL)])
@@ -88,15 +89,20 @@ def syc53_double_layer_oracle():
     return w, ref
 
 
+@pytest.mark.parametrize("merge", [False, True])
 @pytest.mark.parametrize("mode", ["box", "autotuned"])
-def test_syc53_double_layer_vs_oracle_double_layer(tn, syc53_double_layer_oracle, mode):
+def test_syc53_double_layer_vs_oracle_double_layer(tn, syc53_double_layer_oracle, mode, merge):
+    """merge=False: one step per ket or bra tensor (every step on the box kernel); merge=True (the
+    default): consecutive tensors of one layer joined first (the pair contracted on its own, in FP64)."""
     w, ref = syc53_double_layer_oracle
     c = tn.tn_build(w.graph.n, w.graph.edges, w.gates)
     tn.tn_evolve_two_sided(c, w.split, w.chi, w.cutoff)
-    p = tn.tn_path(c, layers=2)
+    p = tn.tn_path(c, layers=2, merge=merge)
+    assert (p.info["n_nodes"] == 2 * w.graph.n) == (not merge)
     for prec, tol in (("fp64", FP64_TOL), ("fp32", TC_TOL)):
         if mode == "box":
-            assert force_box(tn, p, prec) == p.info["n_steps"]
+            nb = force_box(tn, p, prec)
+            assert nb == p.info["n_steps"] if not merge else nb >= p.info["n_steps"] - 2
         else:
             tn.tn_autotune(p, prec, 256)
         assert rel_err(tn.tn_amplitudes(p, w.bits, prec), ref) < tol, prec

@@ -42,23 +42,27 @@ def test_capped_haar_grid_matches_the_oracle_in_each_compression(tn, compress):
     assert rel_err(a, ref) < FP64_TOL
 
 
+@pytest.mark.parametrize("merge", [False, True])
 @pytest.mark.parametrize("prec,tol", [("fp64", FP64_TOL), ("fp32", TC_TOL)])
-def test_double_layer_grid12_vs_statevector(tn, prec, tol):
+def test_double_layer_grid12_vs_statevector(tn, prec, tol, merge):
+    """merge=False: one node per ket and per bra tensor; merge=True (default): consecutive
+    tensors of one layer joined (contracted with each other first, in FP64) where that is cheaper."""
     w = gen.workload("grid12", n_bits=32)
     ref = sv.amplitudes(sv.run(12, w.gates), w.bits)
     c = tn.tn_build(12, w.graph.edges, w.gates)
     tn.tn_evolve_two_sided(c, w.split, 0, 1e-12)
-    p = tn.tn_path(c, layers=2)
-    assert p.info["n_steps"] == 23
+    p = tn.tn_path(c, layers=2, merge=merge)
+    assert (p.info["n_steps"] == 23) == (not merge)
     assert rel_err(tn.tn_amplitudes(p, w.bits, prec), ref) < tol
 
 
+@pytest.mark.parametrize("merge", [False, True])
 @pytest.mark.parametrize("prec,tol", [("fp64", FP64_TOL), ("fp32", TC_TOL)])
-def test_double_layer_syc53_vs_overlap_network(tn, prec, tol):
+def test_double_layer_syc53_vs_overlap_network(tn, prec, tol, merge):
     w = gen.workload("syc53", n_bits=64)
     c = tn.tn_build(w.graph.n, w.graph.edges, w.gates)
     tn.tn_evolve_two_sided(c, w.split, w.chi, w.cutoff)
     a64 = tn.tn_amplitudes(tn.tn_path(c), w.bits, "fp64")
-    p = tn.tn_path(c, layers=2)
-    assert p.info["n_nodes"] == 2 * w.graph.n
+    p = tn.tn_path(c, layers=2, merge=merge)
+    assert (p.info["n_nodes"] == 2 * w.graph.n) == (not merge)
     assert rel_err(tn.tn_amplitudes(p, w.bits, prec), a64) < tol
