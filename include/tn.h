@@ -223,8 +223,13 @@ tn_status tn_circuit_bond_dims(const tn_circuit *c, int32_t side, int32_t *out);
  * e (ket bond of circuit edge e), n_edges + e (its bra bond) and 2 n_edges + q (qubit q's
  * physical index). The sums are those of Eq. overlap without forming the per-qubit overlap
  * tensors first, so the amplitudes are the same; each step absorbs one ket tensor (the same for
- * every bitstring) or one bra tensor. No merging; explicit cut_edges are not accepted
- * (TN_ERR_UNSUPPORTED); automatic cuts are. The path search holds at most 256 nodes, so the
+ * every bitstring) or one bra tensor. Unless opts->no_merge, partial paths are then joined
+ * (supplement, the discussion of Assumption 3): where the path absorbs two tensors of the same
+ * layer in a row that share one edge not cut, the pair is contracted with each other first
+ * (exactly, in FP64: ket pairs once per batch, bra pairs per bitstring) and absorbed in one step,
+ * when that lowers both the complex multiply-adds and the elements the steps read and write; the
+ * amplitudes are the same sums grouped otherwise and no intermediate grows. Explicit cut_edges
+ * are not accepted (TN_ERR_UNSUPPORTED); automatic cuts are. The path search holds at most 256 nodes, so the
  * double-layer network takes every circuit tn_build accepts (at most 128 qubits).
  * Errors: TN_ERR_STATE, TN_ERR_NO_PATH, TN_ERR_ARG, TN_ERR_CUDA, TN_ERR_OOM, TN_ERR_UNSUPPORTED. */
 tn_status tn_path(tn_circuit *c, const tn_path_opts *opts, tn_plan **out, tn_plan_info *info);
@@ -265,7 +270,8 @@ tn_status tn_plan_inspect(const tn_circuit *c, int32_t split_cycle, int32_t chi_
 
 /* Plan details: order[max(n_qubits, n_nodes)] (contraction order of the network's nodes,
  * each named by its representative qubit, then -1 for the merged qubits; for a double-layer
- * plan the 2 n_qubits node ids), cuts[n_cuts] (circuit edge ids; network edge ids for a
+ * plan its n_nodes node ids, q for qubit q's ket tensor and n_qubits + q for its bra tensor, a
+ * joined node named by its first tensor), cuts[n_cuts] (circuit edge ids; network edge ids for a
  * double-layer plan), steps[3*n_steps] = (M, K, N) per step per slice.
  * Any pointer may be NULL. */
 tn_status tn_plan_details(const tn_plan *p, int32_t *order, int32_t *cuts, int64_t *steps);
