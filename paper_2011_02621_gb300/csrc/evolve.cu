@@ -176,6 +176,59 @@ __global__ void __launch_bounds__(GATE_THREADS) gate_kernel(GateParams g, double
     if (tid == 0) s_rot = 0;
     item_sync<TPI>();
     for (int rd = 0; rd < rounds; ++rd) {
+      if constexpr (TPI == 32) {
+        // one warp per item: the round's column pairs (disjoint columns) side by side, LP lanes
+        // per pair, each lane summing rows r = sub, sub + LP, ... and the pair's lanes reducing
+        // with shuffles inside their aligned LP-lane segment
+        const int npairs = Cp / 2;
+        int LP = 32;
+        while (LP > 1 && LP * npairs > 32) LP >>= 1;
+        const int sub = lane & (LP - 1), slot = lane / LP;
+        for (int pi0 = 0; pi0 < npairs; pi0 += 32 / LP) {
+          const int pi = pi0 + slot;
+          int p = 0, q = 0;
+          if (pi == 0) { p = rd; q = Cp - 1; }
+          else { p = (rd + pi) % (Cp - 1); q = (rd - pi + (Cp - 1)) % (Cp - 1); }
+          const bool act = pi < npairs && p < C && q < C;
+          double2 *yp = Y + (int64_t)p * R, *yq = Y + (int64_t)q * R;
+          double al = 0, be = 0, gr = 0, gi = 0;
+          if (act) {
+            for (int r = sub; r < R; r += LP) {
+              double2 a = yp[r], b = yq[r];
+              al = fma(a.x, a.x, fma(a.y, a.y, al));
+              be = fma(b.x, b.x, fma(b.y, b.y, be));
+              gr = fma(a.x, b.x, fma(a.y, b.y, gr));    // conj(a) * b
+              gi = fma(a.x, b.y, fma(-a.y, b.x, gi));
+            }
+          }
+          for (int o = LP >> 1; o; o >>= 1) {
+            al += __shfl_xor_sync(0xffffffffu, al, o);
+            be += __shfl_xor_sync(0xffffffffu, be, o);
+            gr += __shfl_xor_sync(0xffffffffu, gr, o);
+            gi += __shfl_xor_sync(0xffffffffu, gi, o);
+          }
+          if (!act) continue;
+          const double ga = sqrt(gr * gr + gi * gi);
+          const double nab = sqrt(al * be);
+          if (!(ga > tol * nab) || nab <= floor_ab || ga == 0.0 || fmin(al, be) <= floor_col) continue;
+          const double zeta = (be - al) / (2.0 * ga);
+          const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
+          const double2 e = make_double2(gr / ga, -gi / ga);       // conj(gamma)/|gamma|
+          for (int r = sub; r < R; r += LP) {
+            double2 a = yp[r], b = cmul(yq[r], e);
+            yp[r] = make_double2(cs * a.x - sn * b.x, cs * a.y - sn * b.y);
+            yq[r] = make_double2(sn * a.x + cs * b.x, sn * a.y + cs * b.y);
+          }
+          double2 *wp = W + (int64_t)p * C, *wq = W + (int64_t)q * C;
+          for (int r = sub; r < C; r += LP) {
+            double2 a = wp[r], b = cmul(wq[r], e);
+            wp[r] = make_double2(cs * a.x - sn * b.x, cs * a.y - sn * b.y);
+            wq[r] = make_double2(sn * a.x + cs * b.x, sn * a.y + cs * b.y);
+          }
+          if (sub == 0 && ga > 8.0 * tol * nab) s_rot = 1;
+        }
+      } else {
       for (int pi = warp; pi < Cp / 2; pi += nwarp) {
         int p, q;
         if (pi == 0) { p = rd; q = Cp - 1; }
@@ -215,6 +268,7 @@ __global__ void __launch_bounds__(GATE_THREADS) gate_kernel(GateParams g, double
           wq[r] = make_double2(sn * a.x + cs * b.x, sn * a.y + cs * b.y);
         }
         if (lane == 0 && ga > 8.0 * tol * nab) s_rot = 1;
+      }
       }
       item_sync<TPI>();
     }

@@ -1913,8 +1913,8 @@ static tn_status compile_plan(tn_plan *p) {
     if (j > 0 && K * N <= TN_BOX_MAXKN && N <= TN_BOX_MAXN) {
       // Row tiles of the box-tiled streaming kernel: the trailing rest digits (fastest first),
       // the last one taken in part (a divisor of its dim), so that m = t * tm + r splits the
-      // digits of m and orow(m) = orow(t * tm) + orow(r); at most TN_BOX_ROWS_ELEMS / (K + N) rows.
-      const int64_t lim = std::max<int64_t>(1, TN_BOX_ROWS_ELEMS / (K + N));
+      // digits of m and orow(m) = orow(t * tm) + orow(r); at most TN_BOX_ROWS_ELEMS / (2 K + N) rows.
+      const int64_t lim = std::max<int64_t>(1, TN_BOX_ROWS_ELEMS / (2 * K + N));
       int64_t tm = 1;
       for (int r = s.n_rest - 1; r >= 0; --r) {
         const int64_t d = s.rest_dim[r];

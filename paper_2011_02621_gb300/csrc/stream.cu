@@ -10,8 +10,8 @@
 // out for that roof:
 //  * a CTA works on one item: it builds C in shared memory once, then walks row tiles of box_tm
 //    rows whose input is one contiguous block of box_tm * K complex values, copied with 16-byte
-//    cp.async while the previous tile's outputs are being written;
-//  * each thread computes a row's group of TN consecutive columns from shared memory;
+//    cp.async into one of two buffers while the previous tile is computed and written;
+//  * each thread computes two rows' group of TN consecutive columns from shared memory;
 //  * the tile's outputs go out in increasing output offset (a table the plan compiler sorts), so
 //    that the permuted layout of the next step is written with full, coalesced sectors.
 #include <cuda_runtime.h>
@@ -35,12 +35,14 @@ __device__ __forceinline__ void cp_async8(void *smem, const void *g) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
-// Shared memory of one CTA: C[K][N], the input tile [tm][kp], the output tile [tm][np] (rows
-// padded against bank conflicts), the tile's local output row offsets and the column offsets.
+// Shared memory of one CTA: C[K][N], two input tile buffers [tm][kp] (the next tile is copied in
+// while the current one is used), the output tile [tm][np] (rows padded against bank conflicts),
+// the tile's local output row offsets and the column offsets.
 struct BoxLayout {
   int kp, np;
-  size_t c_off, in_off, out_off, orow_off, ocol_off, bytes;
+  size_t c_off, in_off, in_size, out_off, orow_off, ocol_off, bytes;
 };
 
 __host__ __device__ inline size_t box_align16(size_t x) { return (x + 15) & ~(size_t)15; }
@@ -57,7 +59,8 @@ __host__ __device__ inline BoxLayout box_layout(int tm, int K, int N) {
   }
   L.c_off = 0;
   L.in_off = box_align16(L.c_off + (size_t)K * N * sizeof(V));
-  L.out_off = box_align16(L.in_off + (size_t)tm * L.kp * sizeof(V));
+  L.in_size = box_align16((size_t)tm * L.kp * sizeof(V));      // one of the two input tile buffers
+  L.out_off = L.in_off + 2 * L.in_size;
   L.orow_off = box_align16(L.out_off + (size_t)tm * L.np * sizeof(V));
   L.ocol_off = L.orow_off + (size_t)tm * sizeof(int);
   L.bytes = box_align16(L.ocol_off + (size_t)N * sizeof(int));
@@ -91,7 +94,8 @@ step_box_kernel(StepParams s, ContractArgs a, const typename BoxT<R>::V *ket, co
   const int TM = s.box_tm, K = (int)s.K, N = (int)s.N;
   const BoxLayout L = box_layout<V>(TM, K, N);
   V *Cs = reinterpret_cast<V *>(box_raw + L.c_off);
-  V *Ins = reinterpret_cast<V *>(box_raw + L.in_off);
+  V *const Ins0 = reinterpret_cast<V *>(box_raw + L.in_off);
+  V *const Ins1 = reinterpret_cast<V *>(box_raw + L.in_off + L.in_size);
   V *Outs = reinterpret_cast<V *>(box_raw + L.out_off);
   int *orow_s = reinterpret_cast<int *>(box_raw + L.orow_off);
   int *ocol_s = reinterpret_cast<int *>(box_raw + L.ocol_off);
@@ -106,9 +110,10 @@ step_box_kernel(StepParams s, ContractArgs a, const typename BoxT<R>::V *ket, co
   const bool k_pow2 = (K & (K - 1)) == 0;
   const int k_log = __ffs(K) - 1;
 
-  // the input tile t: box_tm rows of K values, contiguous at t * box_tm * K
+  // the input tile t: box_tm rows of K values, contiguous at t * box_tm * K, into buffer t & 1
   auto load = [&](int64_t t) {
     const V *src = tp + t * (int64_t)TM * K;
+    V *const Ins = (t & 1) ? Ins1 : Ins0;
     if (sizeof(V) == 8 && K % 2 == 0) {
       const int n2 = TM * K / 2, kh = K / 2;
       for (int e = tid; e < n2; e += 256) {
@@ -144,29 +149,47 @@ step_box_kernel(StepParams s, ContractArgs a, const typename BoxT<R>::V *ket, co
   const int g = tid % G, r0 = tid / G;
   const uint32_t *wperm = reinterpret_cast<const uint32_t *>(a.tab + s.t_wperm);
   for (int64_t t = t_begin; t < t_end; ++t) {
-    cp_async_wait_all();
+    // the next tile's copy runs while this tile is computed and written (its buffer was last read
+    // by the compute of tile t - 1, which every thread finished before the barrier below it)
+    if (t + 1 < t_end) {
+      load(t + 1);
+      cp_async_wait_one();
+    } else {
+      cp_async_wait_all();
+    }
     __syncthreads();                    // input tile t and C in place; the last tile's outputs written
+    const V *const Ins = (t & 1) ? Ins1 : Ins0;
     if (r0 < RP) {
-      for (int r = r0; r < TM; r += RP) {
-        V acc[TN];
+      // two rows per pass (r and r + RP) against the same C entries
+      for (int r = r0; r < TM; r += 2 * RP) {
+        const bool two = r + RP < TM;
+        V acc0[TN], acc1[TN];
 #pragma unroll
-        for (int j = 0; j < TN; ++j) acc[j] = cz<V>();
-        const V *xr = Ins + r * L.kp;
+        for (int j = 0; j < TN; ++j) acc0[j] = acc1[j] = cz<V>();
+        const V *xr0 = Ins + r * L.kp;
+        const V *xr1 = two ? xr0 + RP * L.kp : xr0;
         const V *cc = Cs + g * TN;
         for (int k = 0; k < K; ++k) {
-          const V x = xr[k];
+          const V x0 = xr0[k], x1 = xr1[k];
           V cv[TN];
           load_c<TN>(cc + k * N, cv);
 #pragma unroll
-          for (int j = 0; j < TN; ++j) acc[j] = cfma(x, cv[j], acc[j]);
+          for (int j = 0; j < TN; ++j) {
+            acc0[j] = cfma(x0, cv[j], acc0[j]);
+            acc1[j] = cfma(x1, cv[j], acc1[j]);
+          }
         }
         V *o = Outs + r * L.np + g * TN;
 #pragma unroll
-        for (int j = 0; j < TN; ++j) o[j] = acc[j];
+        for (int j = 0; j < TN; ++j) o[j] = acc0[j];
+        if (two) {
+          o += RP * L.np;
+#pragma unroll
+          for (int j = 0; j < TN; ++j) o[j] = acc1[j];
+        }
       }
     }
-    __syncthreads();                    // output tile complete; the input tile may be replaced
-    if (t + 1 < t_end) load(t + 1);
+    __syncthreads();                    // output tile complete
     const int obase = orow_of(s, t * (int64_t)TM);
     for (int e = tid; e < TM * N; e += 256) {
       const uint32_t pr = __ldg(wperm + e);

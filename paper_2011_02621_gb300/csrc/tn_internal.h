@@ -138,7 +138,7 @@ bool simt_variant_ok(const StepParams &s, int variant);
 // the box-tiled streaming step (stream.cu): thin steps with K * N <= TN_BOX_MAXKN, N <= TN_BOX_MAXN
 #define TN_BOX_MAXKN 4096
 #define TN_BOX_MAXN 256
-#define TN_BOX_ROWS_ELEMS 4096   // box_tm * (K + N) at most (shared memory of one tile)
+#define TN_BOX_ROWS_ELEMS 6144   // box_tm * (2 K + N) at most (two input tiles and one output tile)
 template <typename R>
 cudaError_t launch_step_box(const StepParams &s, const ContractArgs &a, const void *ket, const void *bra,
                             const void *t_in, const OutDesc &out, cudaStream_t st);
