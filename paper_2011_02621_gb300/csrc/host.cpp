@@ -2385,7 +2385,7 @@ bool step_kernel_ok(const StepParams &s, tn_precision prec, int k) {
   if (k == SK_TC) return prec != TN_FP64 && prec != TN_FP32 && prec != TN_BF16X6 && tc_step_supported(s);
   if (!sk_is_tma(k)) return false;
   if (prec != TN_BF16X6 || !tma_step_supported(s)) return false;
-  return sk_tma_bn(k) != 128 || 2 * s.N >= 128;
+  return sk_tma_bn(k) != 128 || (2 * s.N >= 128 && s.K < TN_TMA_LONG_K);
 }
 
 // The tuned kernels of the plan for this precision, else the shape heuristic: TMA-fed tcgen05 for

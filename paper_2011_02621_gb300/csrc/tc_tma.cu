@@ -513,7 +513,7 @@ bool tma_step_supported(const StepParams &s) {
 cudaError_t launch_step_tma(const StepParams &s, const ContractArgs &a, const Pieces &A, const Pieces &B,
                             const OutDesc &out, int *err, cudaStream_t st, int bn, const float2 *ket,
                             const float2 *bra, const float2 *cbuf, int64_t c_stride) {
-  if (bn == 0) bn = 2 * s.N >= 128 ? 128 : 64;
+  if (bn == 0) bn = (2 * s.N >= 128 && s.K < TN_TMA_LONG_K) ? 128 : 64;
   const int bm = cbuf ? 2 : ket ? 1 : 0;
   if (bm == 1 && !bra) return cudaErrorInvalidValue;
 #define TN_TMA_LAUNCH(BNV, RV, SV)                                                                     \
@@ -522,7 +522,7 @@ cudaError_t launch_step_tma(const StepParams &s, const ContractArgs &a, const Pi
     case 1: return launch_t<BNV, RV, SV, 1>(s, a, A, B, out, err, ket, bra, cbuf, c_stride, st);       \
     default: return launch_t<BNV, RV, SV, 2>(s, a, A, B, out, err, ket, bra, cbuf, c_stride, st);      \
   }
-  if (bn == 128 && 2 * s.N >= 128) { TN_TMA_LAUNCH(128, 3, 2) }
+  if (bn == 128 && 2 * s.N >= 128 && s.K < TN_TMA_LONG_K) { TN_TMA_LAUNCH(128, 3, 2) }
   if (bn == 64) { TN_TMA_LAUNCH(64, 7, 3) }
 #undef TN_TMA_LAUNCH
   return cudaErrorInvalidValue;

@@ -166,6 +166,13 @@ cudaError_t launch_step_tma(const StepParams &s, const ContractArgs &a, const Pi
                             const OutDesc &out, int *err, cudaStream_t st, int bn = 0, const float2 *ket = nullptr,
                             const float2 *bra = nullptr, const float2 *cbuf = nullptr, int64_t c_stride = 0);
 bool tma_step_supported(const StepParams &s);
+// Long contractions on the TMA-fed BF16x6 step take 64-column tiles: the tensor core adds its
+// products into an FP32 accumulator with truncation, so the error grows with the number of MMAs
+// summed into one accumulator; a 64-column tile spreads the order-0 products over 7 TMEM
+// accumulators instead of 3 (measured relative to rms |a| against FP64: the 4x5 grid at 14 cycles,
+// K up to 4096, 8.7e-6 -> 4.9e-6; the 53-qubit overlap network, K = 256, up to 1.05e-5 on 128-column
+// tiles, above the 1e-5 the amplitudes must meet).
+#define TN_TMA_LONG_K 256
 
 // launch accounting
 void tn_count_launch(int64_t k);

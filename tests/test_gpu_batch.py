@@ -166,11 +166,9 @@ def test_autotune_keeps_results(tn, name, n_bits, prec, tol):
     assert all(not k.isdigit() for k in chosen)
     a1 = tn.tn_amplitudes(p, w.bits, prec)
     if prec == "bf16x6":
-        # the amplitudes/s metric counts an amplitude when it is within 1e-5 of FP64
-        rms = np.sqrt(np.mean(np.abs(ref) ** 2))
+        # every amplitude within 1e-5 of FP64, with the heuristic's kernels and the tuned ones
         for a in (a0, a1):
-            r = np.abs(a - ref) / rms
-            assert np.mean(r <= tol) >= 0.99 and r.max() < 2 * tol
+            assert rel_err(a, ref) < tol
         assert any(k.startswith("tcgen05") for k in chosen)
     else:
         assert rel_err(a1, ref) < tol
@@ -203,7 +201,7 @@ def test_tma_built_operand_equals_loaded_operand(tn, name, n_bits, opts):
         for mode in modes[1:]:
             assert np.array_equal(results[(modes[0], bn)], results[(mode, bn)]), (mode, bn)
     ref = tn.tn_amplitudes(p, w.bits, "fp64")
-    tol = TC_TOL if name == "syc53" else 5e-5
+    tol = TC_TOL
     for v in results.values():
         assert rel_err(v, ref) < tol
     with pytest.raises(tn.TNError):

@@ -238,8 +238,9 @@ def test_tensor_core_syc53_vs_oracle_and_fp64(tn):
 
 def test_tensor_core_cuts_and_ragged_tiles(tn):
     """Slices, M not a multiple of 128 and N not a multiple of the tile on the tcgen05 paths, on
-    the deep 14-cycle circuit: FP32 SIMT, BF16x6 and TF32x6 within bounds set from their measured
-    errors here (2.8e-6, ~1e-5 and 2.2e-5 on this plan)."""
+    the deep 14-cycle circuit: FP32 SIMT and BF16x6 within 1e-5 (the tensor-core path's tolerance;
+    BF16x6 steps with K >= 256 run on 64-column tiles, 7 order-0 accumulators), TF32x6 within its
+    form's bound (products of 21-bit pieces, accumulated in FP32 by the tensor core)."""
     w = gen.workload("grid20", n_bits=4)
     ref = statevector_amplitudes(20, w.gates, w.bits)
     c = tn.tn_build(20, w.graph.edges, w.gates)
@@ -247,7 +248,7 @@ def test_tensor_core_cuts_and_ragged_tiles(tn):
     p = tn.tn_path(c, max_intermediate=1 << 22)
     assert p.info["n_slices"] > 1
     assert rel_err(tn.tn_amplitudes(p, w.bits, "fp32"), ref) < 1e-5
-    for prec, bound in (("bf16x6", 2e-5), ("tf32x6", 4e-5)):
+    for prec, bound in (("bf16x6", TC_TOL), ("tf32x6", 4e-5)):
         assert rel_err(tn.tn_amplitudes(p, w.bits, prec), ref) < bound, prec
 
 
@@ -276,4 +277,4 @@ def test_node_merging_is_exact(tn, name, n_bits, opts):
     a_u = tn.tn_amplitudes(pu, w.bits, "fp64")
     assert rel_err(a_m, a_u) < 1e-12
     if name != "grid12":
-        assert rel_err(tn.tn_amplitudes(pm, w.bits, "bf16x6"), a_u) < (TC_TOL if name == "syc53" else 5e-5)
+        assert rel_err(tn.tn_amplitudes(pm, w.bits, "bf16x6"), a_u) < TC_TOL

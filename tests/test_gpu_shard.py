@@ -6,7 +6,7 @@ import pytest
 
 import gen
 from paper_2011_02621_gb300 import shard
-from tests.gpu_common import FP64_TOL, rel_err, statevector_amplitudes
+from tests.gpu_common import FP64_TOL, TC_TOL, rel_err, statevector_amplitudes
 
 pytestmark = pytest.mark.gpu
 
@@ -31,7 +31,7 @@ def grid20(tn):
     return w, c, p
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", FP64_TOL), ("bf16x6", 5e-5)])
+@pytest.mark.parametrize("prec,tol", [("fp64", FP64_TOL), ("bf16x6", TC_TOL)])
 def test_slice_blocks_sum_to_amplitudes(tn, grid20, prec, tol):
     w, c, p = grid20
     S = p.info["n_slices"]
