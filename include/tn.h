@@ -180,6 +180,13 @@ tn_status tn_evolve_two_sided(tn_circuit *c, int32_t split_cycle, int32_t chi_ma
 typedef enum { TN_COMPRESS_ONE_SIDED = 0, TN_COMPRESS_TWO_SIDED = 1 } tn_compress;
 tn_status tn_set_compression(tn_circuit *c, int32_t mode);
 
+/* Cap on the sweeps of the one-sided Jacobi SVD (Eqs. svd/svd2) of every compression of both
+ * halves: 1..1000, 0 = the default (60). A compression that has not converged within the cap sets
+ * the error word of its launch, and the call that ran it returns TN_ERR_TIMEOUT (the bounded
+ * loop ends; the context stays usable). Host only; takes effect at once for the bra half of later
+ * amplitude calls and for the next tn_evolve_two_sided. Errors: TN_ERR_ARG. */
+tn_status tn_set_svd_sweeps(tn_circuit *c, int32_t max_sweeps);
+
 /* Host-only inspection of the gate program of one half (side 0 = ket, 1 = bra) that
  * tn_evolve_two_sided(c, split_cycle, chi_max, cutoff_rel) builds with the circuit's
  * compression mode, from the structural bond bounds (no rank probe, no device work), for CPU
@@ -305,6 +312,8 @@ tn_status tn_amplitudes_slices(tn_plan *p, const uint64_t *bits, int64_t n, tn_p
  *  - The first call on a device looks up the array's device address (a CUDA runtime query,
  *    once per device, with that device current); make that first call before any stream
  *    capture begins.
+ *  - Call it with the plan's device current (the device its circuit was evolved on): the array
+ *    used is the current device's, so another current device is refused with TN_ERR_ARG.
  *  - Batches are sized to fit the array; a plan whose single bitstring and single slice need
  *    more than 32 MiB is rejected with TN_ERR_UNSUPPORTED (use tn_amplitudes, or plan with a
  *    smaller max_intermediate).
@@ -448,6 +457,7 @@ typedef struct {
   double p50_latency_s, p99_latency_s;   /* completion - submission, over completed requests */
   double max_inflight_seen;
   double peak_admitted_bytes;
+  int64_t cancelled;         /* requests removed from the queue by tn_server_cancel */
 } tn_server_stats;
 
 /* Create a server; its worker threads (min(max_inflight, n_streams) of them), each with its
@@ -467,6 +477,13 @@ tn_status tn_server_submit(tn_server *s, tn_plan *p, const uint64_t *bits, int64
 /* Wait for a ticket; timeout_ms < 0 waits forever. Returns the request's
  * own status, or TN_ERR_TIMEOUT if it has not completed in time. */
 tn_status tn_server_wait(tn_server *s, uint64_t ticket, int64_t timeout_ms);
+
+/* Cancel a request that is still queued (no worker has taken it): it is removed, its output is
+ * not written and its ticket is forgotten (a later tn_server_wait on it gives TN_ERR_ARG). The
+ * paper has no counterpart: this is the serving loop's request management. A request that is
+ * running or complete cannot be cancelled: TN_ERR_STATE (wait for it). Errors: TN_ERR_ARG
+ * (unknown ticket), TN_ERR_STATE. */
+tn_status tn_server_cancel(tn_server *s, uint64_t ticket);
 
 tn_status tn_server_stats_get(tn_server *s, tn_server_stats *st);
 

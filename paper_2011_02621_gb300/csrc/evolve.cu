@@ -6,6 +6,7 @@
 #include <math.h>
 
 #include "tn_internal.h"
+#include "tn_smem.h"
 
 namespace {
 
@@ -172,7 +173,8 @@ __global__ void __launch_bounds__(GATE_THREADS) gate_kernel(GateParams g, double
   const int Cp = (C + 1) & ~1;
   const int rounds = Cp - 1;
   bool converged = (C <= 1);
-  for (int sweep = 0; sweep < MAX_SWEEPS && !converged; ++sweep) {
+  const int sweep_cap = g.max_sweeps > 0 ? g.max_sweeps : MAX_SWEEPS;
+  for (int sweep = 0; sweep < sweep_cap && !converged; ++sweep) {
     if (tid == 0) s_rot = 0;
     item_sync<TPI>();
     for (int rd = 0; rd < rounds; ++rd) {
@@ -421,21 +423,6 @@ __global__ void copy_words_kernel(const uint64_t *src, uint64_t *dst, int64_t n)
 
 int64_t gate_work_elems(const GateParams &g) { return work_layout(g).total; }
 
-// Raise a kernel's dynamic shared memory limit to the most the device allows next to the kernel's
-// static shared memory, once (every later launch asks for at most that, so concurrent host
-// threads never lower it under one another).
-template <typename F>
-static cudaError_t allow_max_smem(F *kernel) {
-  int dev = 0, optin = 0;
-  cudaFuncAttributes fa;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kernel);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
-  return e;
-}
-
 cudaError_t launch_gate(const GateParams &g, double2 *base, int64_t item_stride, int items, double2 *gwork,
                         int *errflag, int *rank_out, cudaStream_t st) {
   if (items <= 0) return cudaSuccess;
@@ -445,16 +432,16 @@ cudaError_t launch_gate(const GateParams &g, double2 *base, int64_t item_stride,
   if (warp_per_item) {
     const size_t smem = 4 * (size_t)L.total * sizeof(double2);
     if (smem > 48 * 1024) {
-      static const cudaError_t e = allow_max_smem(gate_kernel<32>);
-      if (e != cudaSuccess) return e;
+      const int lim = tn_smem_optin<gate_kernel<32>>();
+      if (lim < 0 || (size_t)lim < smem) return cudaErrorInvalidValue;
     }
     gate_kernel<32><<<(items + 3) / 4, GATE_THREADS, smem, st>>>(g, base, item_stride, gwork, errflag, items,
                                                                  rank_out);
   } else {
     const size_t smem = g.use_smem ? (size_t)L.total * sizeof(double2) : 0;
     if (smem > 48 * 1024) {
-      static const cudaError_t e = allow_max_smem(gate_kernel<128>);
-      if (e != cudaSuccess) return e;
+      const int lim = tn_smem_optin<gate_kernel<128>>();
+      if (lim < 0 || (size_t)lim < smem) return cudaErrorInvalidValue;
     }
     gate_kernel<128><<<items, GATE_THREADS, smem, st>>>(g, base, item_stride, gwork, errflag, items, rank_out);
   }

@@ -408,6 +408,7 @@ static void build_half(const tn_circuit *c, const std::vector<const tn_gate *> &
   const int n = c->n;
   const bool two_sided = c->compress == TN_COMPRESS_TWO_SIDED;
   h = Half();
+  h.max_sweeps = c->max_sweeps;
   h.dims.assign(c->ne, 1);
   std::vector<M2> pend(n, M2{1, 0, 0, 1});
   std::vector<char> has(n, 0);
@@ -573,7 +574,8 @@ tn_status run_half(const Half &h, int n_qubits, double2 *base, int items, const 
   }
   for (const auto &op : h.seq) {
     if (op.first == 2) {
-      const GateParams &g = h.gp[op.second];
+      GateParams g = h.gp[op.second];
+      g.max_sweeps = h.max_sweeps;
       ProfScope ps("gate_svd_fp64", st, gate_bytes(g) * items, gate_flops(g) * items);
       CUDA_TRY(launch_gate(g, base, stride, items, gwork, errflag, rank_out_dev ? rank_out_dev + op.second : nullptr,
                            st));
@@ -2281,6 +2283,13 @@ extern "C" tn_status tn_program_inspect(const tn_circuit *c, int32_t split_cycle
   });
 }
 
+extern "C" tn_status tn_set_svd_sweeps(tn_circuit *c, int32_t max_sweeps) {
+  if (!c) return tn_fail(TN_ERR_ARG, "tn_set_svd_sweeps: NULL circuit");
+  if (max_sweeps < 0 || max_sweeps > 1000) return tn_fail(TN_ERR_ARG, "tn_set_svd_sweeps: %d outside [0, 1000]", max_sweeps);
+  c->max_sweeps = c->ket.max_sweeps = c->bra.max_sweeps = max_sweeps;
+  return TN_OK;
+}
+
 extern "C" tn_status tn_set_compression(tn_circuit *c, int32_t mode) {
   if (!c) return tn_fail(TN_ERR_ARG, "tn_set_compression: NULL circuit");
   if (mode != TN_COMPRESS_ONE_SIDED && mode != TN_COMPRESS_TWO_SIDED)
@@ -2309,6 +2318,10 @@ extern "C" tn_status tn_plan_details(const tn_plan *p, int32_t *order, int32_t *
 // tn_amplitudes
 // ---------------------------------------------------------------------------
 void ws_release(DevMem &mem, Workspace &w) {
+  if (w.fixed) {   // not the library's memory
+    w = Workspace();
+    return;
+  }
   mem.release(w.bits);
   mem.release(w.bra64);
   mem.release(w.bra32);
@@ -2364,6 +2377,12 @@ void ws_carve(Workspace &w, void *base, const WsSizes &z, int64_t ch, int64_t sc
 tn_status ws_ensure_sized(tn_plan *p, Workspace &w, int kind, int64_t ch, int64_t sc, cudaStream_t st) {
   DevMem &mem = p->c->mem;
   const WsSizes z = ws_sizes(p, kind, ch, sc);
+  if (w.fixed) {   // caller memory: it holds these sizes or the call is refused, never allocated
+    for (int i = 0; i < WS_NBUF; ++i)
+      if ((size_t)z.b[i] > ws_buf(w, i)->bytes)
+        return tn_fail(TN_ERR_OOM, "workspace in fixed memory is too small for %lld bitstrings", (long long)ch);
+    return TN_OK;
+  }
   for (int i = 0; i < WS_NBUF; ++i) {
     tn_status s = mem.ensure(*ws_buf(w, i), (size_t)z.b[i], st);
     if (s != TN_OK) return s;
@@ -2601,9 +2620,11 @@ tn_status run_amplitudes(tn_plan *p, Workspace &w, const uint64_t *bits, int64_t
   if (n == 0) return TN_OK;
   if (n < 0 || !bits || !out) return tn_fail(TN_ERR_ARG, "tn_amplitudes: bad arguments");
   const int kind = prec == TN_FP64 ? 0 : 1;
-  // buffers for min(n, chunk) bitstrings (they grow when a later call needs more)
-  tn_status s = ws_ensure_sized(p, w, kind, std::min<int64_t>(std::max<int64_t>(n, w.chunk), p->chunk[kind]),
-                                p->slice_chunk[kind], st);
+  // buffers for min(n, chunk) bitstrings (they grow when a later call needs more); a fixed
+  // workspace runs in its own batch size
+  tn_status s = w.fixed ? TN_OK
+                        : ws_ensure_sized(p, w, kind, std::min<int64_t>(std::max<int64_t>(n, w.chunk), p->chunk[kind]),
+                                          p->slice_chunk[kind], st);
   if (s != TN_OK) return s;
   const int words = (c->n + 63) / 64;
   const bool bits_dev = is_device_ptr(bits), out_dev = is_device_ptr(out);

@@ -6,7 +6,9 @@
 // batch size), run them as one device batch (the tn_amplitudes path), and scatter the results.
 // A request is admissible when the device memory of its batch fits the HBM budget next to the
 // batches in flight, so requests that arrive while others run are started as soon as a worker
-// and memory are free, and their work overlaps on the device. Latency = completion - submission.
+// and memory are free, and their work overlaps on the device. A worker's workspace lives only as
+// long as its batch (it is released when the batch ends), so the device memory the server holds is
+// the sum of the admitted batches' footprints. Latency = completion - submission.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -55,7 +57,7 @@ struct tn_server {
   double admitted = 0, peak_admitted = 0;
   int inflight = 0, max_inflight_seen = 0;
   double busy_since = -1, busy_total = 0;
-  int64_t submitted = 0, completed = 0, failed = 0, rejected = 0, amplitudes = 0;
+  int64_t submitted = 0, completed = 0, failed = 0, rejected = 0, amplitudes = 0, cancelled = 0;
   std::vector<double> latencies;
 };
 
@@ -73,7 +75,6 @@ double footprint(const tn_plan *p, tn_precision prec, int64_t n) {
 void worker_main(tn_server *s, int wid) {
   cudaStream_t st = nullptr;
   if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) st = nullptr;
-  std::map<tn_plan *, Workspace> ws;   // this worker's workspaces, one per plan it served
   std::unique_lock<std::mutex> lk(s->mu);
   for (;;) {
     // oldest request whose batch fits the budget next to the batches in flight
@@ -118,8 +119,11 @@ void worker_main(tn_server *s, int wid) {
       std::memcpy(bits.data() + off * words, r->bits.data(), (size_t)r->n * words * 8);
       off += r->n;
     }
-    tn_status status = run_amplitudes(p, ws[p], bits.data(), total, head->prec, res.data(), st);
+    Workspace ws;   // this batch's buffers, released before its footprint leaves the admitted sum
+    tn_status status = run_amplitudes(p, ws, bits.data(), total, head->prec, res.data(), st);
     std::string err = status == TN_OK ? std::string() : std::string(tn_last_error());
+    if (st) cudaStreamSynchronize(st);
+    ws_release(p->c->mem, ws);
     const double t = now_s();
 
     lk.lock();
@@ -145,7 +149,6 @@ void worker_main(tn_server *s, int wid) {
     s->cv_work.notify_all();
   }
   lk.unlock();
-  for (auto &kv : ws) ws_release(kv.first->c->mem, kv.second);
   if (st) {
     cudaStreamSynchronize(st);
     cudaStreamDestroy(st);
@@ -244,6 +247,24 @@ extern "C" tn_status tn_server_wait(tn_server *s, uint64_t ticket, int64_t timeo
   return st;
 }
 
+extern "C" tn_status tn_server_cancel(tn_server *s, uint64_t ticket) {
+  if (!s) return tn_fail(TN_ERR_ARG, "tn_server_cancel: NULL server");
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(ticket);
+  if (it == s->reqs.end()) return tn_fail(TN_ERR_ARG, "unknown ticket %llu", (unsigned long long)ticket);
+  Request *r = it->second;
+  auto q = std::find(s->queue.begin(), s->queue.end(), r);
+  if (q == s->queue.end())
+    return tn_fail(TN_ERR_STATE, "ticket %llu is %s: only queued requests can be cancelled",
+                   (unsigned long long)ticket, r->done ? "complete" : "running");
+  s->queue.erase(q);
+  s->reqs.erase(it);
+  delete r;
+  s->cancelled++;
+  s->cv_work.notify_all();   // the budget a worker was waiting on may have been this request's
+  return TN_OK;
+}
+
 extern "C" tn_status tn_server_stats_get(tn_server *s, tn_server_stats *o) {
   if (!s || !o) return tn_fail(TN_ERR_ARG, "tn_server_stats_get: NULL argument");
   std::lock_guard<std::mutex> lk(s->mu);
@@ -258,6 +279,7 @@ extern "C" tn_status tn_server_stats_get(tn_server *s, tn_server_stats *o) {
   o->p99_latency_s = percentile(s->latencies, 0.99);
   o->max_inflight_seen = s->max_inflight_seen;
   o->peak_admitted_bytes = s->peak_admitted;
+  o->cancelled = s->cancelled;
   return TN_OK;
 }
 

@@ -42,11 +42,6 @@ tn_status scratch_address(void **out) {
   return TN_OK;
 }
 
-// allocator that refuses: if the workspace set-up ever asked for more than was carved, the call
-// fails with TN_ERR_OOM instead of allocating
-void *refuse_alloc(size_t, void *, void *) { return nullptr; }
-void refuse_free(void *, size_t, void *, void *) {}
-
 }  // namespace
 
 extern "C" tn_status tn_amplitudes_static(tn_plan *p, const uint64_t *bits, int64_t n, tn_precision prec,
@@ -75,22 +70,20 @@ extern "C" tn_status tn_amplitudes_static(tn_plan *p, const uint64_t *bits, int6
                        (long long)ws_sizes(p, kind, 1, 1).total, (long long)cap);
     }
   }
+  // the array belongs to the device that is current; the plan's tensors live on its circuit's device
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return tn_fail(TN_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+  if (dev != p->c->device)
+    return tn_fail(TN_ERR_ARG, "tn_amplitudes_static: device %d is current, the plan lives on device %d", dev,
+                   p->c->device);
   void *base = nullptr;
   tn_status s = scratch_address(&base);
   if (s != TN_OK) return s;
-  // a private copy of the plan and its circuit whose workspace lives in the static array and
-  // whose allocator refuses; nothing of the caller's plan or circuit is modified
-  tn_circuit cc = *p->c;
-  cc.mem.a.alloc = refuse_alloc;
-  cc.mem.a.free = refuse_free;
-  cc.mem.a.ctx = nullptr;
-  cc.mem.has = true;
-  tn_plan q = *p;
-  q.c = &cc;
-  q.chunk[kind] = (int)ch;
-  q.slice_chunk[kind] = sc;
-  q.ws = Workspace();
-  ws_carve(q.ws, base, ws_sizes(p, kind, ch, sc), ch, sc, (cudaStream_t)cuda_stream);
+  // a workspace carved from the static array: run in its batch size, never grown or released
+  Workspace w;
+  ws_carve(w, base, ws_sizes(p, kind, ch, sc), ch, sc, (cudaStream_t)cuda_stream);
+  w.fixed = true;
   // the error words are cleared by the run itself; every other buffer is written before read
-  return run_amplitudes(&q, q.ws, bits, n, prec, out, (cudaStream_t)cuda_stream);
+  return run_amplitudes(p, w, bits, n, prec, out, (cudaStream_t)cuda_stream);
 }

@@ -362,10 +362,9 @@ cudaError_t launch_bn(const StepParams &s, const ContractArgs &a, const float2 *
   constexpr size_t stage = (size_t)P * (BM * 128 + BN * 128);
   const size_t smem = 2 * stage + 1024;
   static_assert(2 * (size_t)P * (BM * 128 + BN * 128) + 1024 <= 227 * 1024, "shared memory");
-  // once per instantiation (a function-local static is initialised by one thread)
-  static const cudaError_t attr = cudaFuncSetAttribute(tc_step_kernel<KIND, P, ORD, BN, R>,
-                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (attr != cudaSuccess) return attr;
+  // the dynamic shared memory limit on the current device (set once per device)
+  const int lim = tn_smem_optin<tc_step_kernel<KIND, P, ORD, BN, R>>();
+  if (lim < 0 || (size_t)lim < smem) return cudaErrorInvalidValue;
   const int64_t tiles = ((s.M + BM - 1) / BM) * ((2 * s.N + BN - 1) / BN);
   const int64_t grid = tiles * a.items;
   if (grid <= 0) return cudaSuccess;

@@ -458,21 +458,8 @@ cudaError_t launch_t(const StepParams &s, const ContractArgs &a, const Pieces &A
                      cudaStream_t st) {
   constexpr bool BUILD = BM != 0;
   constexpr size_t stage = (size_t)T_P * (T_BM * 128 + BN * 128);
-  // once per instantiation (a function-local static is initialised by one thread): the dynamic
-  // shared memory limit = the device's opt-in maximum minus the kernel's static shared memory
-  static const int max_dyn = [] {
-    int dev = 0, optin = 0;
-    cudaFuncAttributes fa;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
-        cudaFuncGetAttributes(&fa, tma_step_kernel<BN, R, S, BM>) != cudaSuccess)
-      return -1;
-    const int lim = optin - (int)fa.sharedSizeBytes;
-    return cudaFuncSetAttribute(tma_step_kernel<BN, R, S, BM>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) ==
-                   cudaSuccess
-               ? lim
-               : -1;
-  }();
+  // the dynamic shared memory limit on the current device (set once per device)
+  const int max_dyn = tn_smem_optin<tma_step_kernel<BN, R, S, BM>>();
   if (max_dyn < 0) return cudaErrorInvalidValue;
   size_t smem = S * stage + 1024;
   if (smem > (size_t)max_dyn) return cudaErrorInvalidValue;

@@ -331,27 +331,14 @@ template <int BN, int R, int S, int NBUF, int BM>
 cudaError_t launch_p(const StepParams &s, const ContractArgs &a, const Pieces &A, const Pieces &B, const OutDesc &out,
                      int *err, const float2 *cbuf, int64_t c_stride, cudaStream_t st) {
   constexpr size_t stage = (size_t)P_PIECES * (P_BM * 128 + BN * 128);
-  // once per instantiation: the dynamic shared memory limit (opt-in maximum minus static) and
-  // the SM count of the current device
-  static const int max_dyn = [] {
-    int dev = 0, optin = 0;
-    cudaFuncAttributes fa;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
-        cudaFuncGetAttributes(&fa, tma_persist_kernel<BN, R, S, NBUF, BM>) != cudaSuccess)
-      return -1;
-    const int lim = optin - (int)fa.sharedSizeBytes;
-    return cudaFuncSetAttribute(tma_persist_kernel<BN, R, S, NBUF, BM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                lim) == cudaSuccess
-               ? lim
-               : -1;
-  }();
-  static const int sms = [] {
+  // the dynamic shared memory limit on the current device (set once per device), and its SM count
+  const int max_dyn = tn_smem_optin<tma_persist_kernel<BN, R, S, NBUF, BM>>();
+  int sms = -1;
+  {
     int dev = 0, n = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-      return -1;
-    return n;
-  }();
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+      sms = n;
+  }
   if (max_dyn < 0 || sms <= 0) return cudaErrorInvalidValue;
   const size_t smem = S * stage + 1024;
   if (smem > (size_t)max_dyn) return cudaErrorInvalidValue;

@@ -43,6 +43,7 @@ struct Half {
   std::vector<int64_t> node_off;                  // slot offsets (complex elements)
   int64_t item_elems = 2;                         // elements per item (all slots)
   int64_t max_work = 0;                           // global SVD work per item (steps not fitting smem)
+  int max_sweeps = 0;                             // Jacobi sweep cap of every SVD (0: the default)
   int64_t max_gate_mn = 0;
 };
 
@@ -59,6 +60,7 @@ struct tn_circuit {
   int compress = 0;                               // bond compression for the next programs (tn_compress)
   int built_compress = 0;                         // the compression of the current programs
   int device = 0;
+  int max_sweeps = 0;                             // tn_set_svd_sweeps (0: the default)
   Half ket, bra;
   Buf ket_dev, ket_c64, ket_off_dev, bra_off_dev, err_dev, ket_work;
 };
@@ -66,6 +68,7 @@ struct tn_circuit {
 struct Workspace {
   int chunk = 0;
   int64_t slice_chunk = 1;
+  bool fixed = false;                             // carved in memory the caller owns: never grown or freed
   Buf bits, bra64, bra32, gwork, t0, t1, res, err, cbuf;
   Buf ket64, ket32;                               // the ket with merged nodes (plans that merge)
 };

@@ -31,6 +31,7 @@ struct GateParams {
   double2 Q[16];
   int64_t work_stride;         // per-item global work size (complex elements) when !use_smem
   int id;                      // position in the half's gate program (reported when the SVD fails)
+  int max_sweeps;              // cap on Jacobi sweeps (0: the default, 60); then the error word is set
 };
 
 struct Apply1Params {

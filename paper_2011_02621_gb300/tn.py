@@ -75,7 +75,7 @@ class tn_server_stats(C.Structure):
     _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64), ("rejected", C.c_int64),
                 ("amplitudes", C.c_int64), ("busy_seconds", C.c_double), ("p50_latency_s", C.c_double),
                 ("p99_latency_s", C.c_double), ("max_inflight_seen", C.c_double),
-                ("peak_admitted_bytes", C.c_double)]
+                ("peak_admitted_bytes", C.c_double), ("cancelled", C.c_int64)]
 
 
 def _load():
@@ -89,6 +89,7 @@ def _load():
         "tn_evolve_two_sided": (i32, [vp, i32, i32, dbl, vp]),
         "tn_circuit_bond_dims": (i32, [vp, i32, C.POINTER(i32)]),
         "tn_set_compression": (i32, [vp, i32]),
+        "tn_set_svd_sweeps": (i32, [vp, i32]),
         "tn_program_inspect": (i32, [vp, i32, i32, dbl, i32, C.POINTER(i64), C.POINTER(dbl), C.POINTER(i64)]),
         "tn_path": (i32, [vp, C.POINTER(tn_path_opts), C.POINTER(vp), C.POINTER(tn_plan_info)]),
         "tn_plan_details": (i32, [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i64)]),
@@ -116,6 +117,7 @@ def _load():
         "tn_server_submit": (i32, [vp, vp, vp, i64, i32, vp, C.POINTER(C.c_uint64)]),
         "tn_server_wait": (i32, [vp, C.c_uint64, i64]),
         "tn_server_stats_get": (i32, [vp, C.POINTER(tn_server_stats)]),
+        "tn_server_cancel": (i32, [vp, C.c_uint64]),
         "tn_server_free": (None, [vp]),
         "tn_autotune": (i32, [vp, i32, i64, vp, C.POINTER(i32)]),
         "tn_plan_kernels": (i32, [vp, i32, C.POINTER(i32)]),
@@ -279,6 +281,11 @@ def tn_set_compression(c: Circuit, mode: str = "one_sided"):
     if mode not in COMPRESSIONS:
         raise ValueError(f"unknown compression {mode!r}")
     _check(LIB.tn_set_compression(c.ptr, COMPRESSIONS[mode]))
+
+
+def tn_set_svd_sweeps(c: Circuit, max_sweeps: int = 0):
+    """Cap on the Jacobi sweeps of every SVD of both halves (0: the default, 60)."""
+    _check(LIB.tn_set_svd_sweeps(c.ptr, int(max_sweeps)))
 
 
 def tn_evolve_two_sided(c: Circuit, split_cycle: int, chi_max: int = 0, cutoff_rel: float = 1e-12, stream=None,
@@ -608,7 +615,7 @@ def tn_server_wait(s: Server, ticket: int, timeout_ms: int = -1):
     st = LIB.tn_server_wait(s.ptr, C.c_uint64(ticket), int(timeout_ms))
     if st == TN_ERR_TIMEOUT:
         raise TNError(st, "request not complete")
-    res, _ = s._pending.pop(ticket)
+    res, _ = s._pending.pop(ticket, (None, None))
     _check(st)
     return res
 
@@ -617,6 +624,12 @@ def tn_server_free(s: Server):
     if s.ptr:
         LIB.tn_server_free(s.ptr)
         s.ptr = None
+
+
+def tn_server_cancel(s: Server, ticket: int):
+    """Remove a request that is still queued (TN_ERR_STATE if it is running or complete)."""
+    _check(LIB.tn_server_cancel(s.ptr, C.c_uint64(ticket)))
+    s._pending.pop(ticket, None)
 
 
 def tn_server_stats_get(s: Server) -> dict:

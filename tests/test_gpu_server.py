@@ -78,3 +78,80 @@ def test_bounded_wait_and_bad_request(tn):
         tn._check(tn.LIB.tn_server_submit(srv.ptr, p.ptr, None, 5, 0, None, None))
     assert ei.value.status == tn.TN_ERR_ARG
     tn.tn_server_free(srv)
+
+
+def test_device_memory_stays_within_the_budget(tn):
+    """Several plans and workers: every worker's workspace lives only as long as its batch, so the
+    device memory the allocator hands out while the server runs (PyTorch's peak over its baseline)
+    stays within the admission budget (plus the allocator's rounding of each block)."""
+    import torch
+    plans = []
+    for name, opts in (("grid12", {}), ("syc53", {}), ("syc53", {"layers": 2})):
+        w = gen.workload(name, n_bits=1)
+        plans.append((_plan(tn, w, **opts), w.graph.n))
+    budget = 2.5 * 2 ** 30                  # above any one request (plans hold 2 GiB batches), below several
+    torch.cuda.synchronize()
+    base = torch.cuda.memory_allocated()
+    torch.cuda.reset_peak_memory_stats()
+    srv = tn.tn_server_create(hbm_budget_bytes=budget, max_inflight=3)
+    tickets = []
+    for i in range(18):
+        p, n = plans[i % 3]
+        bits = gen.bitstrings(n, 200 + 37 * i, gen.rng(900 + i, 2))
+        tickets.append(tn.tn_server_submit(srv, p, bits, ["bf16x6", "fp32", "fp64"][i % 3]))
+    for t in tickets:
+        tn.tn_server_wait(srv, t)
+    st = tn.tn_server_stats_get(srv)
+    tn.tn_server_free(srv)
+    torch.cuda.synchronize()
+    assert st["completed"] == 18 and st["peak_admitted_bytes"] <= budget
+    peak = torch.cuda.max_memory_allocated() - base
+    assert peak <= 1.05 * budget + 64 * 2 ** 20, (peak, budget)
+    assert torch.cuda.memory_allocated() <= base + 2 * 2 ** 20   # nothing kept after the server
+
+
+def test_queued_requests_can_be_cancelled(tn):
+    """One worker busy with a large batch; requests queued behind it are cancelled on the host:
+    they are removed, never run, and their tickets are forgotten; the others complete as alone."""
+    w = gen.workload("syc53", n_bits=1)
+    p = _plan(tn, w, layers=2)
+    srv = tn.tn_server_create(hbm_budget_bytes=8 * 2 ** 30, max_inflight=1)
+    big = tn.tn_server_submit(srv, p, gen.bitstrings(53, 16384, gen.rng(31, 2)), "fp64")
+    keep_bits = gen.bitstrings(53, 40, gen.rng(32, 2))
+    keep = tn.tn_server_submit(srv, p, keep_bits, "fp32")
+    drop = [tn.tn_server_submit(srv, p, gen.bitstrings(53, 50, gen.rng(33 + i, 2)), "fp32") for i in range(3)]
+    for t in drop:
+        tn.tn_server_cancel(srv, t)
+    with pytest.raises(tn.TNError) as ei:
+        tn.tn_server_cancel(srv, drop[0])              # already gone
+    assert ei.value.status == tn.TN_ERR_ARG
+    got = tn.tn_server_wait(srv, keep)
+    tn.tn_server_wait(srv, big)
+    with pytest.raises(tn.TNError) as ei:
+        tn.tn_server_cancel(srv, keep)                 # complete (and collected): unknown now
+    assert ei.value.status == tn.TN_ERR_ARG
+    with pytest.raises(tn.TNError) as ei:
+        tn.tn_server_wait(srv, drop[1])
+    assert ei.value.status == tn.TN_ERR_ARG
+    st = tn.tn_server_stats_get(srv)
+    assert st["cancelled"] == 3 and st["completed"] == 2 and st["amplitudes"] == 16384 + 40
+    assert rel_err(got, tn.tn_amplitudes(p, keep_bits, "fp32")) < TC_TOL
+    tn.tn_server_free(srv)
+
+
+def test_running_request_cannot_be_cancelled(tn):
+    w = gen.workload("syc53", n_bits=1)
+    p = _plan(tn, w, layers=2)
+    srv = tn.tn_server_create(hbm_budget_bytes=8 * 2 ** 30, max_inflight=1)
+    t = tn.tn_server_submit(srv, p, gen.bitstrings(53, 16384, gen.rng(41, 2)), "fp64")
+    import time
+    for _ in range(200):                               # until the worker has taken it
+        st = tn.tn_server_stats_get(srv)
+        if st["max_inflight_seen"] >= 1:
+            break
+        time.sleep(0.005)
+    with pytest.raises(tn.TNError) as ei:
+        tn.tn_server_cancel(srv, t)
+    assert ei.value.status == tn.TN_ERR_STATE
+    tn.tn_server_wait(srv, t)
+    tn.tn_server_free(srv)

@@ -65,3 +65,41 @@ def test_static_rejects_plan_beyond_its_scratch(tn):
         tn.tn_amplitudes_static(p, w.bits, "bf16x6")
     assert ei.value.status == tn.TN_ERR_UNSUPPORTED
     assert "static scratch" in str(ei.value)
+
+
+SCRATCH = 32 * 2 ** 20
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", FP64_TOL), ("fp32", TC_TOL)])
+def test_static_runs_several_batches(tn, prec, tol):
+    """More bitstrings than the scratch holds at once: the call runs them in several batches."""
+    import torch
+    w = gen.workload("syc53", n_bits=120)
+    p = _plan(tn, w, layers=2)
+    per = p.info["workspace_bytes"] / p.info["chunk_bitstrings"]       # one bitstring's workspace
+    assert per * len(w.bits) > 2 * SCRATCH                             # at least three batches
+    ref = tn.tn_amplitudes(p, w.bits, prec)
+    torch.cuda.synchronize()
+    before = torch.cuda.memory_allocated()
+    for _ in range(2):
+        assert rel_err(tn.tn_amplitudes_static(p, w.bits, prec), ref) < tol
+    torch.cuda.synchronize()
+    assert torch.cuda.memory_allocated() == before
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", FP64_TOL), ("fp32", TC_TOL)])
+def test_static_splits_one_bitstring_into_slice_groups(tn, prec, tol):
+    """A plan with 262144 slices whose single bitstring needs 128 MiB of workspace, more than the
+    scratch, while one slice fits: each bitstring runs as several groups of its slices."""
+    import torch
+    w = gen.workload("grid12", n_bits=3)
+    p = _plan(tn, w, max_intermediate=32)
+    per = p.info["workspace_bytes"] / p.info["chunk_bitstrings"]
+    assert p.info["n_slices"] >= 1 << 16 and per > SCRATCH
+    ref = tn.tn_amplitudes(p, w.bits, prec)
+    torch.cuda.synchronize()
+    before = torch.cuda.memory_allocated()
+    for _ in range(2):
+        assert rel_err(tn.tn_amplitudes_static(p, w.bits, prec), ref) < tol
+    torch.cuda.synchronize()
+    assert torch.cuda.memory_allocated() == before
