@@ -75,26 +75,42 @@ __host__ __device__ inline int C_of(const WorkLayout &L) { return L.C; }
 constexpr int GATE_THREADS = 128;
 constexpr int MAX_SWEEPS = 60;
 
-// TPI threads per item (128: one item per CTA; 32: one warp per item, four items per CTA
-// for small matrices): X_k = P A^k, X_l = Q A^l (Eqs. result1/result2), SVD of the
+// TPI threads per item (128: one item per CTA; 32, 16, 8 or 4: 32 / TPI items per warp, 128 / TPI
+// per CTA, for small matrices): X_k = P A^k, X_l = Q A^l (Eqs. result1/result2), SVD of the
 // smaller-row endpoint by parallel one-sided (Hestenes) Jacobi, keep s_j > cutoff*s_0 (at
 // most dout, zero-padded to dout), A^sv <- U, A^other <- X_other (S V)^T (Eqs. svd/svd2).
+// With several items in a warp every lane runs the same instruction stream: the rotation
+// parameters of the pairs of all those items come from one pass of the FP64 square roots and
+// divisions that dominate the work of small matrices.
 template <int TPI>
 __device__ __forceinline__ void item_sync() {
-  if (TPI == 32) __syncwarp(); else __syncthreads();
+  if (TPI <= 32) __syncwarp(); else __syncthreads();
+}
+
+// sum of x over the TPI lanes of this item's aligned lane group (TPI <= 32)
+template <int TPI>
+__device__ __forceinline__ double group_sum(double x) {
+#pragma unroll
+  for (int o = TPI / 2; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
 }
 
 template <int TPI>
 __global__ void __launch_bounds__(GATE_THREADS) gate_kernel(GateParams g, double2 *base, int64_t item_stride,
                                                             double2 *gwork, int *errflag, int items, int *rank_out) {
   extern __shared__ double2 smem[];
+  constexpr bool SUB = TPI <= 32;                 // items within one warp (no block-wide barrier)
   constexpr int GPB = GATE_THREADS / TPI;         // items per block
   const int grp = threadIdx.x / TPI;
   const int item = blockIdx.x * GPB + grp;
   const int tid = threadIdx.x % TPI;
-  const int lane = tid & 31, warp = tid >> 5, nwarp = TPI / 32;
-  if (TPI == 32 && item >= items) return;         // whole warps only: no block-wide barrier below
-  double2 *A = base + (int64_t)item * item_stride;
+  const int lane = tid & 31, warp = tid >> 5, nwarp = TPI >= 32 ? TPI / 32 : 1;
+  // a warp whose first item is past the end has nothing to do; a group past the end inside a
+  // live warp runs along (its lanes take part in the warp's shuffles) on the last item's data
+  // and writes nothing
+  if (SUB && blockIdx.x * GPB + (int)(threadIdx.x / 32) * (32 / (SUB ? TPI : 32)) >= items) return;
+  const bool valid = item < items;
+  double2 *A = base + (int64_t)(valid ? item : items - 1) * item_stride;
   const WorkLayout L = work_layout(g);
   double2 *work = g.use_smem ? smem + (int64_t)grp * L.total : gwork + (int64_t)item * g.work_stride;
   double2 *Y = work + L.y, *Xo = work + L.xo, *W = work + L.w, *Vp = work + L.vp;
@@ -149,20 +165,25 @@ __global__ void __launch_bounds__(GATE_THREADS) gate_kernel(GateParams g, double
   // iteration ends on rounding-dominated pairs (exactly degenerate spectra are common here).
   __shared__ int s_rot_a[GPB];
   __shared__ double s_fro_a[GPB];
-  __shared__ double s_part_a[GPB][TPI / 32];
+  __shared__ double s_part_a[GPB][TPI >= 32 ? TPI / 32 : 1];
   int &s_rot = s_rot_a[grp];
   double &s_fro = s_fro_a[grp];
   double *s_part = s_part_a[grp];
   {
     double f = 0;
     for (int64_t idx = tid; idx < (int64_t)L.R * L.C; idx += TPI) f = fma(Y[idx].x, Y[idx].x, fma(Y[idx].y, Y[idx].y, f));
-    for (int o = 16; o; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
-    if (lane == 0) s_part[warp] = f;
-    item_sync<TPI>();
-    if (tid == 0) {
-      double t = 0;
-      for (int w = 0; w < TPI / 32; ++w) t += s_part[w];
-      s_fro = t;
+    if constexpr (SUB) {
+      f = group_sum<TPI>(f);
+      if (tid == 0) s_fro = f;
+    } else {
+      for (int o = 16; o; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
+      if (lane == 0) s_part[warp] = f;
+      item_sync<TPI>();
+      if (tid == 0) {
+        double t = 0;
+        for (int w = 0; w < TPI / 32; ++w) t += s_part[w];
+        s_fro = t;
+      }
     }
     item_sync<TPI>();
   }
@@ -174,19 +195,22 @@ __global__ void __launch_bounds__(GATE_THREADS) gate_kernel(GateParams g, double
   const int rounds = Cp - 1;
   bool converged = (C <= 1);
   const int sweep_cap = g.max_sweeps > 0 ? g.max_sweeps : MAX_SWEEPS;
-  for (int sweep = 0; sweep < sweep_cap && !converged; ++sweep) {
+  // the loop runs while any item of the warp (SUB) or the item (TPI 128) is unconverged: a
+  // converged item's pairs are below the rotation threshold and stay as they are
+  for (int sweep = 0; sweep < sweep_cap; ++sweep) {
+    if (SUB ? __all_sync(0xffffffffu, converged) : converged) break;
     if (tid == 0) s_rot = 0;
     item_sync<TPI>();
     for (int rd = 0; rd < rounds; ++rd) {
-      if constexpr (TPI == 32) {
-        // one warp per item: the round's column pairs (disjoint columns) side by side, LP lanes
-        // per pair, each lane summing rows r = sub, sub + LP, ... and the pair's lanes reducing
-        // with shuffles inside their aligned LP-lane segment
+      if constexpr (SUB) {
+        // items of TPI lanes inside a warp: the round's column pairs (disjoint columns) side by
+        // side, LP lanes per pair, each lane summing rows r = sub, sub + LP, ... and the pair's
+        // lanes reducing with shuffles inside their aligned LP-lane segment
         const int npairs = Cp / 2;
-        int LP = 32;
-        while (LP > 1 && LP * npairs > 32) LP >>= 1;
-        const int sub = lane & (LP - 1), slot = lane / LP;
-        for (int pi0 = 0; pi0 < npairs; pi0 += 32 / LP) {
+        int LP = TPI;
+        while (LP > 1 && LP * npairs > TPI) LP >>= 1;
+        const int sub = tid & (LP - 1), slot = tid / LP;
+        for (int pi0 = 0; pi0 < npairs; pi0 += TPI / LP) {
           const int pi = pi0 + slot;
           int p = 0, q = 0;
           if (pi == 0) { p = rd; q = Cp - 1; }
@@ -277,15 +301,25 @@ __global__ void __launch_bounds__(GATE_THREADS) gate_kernel(GateParams g, double
     converged = (s_rot == 0);
     item_sync<TPI>();
   }
-  if (!converged && tid == 0) atomicCAS(errflag, 0, 1 + g.id);   // first failing gate, 1-based
+  if (!converged && tid == 0 && valid) atomicCAS(errflag, 0, 1 + g.id);   // first failing gate, 1-based
 
   // ---- singular values, descending ranks, truncation count
-  for (int j = warp; j < C; j += nwarp) {
-    const double2 *yj = Y + (int64_t)j * R;
-    double s2 = 0;
-    for (int r = lane; r < R; r += 32) s2 = fma(yj[r].x, yj[r].x, fma(yj[r].y, yj[r].y, s2));
-    for (int o = 16; o; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-    if (lane == 0) sig[j] = sqrt(s2);
+  if constexpr (SUB) {
+    for (int j = 0; j < C; ++j) {
+      const double2 *yj = Y + (int64_t)j * R;
+      double s2 = 0;
+      for (int r = tid; r < R; r += TPI) s2 = fma(yj[r].x, yj[r].x, fma(yj[r].y, yj[r].y, s2));
+      s2 = group_sum<TPI>(s2);
+      if (tid == 0) sig[j] = sqrt(s2);
+    }
+  } else {
+    for (int j = warp; j < C; j += nwarp) {
+      const double2 *yj = Y + (int64_t)j * R;
+      double s2 = 0;
+      for (int r = lane; r < R; r += 32) s2 = fma(yj[r].x, yj[r].x, fma(yj[r].y, yj[r].y, s2));
+      for (int o = 16; o; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+      if (lane == 0) sig[j] = sqrt(s2);
+    }
   }
   item_sync<TPI>();
   __shared__ double s_max_a[GPB];
@@ -299,7 +333,7 @@ __global__ void __launch_bounds__(GATE_THREADS) gate_kernel(GateParams g, double
     for (int j = 0; j < C; ++j) kc += (sig[j] > g.cutoff * mx) ? 1 : 0;
     s_max = mx;
     s_keep = kc < g.dout ? kc : g.dout;
-    if (rank_out && item == 0) {
+    if (rank_out && item == 0 && valid) {
       // numerical rank: singular values above the rounding level of the column norms
       const double thr = 4.0 * sqrt((double)R) * 2.220446049250313e-16 * mx;
       int nr = 0;
@@ -355,7 +389,7 @@ __global__ void __launch_bounds__(GATE_THREADS) gate_kernel(GateParams g, double
       }
       int sp = (int)(r / O);
       int64_t o = r % O;
-      An[sp * nv.sig + other_offset(nv, o) + (int64_t)t * nv.stride[nv.pos]] = u;
+      if (valid) An[sp * nv.sig + other_offset(nv, o) + (int64_t)t * nv.stride[nv.pos]] = u;
     }
   }
   item_sync<TPI>();
@@ -376,7 +410,7 @@ __global__ void __launch_bounds__(GATE_THREADS) gate_kernel(GateParams g, double
       for (int c = 0; c < n; ++c) acc = cfma(xr[c], vt[c], acc);
       int sp = (int)(r / O);
       int64_t o = r % O;
-      An[sp * nv.sig + other_offset(nv, o) + (int64_t)t * nv.stride[nv.pos]] = acc;
+      if (valid) An[sp * nv.sig + other_offset(nv, o) + (int64_t)t * nv.stride[nv.pos]] = acc;
     }
   }
 }
@@ -423,28 +457,50 @@ __global__ void copy_words_kernel(const uint64_t *src, uint64_t *dst, int64_t n)
 
 int64_t gate_work_elems(const GateParams &g) { return work_layout(g).total; }
 
+namespace {
+
+template <int TPI>
+cudaError_t launch_items_per_warp(const GateParams &g, const WorkLayout &L, double2 *base, int64_t item_stride,
+                                  int items, double2 *gwork, int *errflag, int *rank_out, cudaStream_t st) {
+  constexpr int GPB = GATE_THREADS / TPI;
+  const size_t smem = (size_t)GPB * L.total * sizeof(double2);
+  if (smem > 48 * 1024) {
+    const int lim = tn_smem_optin<gate_kernel<TPI>>();
+    if (lim < 0 || (size_t)lim < smem) return cudaErrorInvalidValue;
+  }
+  gate_kernel<TPI><<<(items + GPB - 1) / GPB, GATE_THREADS, smem, st>>>(g, base, item_stride, gwork, errflag, items,
+                                                                        rank_out);
+  tn_count_launch(1);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
 cudaError_t launch_gate(const GateParams &g, double2 *base, int64_t item_stride, int items, double2 *gwork,
                         int *errflag, int *rank_out, cudaStream_t st) {
   if (items <= 0) return cudaSuccess;
   const WorkLayout L = work_layout(g);
-  // small matrices: one warp per item, four items per CTA
+  // small matrices: items inside one warp, as many lanes each as a Jacobi round's pairs cover
+  // over all rows (at least 4, at most 32), 128 / lanes items per CTA in shared memory
   const bool warp_per_item = g.use_smem && L.C <= 16 && L.R <= 256 && 4 * L.total * sizeof(double2) <= 96 * 1024;
   if (warp_per_item) {
-    const size_t smem = 4 * (size_t)L.total * sizeof(double2);
-    if (smem > 48 * 1024) {
-      const int lim = tn_smem_optin<gate_kernel<32>>();
-      if (lim < 0 || (size_t)lim < smem) return cudaErrorInvalidValue;
+    const int npairs = ((L.C + 1) & ~1) / 2;
+    int tpi = 4;
+    while (tpi < 32 && tpi < npairs * L.R) tpi <<= 1;
+    while (tpi < 32 && (size_t)(GATE_THREADS / tpi) * L.total * sizeof(double2) > 96 * 1024) tpi <<= 1;
+    switch (tpi) {
+      case 4: return launch_items_per_warp<4>(g, L, base, item_stride, items, gwork, errflag, rank_out, st);
+      case 8: return launch_items_per_warp<8>(g, L, base, item_stride, items, gwork, errflag, rank_out, st);
+      case 16: return launch_items_per_warp<16>(g, L, base, item_stride, items, gwork, errflag, rank_out, st);
+      default: return launch_items_per_warp<32>(g, L, base, item_stride, items, gwork, errflag, rank_out, st);
     }
-    gate_kernel<32><<<(items + 3) / 4, GATE_THREADS, smem, st>>>(g, base, item_stride, gwork, errflag, items,
-                                                                 rank_out);
-  } else {
-    const size_t smem = g.use_smem ? (size_t)L.total * sizeof(double2) : 0;
-    if (smem > 48 * 1024) {
-      const int lim = tn_smem_optin<gate_kernel<128>>();
-      if (lim < 0 || (size_t)lim < smem) return cudaErrorInvalidValue;
-    }
-    gate_kernel<128><<<items, GATE_THREADS, smem, st>>>(g, base, item_stride, gwork, errflag, items, rank_out);
   }
+  const size_t smem = g.use_smem ? (size_t)L.total * sizeof(double2) : 0;
+  if (smem > 48 * 1024) {
+    const int lim = tn_smem_optin<gate_kernel<128>>();
+    if (lim < 0 || (size_t)lim < smem) return cudaErrorInvalidValue;
+  }
+  gate_kernel<128><<<items, GATE_THREADS, smem, st>>>(g, base, item_stride, gwork, errflag, items, rank_out);
   tn_count_launch(1);
   return cudaGetLastError();
 }
