@@ -1691,14 +1691,24 @@ static tn_status validate_plan(const tn_plan *p) {
         if (d % q != 0) return bad("box tile not aligned to the rest digits", (int)j, s.box_tm, s.M);
         q = 1;
       }
-      if (q != 1 || s.M % s.box_tm != 0 || s.box_tm >= 65536)
+      if (q != 1 || s.M % s.box_tm != 0 || s.box_tm >= (1 << 14) || s.t_wperm % 2 != 0)
         return bad("box tile does not divide the rows", (int)j, s.box_tm, s.M);
       std::vector<char> seen((size_t)s.box_tm * s.N, 0);
-      for (int64_t e = 0; e < (int64_t)s.box_tm * s.N; ++e) {
-        const uint32_t pr = (uint32_t)tab[s.t_wperm + e];
-        const int64_t r = pr >> 16, nn = pr & 0xffffu;
-        if (r >= s.box_tm || nn >= s.N || seen[r * s.N + nn]) return bad("box write table", (int)j, e, s.box_tm * s.N);
+      const int64_t tot = (int64_t)s.box_tm * s.N;
+      for (int64_t e = 0; e < tot; ++e) {
+        const uint32_t pr = (uint32_t)tab[s.t_wperm + 2 * e];
+        const int64_t r = (pr >> 16) & 0x3fffu, nn = pr & 0xffffu;
+        if (r >= s.box_tm || nn >= s.N || seen[r * s.N + nn]) return bad("box write table", (int)j, e, tot);
         seen[r * s.N + nn] = 1;
+        int64_t orl = 0, x = r;
+        for (int q = s.n_rest - 1; q >= 0; --q) { orl += (x % s.rest_dim[q]) * s.rest_ostride[q]; x /= s.rest_dim[q]; }
+        if (tab[s.t_wperm + 2 * e + 1] != orl + tab[s.t_ocol + nn]) return bad("box write offset", (int)j, e, tot);
+        if ((pr >> 30) & 1u) {   // a pair: the next entry is (r, n + 1) at the next offset, both even
+          const uint32_t p1 = (uint32_t)tab[s.t_wperm + 2 * e + 2];
+          if (e % 2 || e + 1 >= tot || ((p1 >> 16) & 0x3fffu) != r || (p1 & 0xffffu) != nn + 1 || nn % 2 ||
+              tab[s.t_wperm + 2 * e + 3] != tab[s.t_wperm + 2 * e + 1] + 1 || tab[s.t_wperm + 2 * e + 1] % 2)
+            return bad("box write pair", (int)j, e, tot);
+        }
       }
     }
   }
@@ -1938,9 +1948,23 @@ static tn_status compile_plan(tn_plan *p) {
       std::stable_sort(perm.begin(), perm.end(), [&](int64_t x, int64_t y) {
         return orl[x / N] + ocol[x % N] < orl[y / N] + ocol[y % N];
       });
-      for (int64_t &e : perm) e = ((e / N) << 16) | (e % N);
+      // per output, in that order: (r << 16 | n) and its offset orow(r) + ocol(n) in the tile; bit 30
+      // of an even entry marks it and the next as one pair (same row, columns n and n + 1 with n
+      // even, offsets d and d + 1 with d even), which the kernel moves as one 16-byte value
+      std::vector<int64_t> tabw(2 * tm * N);
+      for (int64_t e = 0; e < tm * N; ++e) {
+        const int64_t r = perm[e] / N, nn = perm[e] % N;
+        tabw[2 * e] = (r << 16) | nn;
+        tabw[2 * e + 1] = orl[r] + ocol[nn];
+      }
+      for (int64_t e = 0; e + 1 < tm * N; e += 2) {
+        const int64_t r0 = perm[e] / N, n0 = perm[e] % N, r1 = perm[e + 1] / N, n1 = perm[e + 1] % N;
+        if (r1 == r0 && n1 == n0 + 1 && n0 % 2 == 0 && tabw[2 * e + 3] == tabw[2 * e + 1] + 1 && tabw[2 * e + 1] % 2 == 0)
+          tabw[2 * e] |= (int64_t)1 << 30;
+      }
       s.box_tm = (int)tm;
-      s.t_wperm = push_tab(perm);
+      if (tab.size() & 1) tab.push_back(0);   // 8-byte aligned: the kernel reads the entries in pairs
+      s.t_wperm = push_tab(tabw);
     }
     std::vector<int64_t> skk, sbb;
     s.ket_sig = leg_strides(i, c.dk, skk);

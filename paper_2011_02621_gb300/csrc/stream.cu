@@ -12,8 +12,10 @@
 //    rows whose input is one contiguous block of box_tm * K complex values, copied with 16-byte
 //    cp.async into one of two buffers while the previous tile is computed and written;
 //  * each thread computes two rows' group of TN consecutive columns from shared memory;
-//  * the tile's outputs go out in increasing output offset (a table the plan compiler sorts), so
-//    that the permuted layout of the next step is written with full, coalesced sectors.
+//  * the tile's outputs go out in increasing output offset (a table the plan compiler sorts: per
+//    output its place in the tile and its offset), so that the permuted layout of the next step is
+//    written with full, coalesced sectors; outputs adjacent both in the tile and in the next
+//    layout move as one 16-byte value.
 #include <cuda_runtime.h>
 
 #include "tn_device.h"
@@ -38,11 +40,11 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 __device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 // Shared memory of one CTA: C[K][N], two input tile buffers [tm][kp] (the next tile is copied in
-// while the current one is used), the output tile [tm][np] (rows padded against bank conflicts),
-// the tile's local output row offsets and the column offsets.
+// while the current one is used) and the output tile [tm][np] (rows padded against bank
+// conflicts; np is even for complex64, so an even column starts a 16-byte pair).
 struct BoxLayout {
   int kp, np;
-  size_t c_off, in_off, in_size, out_off, orow_off, ocol_off, bytes;
+  size_t c_off, in_off, in_size, out_off, bytes;
 };
 
 __host__ __device__ inline size_t box_align16(size_t x) { return (x + 15) & ~(size_t)15; }
@@ -61,9 +63,7 @@ __host__ __device__ inline BoxLayout box_layout(int tm, int K, int N) {
   L.in_off = box_align16(L.c_off + (size_t)K * N * sizeof(V));
   L.in_size = box_align16((size_t)tm * L.kp * sizeof(V));      // one of the two input tile buffers
   L.out_off = L.in_off + 2 * L.in_size;
-  L.orow_off = box_align16(L.out_off + (size_t)tm * L.np * sizeof(V));
-  L.ocol_off = L.orow_off + (size_t)tm * sizeof(int);
-  L.bytes = box_align16(L.ocol_off + (size_t)N * sizeof(int));
+  L.bytes = box_align16(L.out_off + (size_t)tm * L.np * sizeof(V));
   return L;
 }
 
@@ -97,8 +97,6 @@ step_box_kernel(StepParams s, ContractArgs a, const typename BoxT<R>::V *ket, co
   V *const Ins0 = reinterpret_cast<V *>(box_raw + L.in_off);
   V *const Ins1 = reinterpret_cast<V *>(box_raw + L.in_off + L.in_size);
   V *Outs = reinterpret_cast<V *>(box_raw + L.out_off);
-  int *orow_s = reinterpret_cast<int *>(box_raw + L.orow_off);
-  int *ocol_s = reinterpret_cast<int *>(box_raw + L.ocol_off);
   const int tid = threadIdx.x;
   const int64_t T = s.M / TM;                    // row tiles per item
   const int64_t cpi = (T + tpc - 1) / tpc;       // CTAs per item
@@ -131,7 +129,7 @@ step_box_kernel(StepParams s, ContractArgs a, const typename BoxT<R>::V *ket, co
   };
   if (t_begin < t_end) load(t_begin);
 
-  {   // the absorbed node's operand (Eq. overlap) and the offset tables, once per CTA
+  {   // the absorbed node's operand (Eq. overlap), once per CTA
     const V *kp = ket + s.ket_off + c.sa;
     const V *bp = bra + c.b * a.bra_stride + s.bra_off + c.sb;
     const int32_t *bka = a.tab + s.t_bka, *bkb = a.tab + s.t_bkb;
@@ -140,14 +138,12 @@ step_box_kernel(StepParams s, ContractArgs a, const typename BoxT<R>::V *ket, co
       const int k = i / N, n = i - k * N;
       Cs[i] = overlap_elem(kp, bp, (int64_t)bka[k] + bna[n], (int64_t)bkb[k] + bnb[n], s.ket_sig, s.bra_sig, s.phys);
     }
-    for (int r = tid; r < TM; r += 256) orow_s[r] = orow_of(s, r);
-    for (int n = tid; n < N; n += 256) ocol_s[n] = a.tab[s.t_ocol + n];
   }
 
   const int G = N / TN;                 // threads per row
   const int RP = 256 / G;               // rows per pass
   const int g = tid % G, r0 = tid / G;
-  const uint32_t *wperm = reinterpret_cast<const uint32_t *>(a.tab + s.t_wperm);
+  const int2 *wtab = reinterpret_cast<const int2 *>(a.tab + s.t_wperm);   // (r << 16 | n, offset) per output
   for (int64_t t = t_begin; t < t_end; ++t) {
     // the next tile's copy runs while this tile is computed and written (its buffer was last read
     // by the compute of tile t - 1, which every thread finished before the barrier below it)
@@ -191,10 +187,24 @@ step_box_kernel(StepParams s, ContractArgs a, const typename BoxT<R>::V *ket, co
     }
     __syncthreads();                    // output tile complete
     const int obase = orow_of(s, t * (int64_t)TM);
-    for (int e = tid; e < TM * N; e += 256) {
-      const uint32_t pr = __ldg(wperm + e);
-      const int r = (int)(pr >> 16), n = (int)(pr & 0xffffu);
-      store_out(out, a.t_stride, item, obase + orow_s[r] + ocol_s[n], Outs[r * L.np + n]);
+    const int tot = TM * N;
+    for (int e = 2 * tid; e < tot; e += 512) {
+      const int2 w0 = __ldg(wtab + e);
+      const V *src0 = Outs + ((w0.x >> 16) & 0x3fff) * L.np + (w0.x & 0xffff);
+      if constexpr (sizeof(V) == 8) {
+        // a marked pair (same row, columns n, n + 1, offsets d, d + 1, n and d even): one 16-byte
+        // move when the tile's output base keeps it aligned
+        if (((w0.x >> 30) & 1) && out.fmt == 0 && ((obase + w0.y) & 1) == 0) {
+          float2 *dst = reinterpret_cast<float2 *>(out.p) + item * a.t_stride + obase + w0.y;
+          *reinterpret_cast<float4 *>(dst) = *reinterpret_cast<const float4 *>(src0);
+          continue;
+        }
+      }
+      store_out(out, a.t_stride, item, obase + w0.y, *src0);
+      if (e + 1 < tot) {
+        const int2 w1 = __ldg(wtab + e + 1);
+        store_out(out, a.t_stride, item, obase + w1.y, Outs[((w1.x >> 16) & 0x3fff) * L.np + (w1.x & 0xffff)]);
+      }
     }
   }
 }
