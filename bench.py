@@ -192,19 +192,23 @@ def traffic_record(kind):
         return None
     d = json.load(open(p))
     rec = d.get(kind)
-    if not rec or rec.get("source_sha") != source_sha():
+    if not rec or rec.get("source_sha") != source_sha(kind):
         return None
     return rec
 
 
-TRAFFIC_SOURCES = ("tc_tma.cu", "tn_device.h", "tn_internal.h")   # the TMA step kernel and its headers
+# the sources of each kernel kind with a traffic record (kernel and headers)
+_BOX = ("stream.cu", "tn_device.h", "tn_internal.h", "tn_smem.h")
+TRAFFIC_SOURCES = {"contract_step_tcgen05_tma": ("tc_tma.cu", "tn_device.h", "tn_internal.h"),
+                   "contract_step_fp32_box": _BOX, "contract_step_fp32_box_tc_fallback": _BOX,
+                   "gate_svd_fp64": ("evolve.cu", "tn_internal.h", "tn_smem.h")}
 
 
-def source_sha():
-    """Hash of the TMA step kernel's sources: a traffic record taken on other sources is stale."""
+def source_sha(kind="contract_step_tcgen05_tma"):
+    """Hash of a kernel kind's sources: a traffic record taken on other sources is stale."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2011_02621_gb300", "csrc")
-    for f in TRAFFIC_SOURCES:
+    for f in TRAFFIC_SOURCES.get(kind, TRAFFIC_SOURCES["contract_step_tcgen05_tma"]):
         h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -531,6 +535,8 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=64, help="reference arm: oracle bitstrings per step")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--profile-only", action="store_true", help="short run for ncu captures")
+    ap.add_argument("--profile-network", default="double_layer", choices=["double_layer", "overlap"],
+                    help="with --profile-only: the network whose step is profiled")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="serving stream length (0: skip)")
     ap.add_argument("--serve", action="store_true", help="serving comparison only: BF16x6 vs FP64 (one line)")
     ap.add_argument("--no-tune", action="store_true", help="keep the shape heuristic's step kernels")
@@ -577,7 +583,8 @@ def main():
     c = tn.tn_build(w.graph.n, w.graph.edges, w.gates)
     tn.tn_evolve_two_sided(c, w.split, w.chi, w.cutoff)
     # the double-layer network with joined partial paths: the fastest plan of the library
-    plan = tn.tn_path(c, layers=2, mem_budget_bytes=args.mem_gib * 2 ** 30)
+    overlap_only = args.profile_only and args.profile_network == "overlap"
+    plan = tn.tn_path(c, layers=1 if overlap_only else 2, mem_budget_bytes=args.mem_gib * 2 ** 30)
     info = plan.info
     tuned = None if args.no_tune else tn.tn_autotune(plan, args.prec, B, stream=stream)
     bits_dev = torch.from_numpy(packed.view(np.int64).copy()).cuda()

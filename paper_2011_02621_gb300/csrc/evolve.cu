@@ -524,11 +524,13 @@ cudaError_t launch_apply1(const Apply1Params &a, double2 *base, int64_t item_str
   return cudaGetLastError();
 }
 
-// One merged node tensor per item (grid.y strides over items): each thread one output element,
-// the sum over the shared leg in index order, in FP64.
+// Merged node tensors: one output element o of one item per thread, o fastest, so that when the
+// merged tensor is small (tens of elements for a joined pair of bra tensors) a block covers
+// several items; the sum over the shared leg in index order, in FP64.
 __global__ void merge_kernel(MergeParams m, double2 *base, int64_t item_stride, int64_t items) {
-  const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (o >= m.out_size) return;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= items * m.out_size) return;
+  const int64_t item = idx / m.out_size, o = idx % m.out_size;
   int64_t r = o, iu = 0, iv = 0;
   for (int j = m.nv - 1; j >= 0; --j) {
     iv += (r % m.dv[j]) * m.sv[j];
@@ -540,25 +542,22 @@ __global__ void merge_kernel(MergeParams m, double2 *base, int64_t item_stride, 
   }
   iv += (r % m.pv) * m.sv_p;
   iu += (r / m.pv) * m.su_p;
-  for (int64_t item = blockIdx.y; item < items; item += gridDim.y) {
-    const double2 *U = base + item * item_stride + m.u_off + iu;
-    const double2 *V = base + item * item_stride + m.v_off + iv;
-    double2 acc = make_double2(0.0, 0.0);
-    for (int x = 0; x < m.da; ++x) {
-      const double2 u = U[x * m.su_a], v = V[x * m.sv_a];
-      acc.x = fma(u.x, v.x, fma(-u.y, v.y, acc.x));
-      acc.y = fma(u.x, v.y, fma(u.y, v.x, acc.y));
-    }
-    base[item * item_stride + m.out_off + o] = acc;
+  const double2 *U = base + item * item_stride + m.u_off + iu;
+  const double2 *V = base + item * item_stride + m.v_off + iv;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int x = 0; x < m.da; ++x) {
+    const double2 u = U[x * m.su_a], v = V[x * m.sv_a];
+    acc.x = fma(u.x, v.x, fma(-u.y, v.y, acc.x));
+    acc.y = fma(u.x, v.y, fma(u.y, v.x, acc.y));
   }
+  base[item * item_stride + m.out_off + o] = acc;
 }
 
 cudaError_t launch_merge(const MergeParams &m, double2 *base, int64_t item_stride, int64_t items, cudaStream_t st) {
   if (items <= 0 || m.out_size <= 0) return cudaSuccess;
-  const int64_t gx = (m.out_size + 255) / 256;
-  if (gx > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-  merge_kernel<<<dim3((unsigned)gx, (unsigned)(items < 65535 ? items : 65535)), 256, 0, st>>>(m, base, item_stride,
-                                                                                             items);
+  const int64_t blocks = (items * m.out_size + 255) / 256;
+  if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  merge_kernel<<<(unsigned)blocks, 256, 0, st>>>(m, base, item_stride, items);
   tn_count_launch(1);
   return cudaGetLastError();
 }

@@ -56,9 +56,9 @@ def test_traffic_record_is_dropped_when_the_kernel_sources_change(tmp_path, monk
     (tmp_path / "profiles").mkdir()
     (tmp_path / "profiles" / "traffic.json").write_text(json.dumps(rec))
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    monkeypatch.setattr(bench, "source_sha", lambda: rec["contract_step_tcgen05_tma"]["source_sha"])
+    monkeypatch.setattr(bench, "source_sha", lambda kind=None: rec["contract_step_tcgen05_tma"]["source_sha"])
     assert bench.traffic_record("contract_step_tcgen05_tma")["dram_bytes_per_bitstring_step"] == 100.0
     r = bench.roofline(_prof("contract_step_tcgen05_tma", 10, 10.0, 1e10, 1e12), 2, "bf16x6", bench.peaks(), 1000)
     assert r["traffic"] == pytest.approx(100.0 * 1000 / 5)      # scaled to one launch's bitstrings
-    monkeypatch.setattr(bench, "source_sha", lambda: "0" * 16)
+    monkeypatch.setattr(bench, "source_sha", lambda kind=None: "0" * 16)
     assert bench.traffic_record("contract_step_tcgen05_tma") is None
