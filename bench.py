@@ -184,14 +184,15 @@ class Clocks:
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
-def traffic_record(kind):
-    """DRAM bytes of `kind` per bitstring and step, from a committed ncu capture of a small case
-    (profiles/traffic.json), if the kernel sources are unchanged since the capture."""
+def traffic_record(kind, network="double_layer"):
+    """DRAM bytes of `kind` on `network`'s plan relative to its algorithmic bytes, from a committed
+    ncu capture of a small case (profiles/traffic.json), if the kernel sources are unchanged since
+    the capture."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
-    rec = d.get(kind)
+    rec = d.get(network, {}).get(kind)
     if not rec or rec.get("source_sha") != source_sha(kind):
         return None
     return rec
@@ -370,7 +371,7 @@ def serving_run(tn, np, prec, seconds, load=0.8, seed=2011_02621 + 5, plans=None
                       "arrival_rate_per_s": lam, "max_inflight_seen": st["max_inflight_seen"]})
 
 
-def roofline(prof, steps, prec, pk, n_bits):
+def roofline(prof, steps, prec, pk, n_bits, network="double_layer"):
     """The roofline object of the dominant kernel kind of a profiled run: which roof binds it
     (tensor pipe for tcgen05, plain ALU for SIMT FP32 / FP64, else HBM, by its algorithmic
     intensity against the ridge of its compute roof), achieved against that peak, and the DRAM
@@ -395,9 +396,10 @@ def roofline(prof, steps, prec, pk, n_bits):
     else:
         roof = {"bound": "hbm", "achieved": bytes_pl / per_launch_s / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    tr = traffic_record(kind)
-    # scaled to this run's launches by the bitstrings they process (traffic grows in proportion)
-    roof["traffic"] = tr["dram_bytes_per_bitstring_step"] * n_bits / (rec["launches"] / steps) if tr else None
+    tr = traffic_record(kind, network)
+    # per launch: the captured kernel's DRAM bytes per algorithmic byte times this run's algorithmic
+    # bytes per launch (the capture runs a small case whose steps and batch differ from this run's)
+    roof["traffic"] = tr["dram_over_algorithmic"] * bytes_pl if tr else None
     roof.update({"kernel": kind, "launches_per_step": rec["launches"] / steps,
                  "algorithmic_bytes_per_launch": bytes_pl, "algorithmic_flops_per_launch": flops_pl,
                  "avg_launch_ms": per_launch_s * 1000,
@@ -622,7 +624,10 @@ def main():
         torch.cuda.synchronize()
         torch.cuda.profiler.stop()
         if rank == 0:
-            print(json.dumps({"profile_only": True, "info": info}))
+            ks = tn.tn_plan_kernels(plan, args.prec)
+            _, _, mkn = tn.tn_plan_details(plan)
+            print(json.dumps({"profile_only": True, "info": info, "bitstrings": B, "chunk": info["chunk_bitstrings"],
+                              "steps": [[int(x) for x in r] for r in mkn], "kernels": ks}))
         return 0
 
     clocks = Clocks(local)
@@ -710,7 +715,7 @@ def main():
             out2 = torch.empty(B, dtype=torch.complex128, device="cuda")
             ts, prof2, _ = form_run(tn, np, torch, c, w, p_ov, bits_dev, out2, "bf16x6", sec_steps, sec_warm, flush)
             e2 = np.abs(out2.cpu().numpy()[idx] - a64) / rms
-            roof2 = roofline(prof2, sec_steps, "bf16x6", pk, B)
+            roof2 = roofline(prof2, sec_steps, "bf16x6", pk, B, network="overlap")
             line["overlap_network"] = {
                 "value": r3(B / ts * float(np.mean(e2 <= TOL))), "ms_per_step": r3(1000 * ts),
                 "max_rel_err": r3(float(e2.max())), "plan": r3({k: p_ov.info[k] for k in ("n_steps", "cmacs")}),

@@ -52,13 +52,17 @@ def test_kernel_table_is_sorted_by_time_per_step():
 
 
 def test_traffic_record_is_dropped_when_the_kernel_sources_change(tmp_path, monkeypatch):
-    rec = {"contract_step_tcgen05_tma": {"dram_bytes_per_bitstring_step": 100.0, "source_sha": bench.source_sha()}}
+    """A network's record gives the kernel's DRAM bytes per algorithmic byte; the roofline scales it to
+    the run's algorithmic bytes per launch, and drops it once the kernel's sources hash differently."""
+    kind = "contract_step_tcgen05_tma"
+    rec = {"overlap": {kind: {"dram_over_algorithmic": 0.9, "source_sha": bench.source_sha(kind)}}}
     (tmp_path / "profiles").mkdir()
     (tmp_path / "profiles" / "traffic.json").write_text(json.dumps(rec))
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    monkeypatch.setattr(bench, "source_sha", lambda kind=None: rec["contract_step_tcgen05_tma"]["source_sha"])
-    assert bench.traffic_record("contract_step_tcgen05_tma")["dram_bytes_per_bitstring_step"] == 100.0
-    r = bench.roofline(_prof("contract_step_tcgen05_tma", 10, 10.0, 1e10, 1e12), 2, "bf16x6", bench.peaks(), 1000)
-    assert r["traffic"] == pytest.approx(100.0 * 1000 / 5)      # scaled to one launch's bitstrings
+    monkeypatch.setattr(bench, "source_sha", lambda kind=None: rec["overlap"][kind]["source_sha"])
+    assert bench.traffic_record(kind, "overlap")["dram_over_algorithmic"] == 0.9
+    assert bench.traffic_record(kind, "double_layer") is None           # another network's plan
+    r = bench.roofline(_prof(kind, 10, 10.0, 1e10, 1e12), 2, "bf16x6", bench.peaks(), 1000, network="overlap")
+    assert r["traffic"] == pytest.approx(0.9 * 1e10 / 10)               # per launch
     monkeypatch.setattr(bench, "source_sha", lambda kind=None: "0" * 16)
-    assert bench.traffic_record("contract_step_tcgen05_tma") is None
+    assert bench.traffic_record(kind, "overlap") is None
