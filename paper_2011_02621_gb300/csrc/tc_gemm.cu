@@ -24,6 +24,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "tc_ptx.h"
 #include "tn_device.h"
 #include "tn_internal.h"
 
@@ -33,59 +34,14 @@ constexpr int TC_THREADS = 256;   // 8 warps: all load and split operands, warp 
 constexpr int BM = 128;          // rows per tile (M of the MMA)
 constexpr long long WAIT_CYCLES = 500000000LL;    // ~0.25 s at 2 GHz
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
+using tcx::s_u32;
 
 // 128B swizzle (Swizzle<3,4,3>): XOR the 16-byte chunk index with the row within the 8-row atom
 __device__ __forceinline__ uint32_t swz(uint32_t off) { return off ^ (((off >> 7) & 7u) << 4); }
 
-// shared-memory matrix descriptor, K-major, SWIZZLE_128B, 8-row atoms 1024 bytes apart
-__device__ __forceinline__ uint64_t make_desc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-  d |= (uint64_t)(1u) << 16;                    // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)((1024u >> 4) & 0x3FFFu) << 32; // stride byte offset: next 8-row group
-  d |= (uint64_t)1 << 46;                       // descriptor version for tcgen05
-  d |= (uint64_t)2 << 61;                       // SWIZZLE_128B
-  return d;
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t a, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(a), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
 // bounded wait: false (and an error code) if the phase did not complete within the limit
-__device__ bool mbar_wait(uint32_t a, uint32_t parity, int *err, int code) {
-  const long long t0 = clock64();
-  while (!mbar_try_wait(a, parity)) {
-    if (clock64() - t0 > WAIT_CYCLES) {
-      atomicCAS(err, 0, code);
-      return false;
-    }
-  }
-  return true;
-}
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-__device__ __forceinline__ void mma_commit(uint32_t mbar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
-               : "memory");
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, int *err, int code) {
+  return tcx::bar_wait(a, parity, err, code, WAIT_CYCLES);
 }
 
 __device__ __forceinline__ float tf32_rna(float x) {
@@ -199,12 +155,12 @@ tc_step_kernel(StepParams s, ContractArgs a, const float2 *__restrict__ cbuf, in
   const int32_t *ocol = a.tab + s.t_ocol;
 
   if (tid == 0) {
-    mbar_init(smem_u32(&mbar[0]), 1);
-    mbar_init(smem_u32(&mbar[1]), 1);
+    tcx::bar_init(s_u32(&mbar[0]), 1);
+    tcx::bar_init(s_u32(&mbar[1]), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_s)),
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(s_u32(&tmem_base_s)),
                  "r"(TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
@@ -228,9 +184,9 @@ tc_step_kernel(StepParams s, ContractArgs a, const float2 *__restrict__ cbuf, in
     }
     rowoff[tid] = off;                           // output row offset in the next layout
   }
-  tc_fence_before();
+  tcx::fence_before();
   __syncthreads();
-  tc_fence_after();
+  tcx::fence_after();
   const uint32_t tmem = tmem_base_s;
   const uint32_t idesc = make_idesc_k<KIND>(BN);
   const int64_t nk = (s.K + BKC - 1) / BKC;
@@ -262,7 +218,7 @@ tc_step_kernel(StepParams s, ContractArgs a, const float2 *__restrict__ cbuf, in
     uint8_t *Ab = smem + st * STAGE, *Bb = Ab + P * A_BYTES;
     if (kc >= 2 && !bad) {
       // the MMAs that last read this stage (chunk kc-2) must be complete before it is overwritten
-      if (!mbar_wait(smem_u32(&mbar[st]), (uint32_t)(((kc - 2) >> 1) & 1), err, 1)) bad = true;
+      if (!mbar_wait(s_u32(&mbar[st]), (uint32_t)(((kc - 2) >> 1) & 1), err, 1)) bad = true;
     }
     if (__syncthreads_or(bad)) { bad = true; break; }
     // ---- A tile (rows of T_in) and B tile (real embedding of C: row 2n (Re, -Im), row 2n+1 (Im, Re))
@@ -278,18 +234,18 @@ tc_step_kernel(StepParams s, ContractArgs a, const float2 *__restrict__ cbuf, in
       st_pieces<KIND, P>(Bb, B_BYTES, 2 * nl + 1, 2 * kk, vb[i].y, vb[i].x);
     }
     if (kc + 1 < nk) load_chunk(kc + 1);         // next chunk's loads overlap this chunk's MMAs
-    fence_async_smem();
+    tcx::fence_async_smem();
     __syncthreads();
     if (tid == 0) {
-      tc_fence_after();
-      const uint32_t a0 = smem_u32(Ab), b0 = smem_u32(Bb);
+      tcx::fence_after();
+      const uint32_t a0 = s_u32(Ab), b0 = s_u32(Bb);
 #pragma unroll
       for (int ks = 0; ks < KSTEPS; ++ks) {
         const uint32_t off = (uint32_t)ks * 32u;
         const int64_t t = kc * KSTEPS + ks;           // global k-step
         const bool first = (t == 0);
         // order 0 -> accumulator t % R (first use: t < R); order o >= 1 -> accumulator R + o - 1
-        Op<KIND>::mma(tmem + (uint32_t)((t % R) * BN), make_desc(a0 + off), make_desc(b0 + off), idesc,
+        Op<KIND>::mma(tmem + (uint32_t)((t % R) * BN), tcx::desc_sw128(a0 + off), tcx::desc_sw128(b0 + off), idesc,
                       t < R ? 0u : 1u);
 #pragma unroll
         for (int o = 1; o <= ORD; ++o) {
@@ -298,12 +254,12 @@ tc_step_kernel(StepParams s, ContractArgs a, const float2 *__restrict__ cbuf, in
             const int j = o - i;
             if (j < 0 || j >= P) continue;
             const uint32_t acc = (first && i == (o < P ? 0 : o - P + 1)) ? 0u : 1u;
-            Op<KIND>::mma(tmem + (uint32_t)((R + o - 1) * BN), make_desc(a0 + i * A_BYTES + off),
-                          make_desc(b0 + j * B_BYTES + off), idesc, acc);
+            Op<KIND>::mma(tmem + (uint32_t)((R + o - 1) * BN), tcx::desc_sw128(a0 + i * A_BYTES + off),
+                          tcx::desc_sw128(b0 + j * B_BYTES + off), idesc, acc);
           }
         }
       }
-      mma_commit(smem_u32(&mbar[st]));
+      tcx::mma_commit_to(s_u32(&mbar[st]));
     }
     ++issued;
   }
@@ -311,10 +267,10 @@ tc_step_kernel(StepParams s, ContractArgs a, const float2 *__restrict__ cbuf, in
   // so that no MMA is still reading shared memory or writing TMEM when the CTA frees them
   if (issued > 0) {
     const int64_t last = issued - 1;
-    if (!mbar_wait(smem_u32(&mbar[last & 1]), (uint32_t)((last >> 1) & 1), err, 2)) bad = true;
+    if (!mbar_wait(s_u32(&mbar[last & 1]), (uint32_t)((last >> 1) & 1), err, 2)) bad = true;
   }
   bad = __syncthreads_or(bad);
-  tc_fence_after();
+  tcx::fence_after();
   if (!bad && issued == nk) {
     // ---- epilogue: warp w reads TMEM lanes 32(w%4).. (rows) and half (w/4) of the columns, 16 at a
     // time, and adds the accumulators from the smallest up
@@ -349,7 +305,7 @@ tc_step_kernel(StepParams s, ContractArgs a, const float2 *__restrict__ cbuf, in
       }
     }
   }
-  tc_fence_before();
+  tcx::fence_before();
   __syncthreads();
   if (warp == 0) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");

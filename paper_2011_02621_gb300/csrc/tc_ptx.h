@@ -1,4 +1,6 @@
-// Inline-PTX helpers for the tcgen05 / TMA / mbarrier kernels (sm_100a family).
+// Inline-PTX helpers shared by the tcgen05 / TMA / mbarrier kernels (sm_100a family): the
+// TMA-fed step (tc_tma.cu), its persistent form (tc_tma_persist.cu) and the step with the operand
+// split in the kernel (tc_gemm.cu).
 #pragma once
 
 #include <cuda.h>
@@ -85,6 +87,11 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t ad, uint64_t bd
 __device__ __forceinline__ void mma_commit_to(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// make generic-proxy writes to shared memory visible to the async proxy (the MMA's operand reads)
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 __device__ __forceinline__ void sts128(uint32_t a, const uint32_t w[4]) {
   asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3])

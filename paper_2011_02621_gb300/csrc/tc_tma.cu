@@ -31,6 +31,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "tc_ptx.h"
 #include "tn_device.h"
 #include "tn_internal.h"
 
@@ -41,88 +42,22 @@ constexpr int T_BM = 128;
 constexpr int T_P = 3;
 constexpr long long T_WAIT = 500000000LL;   // ~0.25 s at 2 GHz
 
-__device__ __forceinline__ uint32_t s_u32(const void *p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
+using tcx::bar_arrive;
+using tcx::bar_expect_tx;
+using tcx::bar_init;
+using tcx::desc_sw128;
+using tcx::mma_bf16;
+using tcx::mma_commit_to;
+using tcx::s_u32;
+using tcx::sts128;
+using tcx::sw128_off;
+using tcx::tma_3d;
 
-__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-  d |= (uint64_t)1 << 16;                        // leading byte offset (unused, swizzled K-major)
-  d |= (uint64_t)(1024u >> 4) << 32;             // stride byte offset: next 8-row group
-  d |= (uint64_t)1 << 46;                        // descriptor version for tcgen05
-  d |= (uint64_t)2 << 61;                        // SWIZZLE_128B
-  return d;
-}
+__device__ __forceinline__ uint32_t idesc_bf16(int bn) { return tcx::idesc_bf16(T_BM, bn); }
 
-__device__ __forceinline__ uint32_t idesc_bf16(int bn) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(bn >> 3) << 17) | ((uint32_t)(T_BM >> 4) << 24);
-}
-
-__device__ __forceinline__ void bar_init(uint32_t a, uint32_t n) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(n) : "memory");
-}
-
-__device__ __forceinline__ bool bar_try(uint32_t a, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(a), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-__device__ bool bar_wait(uint32_t a, uint32_t parity, int *err, int code) {
-  const long long t0 = clock64();
-  while (!bar_try(a, parity)) {
-    if (clock64() - t0 > T_WAIT) {
-      atomicCAS(err, 0, code);
-      return false;
-    }
-  }
-  return true;
-}
-
-__device__ __forceinline__ void bar_expect_tx(uint32_t a, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ void tma_3d(uint32_t dst, const CUtensorMap *map, int x, int y, int z, uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
-      "[%5];" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
-      : "memory");
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-      "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
-      : "memory");
-}
-
-__device__ __forceinline__ void bar_arrive(uint32_t a) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
-}
-
-__device__ __forceinline__ void sts128(uint32_t a, const uint32_t w[4]) {
-  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3])
-               : "memory");
-}
-
-// byte offset of 16-byte chunk c of row r in a 128-byte-swizzled K-major tile (1024-byte aligned):
-// rows of 128 bytes, groups of 8 rows, chunk index XOR (row mod 8) -- the layout TMA writes with
-// CU_TENSOR_MAP_SWIZZLE_128B and the MMA descriptor reads with layout type SWIZZLE_128B
-__device__ __forceinline__ uint32_t sw128_off(int r, int c) {
-  return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((c ^ (r & 7)) << 4));
-}
-
-__device__ __forceinline__ void mma_commit_to(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+// bounded wait: after T_WAIT clocks the error code is recorded and the wait gives up
+__device__ __forceinline__ bool bar_wait(uint32_t a, uint32_t parity, int *err, int code) {
+  return tcx::bar_wait(a, parity, err, code, T_WAIT);
 }
 
 }  // namespace
