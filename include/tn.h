@@ -398,7 +398,10 @@ int64_t tn_launch_count(int32_t reset);
  * with its algorithmic bytes and flops. tn_profile_enable(1) clears the
  * records; tn_profile_read synchronises the recorded events and returns kind
  * `idx` (TN_ERR_ARG past the last kind): name (NUL-terminated, at most
- * name_len bytes), launches, total milliseconds, algorithmic bytes and flops. */
+ * name_len bytes), launches, total milliseconds, algorithmic bytes and flops.
+ * on = 2 keeps one record per kind and contraction step: the launches of
+ * the step at index i of the lists of tn_plan_details and tn_plan_kernels
+ * are named "<kind>#i". on = 0 stops recording. */
 tn_status tn_profile_enable(int32_t on);
 tn_status tn_profile_read(int32_t idx, char *name, int32_t name_len, int64_t *launches, double *ms,
                           double *bytes, double *flops);

@@ -19,7 +19,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtn.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
-CU = ["evolve.cu", "contract.cu", "tc_gemm.cu", "tc_tma.cu", "tc_tma_persist.cu", "static_scratch.cu", "stream.cu"]
+CU = ["evolve.cu", "contract.cu", "tc_gemm.cu", "tc_tma.cu", "tc_tma_persist.cu", "tc_tma_persist_loadb.cu",
+      "static_scratch.cu", "stream.cu"]
 CPP = ["host.cpp", "server.cpp", "tune.cpp", "batch.cpp"]
 
 
@@ -46,10 +47,23 @@ def _stale() -> bool:
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = _sources() + [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith(".h")]
+    deps = _sources() + [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".h", ".cuh"))]
     deps.append(os.path.join(ROOT, "include", "tn.h"))
     deps.append(__file__)
     return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
+
+
+def _big_stack():
+    """The compiler's optimiser recurses deeply on the large unrolled tensor-core kernels; on some
+    hosts the default 8 MiB stack is too small for it, so the build raises its own soft stack
+    limit to the hard one (the compiles inherit it)."""
+    try:
+        import resource
+        soft, hard = resource.getrlimit(resource.RLIMIT_STACK)
+        want = hard if hard == resource.RLIM_INFINITY else max(soft, hard)
+        resource.setrlimit(resource.RLIMIT_STACK, (want, hard))
+    except (ImportError, ValueError, OSError):
+        pass
 
 
 def _run(cmd):
@@ -66,6 +80,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     cuda = cuda_home()
     nvcc = os.path.join(cuda, "bin", "nvcc")
     os.makedirs(BUILD, exist_ok=True)
+    _big_stack()
     inc = ["-I" + CSRC, "-I" + os.path.join(ROOT, "include"), "-I" + os.path.join(cuda, "include")]
     jobs = []
     for f in _sources():

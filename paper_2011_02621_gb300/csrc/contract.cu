@@ -283,7 +283,7 @@ step_stream_kernel(StepParams s, ContractArgs a, const typename C2T<R>::T *ket, 
   __syncthreads();
   const V *tp = tin + item * a.t_stride;
   const int64_t m1 = m0 + rows_per_cta < s.M ? m0 + rows_per_cta : s.M;
-  const bool four = (N == 4 && oc[3] - oc[0] == 3);   // the four outputs of a row are contiguous
+  const bool four = (N == 4 && oc[1] == oc[0] + 1 && oc[2] == oc[0] + 2 && oc[3] == oc[0] + 3);   // consecutive
   for (int64_t m = m0 + tid; m < m1; m += 256) {
     V x[16];
 #pragma unroll
@@ -316,35 +316,60 @@ step_stream_kernel(StepParams s, ContractArgs a, const typename C2T<R>::T *ket, 
   }
 }
 
-// The same streaming step with K and N fixed at compile time (small register footprint).
+// The same streaming step with K and N fixed at compile time (small register footprint): a
+// thread holds its row of T_in in registers (16-byte loads for complex64 when K is even), and
+// each group of four columns whose outputs are adjacent in the next layout goes out as one
+// four-wide store.
 template <typename R, int KK, int NN>
 __global__ void __launch_bounds__(256)
 step_stream_fixed(StepParams s, ContractArgs a, const typename C2T<R>::T *ket, const typename C2T<R>::T *bra,
                   const typename C2T<R>::T *tin, OutDesc out, int64_t rows_per_cta) {
   using V = typename C2T<R>::T;
+  constexpr int NQ = (NN + 3) / 4;
   __shared__ V Cs[KK * NN];
   __shared__ int oc[NN];
+  __shared__ int four[NQ];
   const int tid = threadIdx.x;
   const int64_t ctas_m = (s.M + rows_per_cta - 1) / rows_per_cta;
   const int64_t item = blockIdx.x / ctas_m;
   const int64_t m0 = (blockIdx.x % ctas_m) * rows_per_cta;
   ItemCtx c = item_ctx(a, s, item);
-  if (tid < KK * NN) {
+  {
     const V *kp = ket + s.ket_off + c.sa;
     const V *bp = bra + c.b * a.bra_stride + s.bra_off + c.sb;
-    const int k = tid / NN, n = tid % NN;
-    Cs[tid] = overlap_elem(kp, bp, (int64_t)a.tab[s.t_bka + k] + a.tab[s.t_bna + n],
+    for (int i = tid; i < KK * NN; i += 256) {
+      const int k = i / NN, n = i - k * NN;
+      Cs[i] = overlap_elem(kp, bp, (int64_t)a.tab[s.t_bka + k] + a.tab[s.t_bna + n],
                            (int64_t)a.tab[s.t_bkb + k] + a.tab[s.t_bnb + n], s.ket_sig, s.bra_sig, s.phys);
+    }
   }
   if (tid < NN) oc[tid] = a.tab[s.t_ocol + tid];
   __syncthreads();
+  if (tid < NQ) {   // columns 4q .. 4q + 3 land on consecutive offsets
+    bool f = NN % 4 == 0;
+    if (f)
+      for (int j = 1; j < 4; ++j) f = f && oc[4 * tid + j] == oc[4 * tid] + j;
+    four[tid] = f;
+  }
+  __syncthreads();
   const V *tp = tin + item * a.t_stride;
   const int64_t m1 = m0 + rows_per_cta < s.M ? m0 + rows_per_cta : s.M;
-  const bool four = (NN == 4 && oc[3] - oc[0] == 3);
   for (int64_t m = m0 + tid; m < m1; m += 256) {
     V x[KK];
+    if constexpr (sizeof(V) == 8 && KK % 2 == 0) {
+      const float4 *src = reinterpret_cast<const float4 *>(tp + m * KK);
 #pragma unroll
-    for (int k = 0; k < KK; ++k) x[k] = tp[m * KK + k];
+      for (int k = 0; k < KK; k += 2) {
+        const float4 q = src[k / 2];
+        x[k].x = q.x;
+        x[k].y = q.y;
+        x[k + 1].x = q.z;
+        x[k + 1].y = q.w;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < KK; ++k) x[k] = tp[m * KK + k];
+    }
     const int ro = orow_of(s, m);
     R v[2 * NN];
 #pragma unroll
@@ -355,15 +380,18 @@ step_stream_fixed(StepParams s, ContractArgs a, const typename C2T<R>::T *ket, c
       v[2 * n] = acc.x;
       v[2 * n + 1] = acc.y;
     }
-    if (NN == 4 && four) {
-      store_out4(out, a.t_stride, item, ro + oc[0], v);
-    } else {
 #pragma unroll
-      for (int n = 0; n < NN; ++n) {
-        V t;
-        t.x = v[2 * n];
-        t.y = v[2 * n + 1];
-        store_out(out, a.t_stride, item, ro + oc[n], t);
+    for (int q = 0; q < NQ; ++q) {
+      if (NN % 4 == 0 && four[q]) {
+        store_out4(out, a.t_stride, item, ro + oc[4 * q], v + 8 * q);
+      } else {
+#pragma unroll
+        for (int n = 4 * q; n < 4 * q + 4 && n < NN; ++n) {
+          V t;
+          t.x = v[2 * n];
+          t.y = v[2 * n + 1];
+          store_out(out, a.t_stride, item, ro + oc[n], t);
+        }
       }
     }
   }
@@ -463,20 +491,24 @@ cudaError_t launch_form_b_pieces(const StepParams &s, const ContractArgs &a, con
 
 // (K, N) pairs with a compile-time streaming kernel
 #define TN_FIXED_LIST(X) \
-  X(4, 4) X(1, 4) X(4, 1) X(2, 2) X(2, 4) X(4, 2) X(1, 2) X(2, 1) X(4, 16) X(16, 4) X(16, 1) X(1, 16)
+  X(4, 4) X(1, 4) X(4, 1) X(2, 2) X(2, 4) X(4, 2) X(1, 2) X(2, 1) X(4, 16) X(16, 4) X(16, 1) X(1, 16) \
+  X(8, 8) X(8, 4) X(4, 8) X(8, 2) X(2, 8) X(16, 16) X(16, 8) X(8, 16)
 
-static bool has_fixed(int64_t K, int64_t N) {
-#define TN_HAS(k, n) if (K == k && N == n) return true;
+// complex128 keeps to K * N <= 32: a larger C tile held in registers spills
+template <typename R> constexpr bool fixed_fits(int k, int n) { return sizeof(R) == 4 || k * n <= 32; }
+
+static bool has_fixed(int64_t K, int64_t N, bool fp64) {
+#define TN_HAS(k, n) if (K == k && N == n) return fp64 ? fixed_fits<double>(k, n) : fixed_fits<float>(k, n);
   TN_FIXED_LIST(TN_HAS)
 #undef TN_HAS
   return false;
 }
 
-bool simt_variant_ok(const StepParams &s, int v) {
+bool simt_variant_ok(const StepParams &s, int v, bool fp64) {
   switch (v) {
     case SIMT_AUTO: case SIMT_T64: case SIMT_T128: case SIMT_T256: return true;
     case SIMT_STREAM: return s.K <= 16 && s.N <= 16;
-    case SIMT_FIXED: return has_fixed(s.K, s.N);
+    case SIMT_FIXED: return has_fixed(s.K, s.N, fp64);
     case SIMT_SMALL: return s.M * s.N <= 256;
     case SIMT_NARROW: return s.M <= 16 && s.M * s.K <= 2048;
     case SIMT_BOX: return s.box_tm > 0 && s.K * s.N <= TN_BOX_MAXKN && s.N <= TN_BOX_MAXN;
@@ -489,9 +521,9 @@ cudaError_t launch_step(const StepParams &s, const ContractArgs &a, const void *
                         const void *t_in, const OutDesc &t_out, cudaStream_t st, int variant) {
   using V = typename C2T<R>::T;
   if (a.items <= 0) return cudaSuccess;
-  if (!simt_variant_ok(s, variant)) return cudaErrorInvalidValue;
+  if (!simt_variant_ok(s, variant, sizeof(R) == 8)) return cudaErrorInvalidValue;
   if (variant == SIMT_AUTO) {   // the shape heuristic
-    if (s.M >= 512 && has_fixed(s.K, s.N)) variant = SIMT_FIXED;
+    if (s.M >= 512 && has_fixed(s.K, s.N, sizeof(R) == 8)) variant = SIMT_FIXED;
     else if (s.K <= 16 && s.N <= 16 && s.M >= 512) variant = SIMT_STREAM;
     else if (s.M * s.N <= 16) variant = SIMT_SMALL;
     else if (s.M <= 16 && s.M * s.K <= 2048 && s.N >= 256) variant = SIMT_NARROW;
@@ -500,8 +532,11 @@ cudaError_t launch_step(const StepParams &s, const ContractArgs &a, const void *
   switch (variant) {
     case SIMT_BOX: return launch_step_box<R>(s, a, ket, bra, t_in, t_out, st);
     case SIMT_FIXED:
-#define TN_FIXED(k, n) \
-  if (s.K == k && s.N == n) return launch_stream_fixed<R, k, n>(s, a, ket, bra, t_in, t_out, st);
+#define TN_FIXED(k, n)                                                                   \
+  if (s.K == k && s.N == n) {                                                            \
+    if constexpr (fixed_fits<R>(k, n)) return launch_stream_fixed<R, k, n>(s, a, ket, bra, t_in, t_out, st); \
+    return cudaErrorInvalidValue;                                                        \
+  }
       TN_FIXED_LIST(TN_FIXED)
 #undef TN_FIXED
       return cudaErrorInvalidValue;

@@ -19,6 +19,7 @@
 #include <unordered_set>
 #include <vector>
 
+#include "tc_persist.h"
 #include "tn_host.h"
 
 typedef std::complex<double> cd;
@@ -75,6 +76,8 @@ struct ProfRec {
 };
 std::mutex g_prof_mu;
 bool g_prof_on = false;
+bool g_prof_steps = false;              // one record per contraction step
+thread_local int g_prof_step = -1;      // the contraction step this thread enqueues (-1: none)
 std::vector<ProfKind> g_kinds;
 std::vector<ProfRec> g_recs;
 std::vector<cudaEvent_t> g_event_pool;
@@ -113,12 +116,14 @@ ProfScope::ProfScope(const char *kind, cudaStream_t stream, double bytes, double
   }
   std::lock_guard<std::mutex> lk(g_prof_mu);
   if (!g_prof_on) return;
+  std::string name = kind;
+  if (g_prof_steps && g_prof_step >= 0) name += "#" + std::to_string(g_prof_step);
   int k = -1;
   for (size_t i = 0; i < g_kinds.size(); ++i)
-    if (g_kinds[i].name == kind) k = (int)i;
+    if (g_kinds[i].name == name) k = (int)i;
   if (k < 0) {
     g_kinds.push_back(ProfKind());
-    g_kinds.back().name = kind;
+    g_kinds.back().name = name;
     k = (int)g_kinds.size() - 1;
   }
   g_kinds[k].launches += 1;
@@ -131,6 +136,9 @@ ProfScope::ProfScope(const char *kind, cudaStream_t stream, double bytes, double
   st = stream;
 }
 
+ProfStep::ProfStep(int step) { g_prof_step = step; }
+ProfStep::~ProfStep() { g_prof_step = -1; }
+
 ProfScope::~ProfScope() {
   if (slot < 0) return;
   std::lock_guard<std::mutex> lk(g_prof_mu);
@@ -142,6 +150,7 @@ extern "C" tn_status tn_profile_enable(int32_t on) {
   prof_drain();
   g_kinds.clear();
   g_prof_on = on != 0;
+  g_prof_steps = on == 2;
   return TN_OK;
 }
 
@@ -2424,10 +2433,13 @@ bool step_kernel_ok(const StepParams &s, tn_precision prec, int k) {
   // a double-layer step (one tensor and the unit operand, a zero physical stride) never uses a
   // kernel that builds the operand from node tensors staged in shared memory
   if ((s.ket_sig == 0 || s.bra_sig == 0) && sk_is_tma(k) && sk_tma_bmode(k) == 1) return false;
-  if (k < SK_TC) return simt_variant_ok(s, k);
+  if (k < SK_TC) return simt_variant_ok(s, k, prec == TN_FP64);
   if (k == SK_TC) return prec != TN_FP64 && prec != TN_FP32 && prec != TN_BF16X6 && tc_step_supported(s);
   if (!sk_is_tma(k)) return false;
   if (prec != TN_BF16X6 || !tma_step_supported(s)) return false;
+  // the persistent form keeps three order-0 accumulators at either tile width (TMEM holds two
+  // accumulator sets at 64 columns), so it takes the short-K rule of the 128-column tile
+  if (sk_tma_persist(k) && s.K >= TN_TMA_LONG_K) return false;
   return sk_tma_bn(k) != 128 || (2 * s.N >= 128 && s.K < TN_TMA_LONG_K);
 }
 
@@ -2453,11 +2465,12 @@ bool is_device_ptr(const void *p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-// The intermediate's output format: bf16 pieces when the consuming step is TMA-fed, else complex.
+// The intermediate's output format: bf16 pieces when the consuming step's kernel reads them (the
+// TMA-fed kernels but the complex64-A one), else complex.
 static OutDesc out_desc(void *buf, const std::vector<int> &ks, size_t consumer, int64_t plane_u32) {
   OutDesc o;
   o.p = buf;
-  o.fmt = (consumer < ks.size() && sk_is_tma(ks[consumer])) ? 1 : 0;
+  o.fmt = (consumer < ks.size() && sk_reads_pieces(ks[consumer])) ? 1 : 0;
   o.plane_u32 = plane_u32;
   return o;
 }
@@ -2509,16 +2522,53 @@ cudaError_t enqueue_step(const tn_plan *p, const Workspace &w, size_t j, int k, 
                            (const float2 *)bra);
   }
   if (sk_tma_bmode(k) == 2) {
+    // a ket tensor's overlap operand does not depend on the bitstring, only on the slice: items
+    // 0 .. n_slices - 1 (the first bitstring's) hold every distinct copy, formed once
+    const bool shared = j < p->step_layer.size() && p->step_layer[j] == 1;
+    const int64_t c_items = shared ? a.n_slices : a.items;
     {
-      ProfScope ps("overlap_form_c64", st, 8.0 * items * (double)sp.K * sp.N, 16.0 * items * (double)sp.K * sp.N);
-      cudaError_t e = launch_form_c(sp, a, (const float2 *)ket, (const float2 *)bra, (float2 *)w.cbuf.p, p->maxKN, st);
+      ContractArgs af = a;
+      af.items = c_items;
+      ProfScope ps("overlap_form_c64", st, 8.0 * c_items * (double)sp.K * sp.N, 16.0 * c_items * (double)sp.K * sp.N);
+      cudaError_t e = launch_form_c(sp, af, (const float2 *)ket, (const float2 *)bra, (float2 *)w.cbuf.p, p->maxKN, st);
       if (e != cudaSuccess) return e;
     }
+    if (sk_tma_c64a(k)) {
+      // algorithmic bytes: A and the overlap tensor read as complex64, output written
+      ProfScope ps("contract_step_tcgen05_tma_persist_c64a", st,
+                   items * (8.0 * (double)sp.M * sp.K + out_b) + 8.0 * c_items * (double)sp.K * sp.N, fl);
+      return launch_step_tma_persistent(sp, a, A, B, od, (int *)w.err.p + 1, st, sk_tma_bn(k),
+                                        (const float2 *)w.cbuf.p, p->maxKN, c_items, (const float2 *)tin);
+    }
     // algorithmic bytes: A pieces and the complex64 overlap tensor read, output written
-    ProfScope ps("contract_step_tcgen05_tma", st, items * (12.0 * (double)sp.M * sp.K + 8.0 * (double)sp.K * sp.N + out_b),
-                 fl);
+    const double by_c = items * (12.0 * (double)sp.M * sp.K + out_b) + 8.0 * c_items * (double)sp.K * sp.N;
+    if (sk_tma_persist(k)) {
+      ProfScope ps("contract_step_tcgen05_tma_persist", st, by_c, fl);
+      return launch_step_tma_persistent(sp, a, A, B, od, (int *)w.err.p + 1, st, sk_tma_bn(k),
+                                        (const float2 *)w.cbuf.p, p->maxKN, c_items);
+    }
+    ProfScope ps("contract_step_tcgen05_tma", st, by_c, fl);
     return launch_step_tma(sp, a, A, B, od, (int *)w.err.p + 1, st, sk_tma_bn(k), nullptr, nullptr,
-                           (const float2 *)w.cbuf.p, p->maxKN);
+                           (const float2 *)w.cbuf.p, p->maxKN, c_items);
+  }
+  if (sk_tma_persist(k)) {
+    // B pieces formed in HBM (once per slice for a ket tensor) and loaded by TMA
+    const bool shared = j < p->step_layer.size() && p->step_layer[j] == 1;
+    const int64_t c_items = shared ? a.n_slices : a.items;
+    {
+      ContractArgs af = a;
+      af.items = c_items;
+      ProfScope ps("overlap_form_bf16_pieces", st, 24.0 * c_items * (double)sp.K * sp.N,
+                   16.0 * c_items * (double)sp.K * sp.N);
+      cudaError_t e = launch_form_b_pieces(sp, af, (const float2 *)ket, (const float2 *)bra, B, st);
+      if (e != cudaSuccess) return e;
+    }
+    const bool c64a = sk_tma_c64a(k);
+    const double by_p = items * ((c64a ? 8.0 : 12.0) * (double)sp.M * sp.K + out_b) + 24.0 * c_items * (double)sp.K * sp.N;
+    ProfScope ps(c64a ? "contract_step_tcgen05_tma_persist_c64a_loadb" : "contract_step_tcgen05_tma_persist_loadb", st,
+                 by_p, fl);
+    return launch_step_tma_persistent(sp, a, A, B, od, (int *)w.err.p + 1, st, sk_tma_bn(k), nullptr, 0, c_items,
+                                      c64a ? (const float2 *)tin : nullptr);
   }
   {
     ProfScope ps("overlap_form_bf16_pieces", st, 24.0 * items * (double)sp.K * sp.N, 16.0 * items * (double)sp.K * sp.N);
@@ -2615,6 +2665,7 @@ tn_status enqueue_chunk(tn_plan *p, Workspace &w, const uint64_t *bits_dev, int6
       else CUDA_TRY(launch_form<double>(p->steps[0], aj, kj, bj, od, st));
     }
     for (size_t j = 1; j < nsteps; ++j) {
+      const ProfStep pst((int)j - 1);   // the index of the step in the plan's public lists
       operands(j, a, kj, bj, aj);
       CUDA_TRY(enqueue_step(p, w, j, ks[j], prec, aj, kj, bj, tin, tout,
                             out_desc(tout, ks, j + 1, cap * p->maxT), st));

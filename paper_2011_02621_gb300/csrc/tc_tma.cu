@@ -70,7 +70,7 @@ tma_step_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__
                 const __grid_constant__ CUtensorMap tA2, const __grid_constant__ CUtensorMap tB0,
                 const __grid_constant__ CUtensorMap tB1, const __grid_constant__ CUtensorMap tB2, StepParams s,
                 ContractArgs a, OutDesc out, int *err, const float2 *ket, const float2 *bra, const float2 *cbuf,
-                int64_t c_stride, int staged) {
+                int64_t c_stride, int64_t c_items, int staged) {
   constexpr bool BUILD = BM != 0;
   constexpr int A_BYTES = T_BM * 128, B_BYTES = BN * 128;
   constexpr int STAGE = T_P * (A_BYTES + B_BYTES);
@@ -220,7 +220,7 @@ tma_step_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__
             const int64_t n = n_base + nl, k0 = kc * 32 + c16 * 4;
             x[j][0] = x[j][1] = make_float4(0.f, 0.f, 0.f, 0.f);
             if (n < s.N && k0 < s.K) {   // K % 4 == 0: the four k are all in range or all out
-              const float4 *src = reinterpret_cast<const float4 *>(cbuf + item * c_stride + n * s.K + k0);
+              const float4 *src = reinterpret_cast<const float4 *>(cbuf + (item % c_items) * c_stride + n * s.K + k0);
               x[j][0] = __ldg(src);
               x[j][1] = __ldg(src + 1);
             }
@@ -338,18 +338,7 @@ tma_step_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__
           if (g >= R || (int64_t)g < nk * 4) v += __uint_as_float(r[g][j]);   // unwritten order-0 slots skipped
         acc[j] = v;
       }
-      if (ro >= 0) {
-        const int64_t n0 = (nr0 + c0) >> 1;    // eight complex columns n0 .. n0 + 7
-        if (n0 + 7 < s.N && ocol[n0 + 7] - ocol[n0] == 7) {
-          store_out8(out, a.t_stride, item, ro + ocol[n0], acc);
-        } else {
-#pragma unroll
-          for (int j = 0; j < 16; j += 2) {
-            const int64_t n = n0 + (j >> 1);
-            if (n < s.N) store_out(out, a.t_stride, item, ro + ocol[n], make_float2(acc[j], acc[j + 1]));
-          }
-        }
-      }
+      if (ro >= 0) store_cols8(out, a.t_stride, item, ro, ocol, (nr0 + c0) >> 1, s.N, acc);   // eight complex columns
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -390,7 +379,7 @@ bool make_map(CUtensorMap *m, const void *base, uint64_t inner, uint64_t rows, u
 template <int BN, int R, int S, int BM>
 cudaError_t launch_t(const StepParams &s, const ContractArgs &a, const Pieces &A, const Pieces &B, const OutDesc &out,
                      int *err, const float2 *ket, const float2 *bra, const float2 *cbuf, int64_t c_stride,
-                     cudaStream_t st) {
+                     int64_t c_items, cudaStream_t st) {
   constexpr bool BUILD = BM != 0;
   constexpr size_t stage = (size_t)T_P * (T_BM * 128 + BN * 128);
   // the dynamic shared memory limit on the current device (set once per device)
@@ -420,7 +409,8 @@ cudaError_t launch_t(const StepParams &s, const ContractArgs &a, const Pieces &A
   if (grid <= 0) return cudaSuccess;
   if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
   tma_step_kernel<BN, R, S, BM><<<(unsigned)grid, T_THREADS, smem, st>>>(mA[0], mA[1], mA[2], mB[0], mB[1], mB[2], s,
-                                                                         a, out, err, ket, bra, cbuf, c_stride, staged);
+                                                                         a, out, err, ket, bra, cbuf, c_stride,
+                                                                         c_items > 0 ? c_items : a.items, staged);
   tn_count_launch(1);
   return cudaGetLastError();
 }
@@ -434,15 +424,15 @@ bool tma_step_supported(const StepParams &s) {
 
 cudaError_t launch_step_tma(const StepParams &s, const ContractArgs &a, const Pieces &A, const Pieces &B,
                             const OutDesc &out, int *err, cudaStream_t st, int bn, const float2 *ket,
-                            const float2 *bra, const float2 *cbuf, int64_t c_stride) {
+                            const float2 *bra, const float2 *cbuf, int64_t c_stride, int64_t c_items) {
   if (bn == 0) bn = (2 * s.N >= 128 && s.K < TN_TMA_LONG_K) ? 128 : 64;
   const int bm = cbuf ? 2 : ket ? 1 : 0;
   if (bm == 1 && !bra) return cudaErrorInvalidValue;
 #define TN_TMA_LAUNCH(BNV, RV, SV)                                                                     \
   switch (bm) {                                                                                        \
-    case 0: return launch_t<BNV, RV, SV, 0>(s, a, A, B, out, err, ket, bra, cbuf, c_stride, st);       \
-    case 1: return launch_t<BNV, RV, SV, 1>(s, a, A, B, out, err, ket, bra, cbuf, c_stride, st);       \
-    default: return launch_t<BNV, RV, SV, 2>(s, a, A, B, out, err, ket, bra, cbuf, c_stride, st);      \
+    case 0: return launch_t<BNV, RV, SV, 0>(s, a, A, B, out, err, ket, bra, cbuf, c_stride, c_items, st);       \
+    case 1: return launch_t<BNV, RV, SV, 1>(s, a, A, B, out, err, ket, bra, cbuf, c_stride, c_items, st);       \
+    default: return launch_t<BNV, RV, SV, 2>(s, a, A, B, out, err, ket, bra, cbuf, c_stride, c_items, st);      \
   }
   if (bn == 128 && 2 * s.N >= 128 && s.K < TN_TMA_LONG_K) { TN_TMA_LAUNCH(128, 3, 2) }
   if (bn == 64) { TN_TMA_LAUNCH(64, 7, 3) }

@@ -8,21 +8,19 @@
 #include "tn_internal.h"
 #include "tn_smem.h"
 
-__device__ __forceinline__ float tn_bf16_round(float x) {   // nearest bf16, as a float
-  uint32_t r;
-  asm("{\n\t.reg .b16 h;\n\tcvt.rn.bf16.f32 h, %1;\n\tmov.b32 %0, {0, h};\n\t}" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
-}
-
-// x = x_0 + x_1 + x_2 with each x_q a bf16 value (the remainders are exact in fp32);
-// w[q] packs (re_q, im_q) as a bf16 pair, re in the low half
+// x = x_0 + x_1 + x_2 and y = y_0 + y_1 + y_2 with each piece a bf16 value (nearest, ties to
+// even; the remainders are exact in fp32); w[q] packs (x_q, y_q) as a bf16 pair, x in the low
+// half, both rounded by one instruction
 __device__ __forceinline__ void tn_split3(float x, float y, uint32_t w[3]) {
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
-    const float hx = tn_bf16_round(x), hy = tn_bf16_round(y);
-    w[q] = (__float_as_uint(hx) >> 16) | (__float_as_uint(hy) & 0xFFFF0000u);
-    x -= hx;
-    y -= hy;
+    uint32_t h;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(y), "f"(x));
+    w[q] = h;
+    if (q < 2) {
+      x -= __uint_as_float(h << 16);
+      y -= __uint_as_float(h & 0xFFFF0000u);
+    }
   }
 }
 
@@ -124,6 +122,37 @@ __device__ __forceinline__ void store_out4(const OutDesc &o, int64_t t_stride, i
   double2 *b = reinterpret_cast<double2 *>(o.p) + item * t_stride + off;
 #pragma unroll
   for (int j = 0; j < 4; ++j) b[j] = make_double2(v[2 * j], v[2 * j + 1]);
+}
+
+// columns n .. n + len - 1 of a step land on consecutive output offsets, in order
+__device__ __forceinline__ bool tn_contig(const int32_t *ocol, int64_t n, int len) {
+  const int32_t o = ocol[n];
+  bool ok = true;
+#pragma unroll
+  for (int i = 1; i < len; ++i) ok = ok && ocol[n + i] == o + i;
+  return ok;
+}
+
+// The 16 fp32 results v (eight complex columns n0 .. n0 + 7 of one row, ro its row offset) of a
+// tensor-core epilogue into the next step's layout: one eight-wide store when the eight columns
+// are consecutive there, else four-wide stores for consecutive groups of four, else one by one.
+__device__ __forceinline__ void store_cols8(const OutDesc &o, int64_t t_stride, int64_t item, int64_t ro,
+                                            const int32_t *ocol, int64_t n0, int64_t N, const float v[16]) {
+  if (n0 + 7 < N && tn_contig(ocol, n0, 8)) {
+    store_out8(o, t_stride, item, ro + ocol[n0], v);
+    return;
+  }
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int64_t nb = n0 + 4 * h;
+    if (nb + 3 < N && tn_contig(ocol, nb, 4)) {
+      store_out4(o, t_stride, item, ro + ocol[nb], v + 8 * h);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (nb + j < N) store_out(o, t_stride, item, ro + ocol[nb + j], make_float2(v[8 * h + 2 * j], v[8 * h + 2 * j + 1]));
+    }
+  }
 }
 
 // ---- overlap elements and item context (shared by the formation, SIMT and TMA kernels)

@@ -125,15 +125,26 @@ struct tn_plan {
 
 // Kernel of one contraction step: a SimtVariant (SIMT, complex FMA), tcgen05 with the operand split in
 // the kernel, or TMA-fed tcgen05 (BF16x6) with a shape-picked or fixed tile width, building the
-// overlap operand in shared memory (SK_TMA*) or loading it after a formation pass (SK_TMAF*).
+// overlap operand in shared memory (SK_TMA*), loading it after a formation pass (SK_TMAF*), or
+// splitting its complex64 form on chip, one tile per CTA (SK_TMAC*) or persistent (SK_TMAP*).
 enum StepKernel {
   SK_TC = 16,
   SK_TMA = 32, SK_TMA128 = 33, SK_TMA64 = 34,     // B built from the node tensors in shared memory
   SK_TMAF = 40, SK_TMAF128 = 41, SK_TMAF64 = 42,  // B pieces formed in HBM, loaded by TMA
-  SK_TMAC = 48, SK_TMAC128 = 49, SK_TMAC64 = 50   // B formed in HBM as complex64, split on chip
+  SK_TMAC = 48, SK_TMAC128 = 49, SK_TMAC64 = 50,  // B formed in HBM as complex64, split on chip
+  SK_TMAP = 56, SK_TMAP128 = 57, SK_TMAP64 = 58,  // the same, one persistent CTA per SM
+  SK_TMAPA = 64, SK_TMAPA128 = 65, SK_TMAPA64 = 66,  // persistent, A read as complex64 and split on chip too
+  SK_TMAPF = 72, SK_TMAPF128 = 73, SK_TMAPF64 = 74,  // persistent, A and B pieces by TMA (B formed in HBM,
+                                                     // once per slice for a ket tensor)
+  SK_TMAPFA = 80, SK_TMAPFA128 = 81, SK_TMAPFA64 = 82  // persistent, A complex64 split on chip, B pieces by TMA
 };
-inline bool sk_is_tma(int k) { return k >= SK_TMA && k <= SK_TMAC64 && (k & 7) <= 2; }
-inline int sk_tma_bmode(int k) { return k >= SK_TMAC ? 2 : k >= SK_TMAF ? 0 : 1; }
+inline bool sk_is_tma(int k) { return k >= SK_TMA && k <= SK_TMAPFA64 && (k & 7) <= 2; }
+inline bool sk_tma_persist(int k) { return sk_is_tma(k) && k >= SK_TMAP; }
+// the kernel reads its input as complex64 and splits it on chip
+inline bool sk_tma_c64a(int k) { return sk_is_tma(k) && ((k >= SK_TMAPA && k < SK_TMAPF) || k >= SK_TMAPFA); }
+// the kernel reads its input as the bf16 pieces its producer writes (else as complex64)
+inline bool sk_reads_pieces(int k) { return sk_is_tma(k) && !sk_tma_c64a(k); }
+inline int sk_tma_bmode(int k) { return k >= SK_TMAPF ? 0 : k >= SK_TMAC ? 2 : k >= SK_TMAF ? 0 : 1; }
 inline int sk_tma_bn(int k) { return (k & 7) == 1 ? 128 : (k & 7) == 2 ? 64 : 0; }
 std::vector<int> step_kernels(const tn_plan *p, tn_precision prec);
 bool step_kernel_ok(const StepParams &s, tn_precision prec, int k);
@@ -172,6 +183,11 @@ tn_status run_half(const Half &h, int n_qubits, double2 *base, int items, const 
                    int *rank_out_dev, const double2 *init_vec_dev, int64_t item_stride = 0);
 
 // tracing: events around launches, attributed to a kernel kind
+// the contraction step whose launches the ProfScopes of this thread belong to, while it lives
+struct ProfStep {
+  explicit ProfStep(int step);
+  ~ProfStep();
+};
 struct ProfScope {
   int slot = -1;
   cudaStream_t st = 0;

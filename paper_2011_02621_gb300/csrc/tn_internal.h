@@ -135,7 +135,7 @@ cudaError_t launch_step(const StepParams &s, const ContractArgs &a, const void *
 // SIMT step kernels: the shape heuristic or one kernel forced (the autotuner's candidates)
 enum SimtVariant { SIMT_AUTO = 0, SIMT_T64 = 1, SIMT_T128 = 2, SIMT_T256 = 3, SIMT_STREAM = 4, SIMT_FIXED = 5,
                    SIMT_SMALL = 6, SIMT_NARROW = 7, SIMT_BOX = 8 };
-bool simt_variant_ok(const StepParams &s, int variant);
+bool simt_variant_ok(const StepParams &s, int variant, bool fp64);
 // the box-tiled streaming step (stream.cu): thin steps with K * N <= TN_BOX_MAXKN, N <= TN_BOX_MAXN
 #define TN_BOX_MAXKN 4096
 #define TN_BOX_MAXN 256
@@ -160,12 +160,14 @@ cudaError_t launch_form_b_pieces(const StepParams &s, const ContractArgs &a, con
                                  const Pieces &B, cudaStream_t st);
 // TMA-fed tcgen05 step (BF16x6) from pre-split A and B pieces
 // bn: output tile width in real columns (128 or 64; 0 picks by shape). The B operand: with cbuf
-// (the overlap tensor as complex64 [N][K] per item, c_stride elements apart, from
-// launch_form_c) the kernel splits it in shared memory; else with ket and bra (the complex64
-// node tensors) it builds it in shared memory; else it loads B, formed by launch_form_b_pieces.
+// (the overlap tensor as complex64 [N][K], c_stride elements apart, from launch_form_c; item i
+// reads copy i % c_items, c_items 0 meaning one copy per item) the kernel splits it in shared
+// memory; else with ket and bra (the complex64 node tensors) it builds it in shared memory; else
+// it loads B, formed by launch_form_b_pieces.
 cudaError_t launch_step_tma(const StepParams &s, const ContractArgs &a, const Pieces &A, const Pieces &B,
                             const OutDesc &out, int *err, cudaStream_t st, int bn = 0, const float2 *ket = nullptr,
-                            const float2 *bra = nullptr, const float2 *cbuf = nullptr, int64_t c_stride = 0);
+                            const float2 *bra = nullptr, const float2 *cbuf = nullptr, int64_t c_stride = 0,
+                            int64_t c_items = 0);
 bool tma_step_supported(const StepParams &s);
 // Long contractions on the TMA-fed BF16x6 step take 64-column tiles: the tensor core adds its
 // products into an FP32 accumulator with truncation, so the error grows with the number of MMAs

@@ -7,8 +7,10 @@
 // operand built on chip from the node tensors, formed in HBM as complex64 and split on chip, or
 // formed in HBM as bf16 pieces and loaded. The shape
 // heuristic picks one; the autotuner times every kernel that supports the step on the plan's own
-// workspace, at the batch size given, and keeps the fastest. The heuristic's kernel is kept unless
-// another is at least 3% faster. Choices are stored in the plan per precision and used by every
+// workspace, at the batch size given, and keeps the fastest. Most TMA-fed kernels read their input
+// as bf16 pieces, which the previous step then has to write: each candidate is charged the
+// previous step's time in the output format it implies; a second pass then re-picks each step's kernel in
+// its final output format. The heuristic's kernel is kept unless another is at least 3% faster. Choices are stored in the plan per precision and used by every
 // later tn_amplitudes, tn_amplitudes_static, server and batch call on that plan. A workspace the
 // tuner had to allocate is released before it returns.
 #include <algorithm>
@@ -20,7 +22,8 @@ namespace {
 
 const int kCandidates[] = {SIMT_AUTO, SIMT_T64,  SIMT_T128, SIMT_T256, SIMT_STREAM, SIMT_FIXED, SIMT_SMALL, SIMT_NARROW, SIMT_BOX, SK_TC,
                            SK_TMA,    SK_TMA128, SK_TMA64,  SK_TMAF,   SK_TMAF128,  SK_TMAF64,  SK_TMAC,    SK_TMAC128,
-                           SK_TMAC64};
+                           SK_TMAC64, SK_TMAP,   SK_TMAP128, SK_TMAP64,  SK_TMAPA,    SK_TMAPA128, SK_TMAPA64,
+                           SK_TMAPF,  SK_TMAPF128, SK_TMAPF64, SK_TMAPFA, SK_TMAPFA128, SK_TMAPFA64};
 
 struct Events {
   cudaEvent_t a = nullptr, b = nullptr;
@@ -80,45 +83,80 @@ extern "C" tn_status tn_autotune(tn_plan *p, tn_precision prec, int64_t n_bits, 
   const int64_t cap = (int64_t)w.chunk * w.slice_chunk;
   Events ev;
   if (!ev.a || !ev.b) return tn_fail(TN_ERR_CUDA, "tn_autotune: cudaEventCreate failed");
-  for (size_t j = 1; j < p->steps.size(); ++j) {
-    const StepParams &sp = p->steps[j];
+  // one step's launch time with kernel k, writing its output in format fmt (0 complex64, 1 the
+  // bf16 pieces a TMA-fed consumer reads): one untimed launch, then enough for about 0.5 ms
+  auto time_of = [&](size_t j, int k, int fmt, float &ms) -> tn_status {
     OutDesc od;
     od.p = w.t1.p;
-    od.fmt = (j + 1 < ks.size() && sk_is_tma(ks[j + 1])) ? 1 : 0;
+    od.fmt = fmt;
     od.plane_u32 = cap * p->maxT;
-    auto time_of = [&](int k, float &ms) -> tn_status {
-      // one untimed launch, then enough launches for about half a millisecond
-      ms = 0;
-      cudaError_t e = cudaSuccess;
-      for (int rep = 0, r = 1; rep < 2; ++rep) {
-        CUDA_TRY(cudaEventRecord(ev.a, st));
-        const void *kj, *bj;
-        ContractArgs aj;
-        step_operands(p, j, kind, ket, bra, a, kj, bj, aj);
-        for (int i = 0; i < r && e == cudaSuccess; ++i)
-          e = enqueue_step(p, w, j, k, prec, aj, kj, bj, w.t0.p, w.t1.p, od, st);
-        if (e != cudaSuccess) {
-          cudaStreamSynchronize(st);
-          return tn_fail(TN_ERR_CUDA, "step %zu kernel %d: %s", j, k, cudaGetErrorString(e));
-        }
-        CUDA_TRY(cudaEventRecord(ev.b, st));
-        CUDA_TRY(cudaEventSynchronize(ev.b));
-        float t = 0;
-        CUDA_TRY(cudaEventElapsedTime(&t, ev.a, ev.b));
-        ms = t / (float)r;
-        r = std::max(1, std::min(50, (int)(0.5f / std::max(ms, 1e-4f))));
+    ms = 0;
+    cudaError_t e = cudaSuccess;
+    for (int rep = 0, r = 1; rep < 2; ++rep) {
+      CUDA_TRY(cudaEventRecord(ev.a, st));
+      const void *kj, *bj;
+      ContractArgs aj;
+      step_operands(p, j, kind, ket, bra, a, kj, bj, aj);
+      for (int i = 0; i < r && e == cudaSuccess; ++i)
+        e = enqueue_step(p, w, j, k, prec, aj, kj, bj, w.t0.p, w.t1.p, od, st);
+      if (e != cudaSuccess) {
+        cudaStreamSynchronize(st);
+        return tn_fail(TN_ERR_CUDA, "step %zu kernel %d: %s", j, k, cudaGetErrorString(e));
       }
-      return TN_OK;
-    };
+      CUDA_TRY(cudaEventRecord(ev.b, st));
+      CUDA_TRY(cudaEventSynchronize(ev.b));
+      float t = 0;
+      CUDA_TRY(cudaEventElapsedTime(&t, ev.a, ev.b));
+      ms = t / (float)r;
+      r = std::max(1, std::min(50, (int)(0.5f / std::max(ms, 1e-4f))));
+    }
+    return TN_OK;
+  };
+  for (size_t j = 1; j < p->steps.size(); ++j) {
+    const StepParams &sp = p->steps[j];
+    const int fmt = (j + 1 < ks.size() && sk_reads_pieces(ks[j + 1])) ? 1 : 0;
+    // a kernel here that reads bf16 pieces makes the previous step write them: each candidate is
+    // charged the previous step's time (its chosen kernel) in the output format it implies
+    float prev_ms[2] = {0, 0};
+    if (j >= 2 && prec == TN_BF16X6) {
+      for (int f = 0; f < 2; ++f) {
+        tn_status ts = time_of(j - 1, ks[j - 1], f, prev_ms[f]);
+        if (ts != TN_OK) return ts;
+      }
+    }
     const int dflt = ks[j];
     float best_ms = 0;
-    tn_status ts = time_of(dflt, best_ms);
+    tn_status ts = time_of(j, dflt, fmt, best_ms);
     if (ts != TN_OK) return ts;
+    best_ms += prev_ms[sk_reads_pieces(dflt) ? 1 : 0];
     int best = dflt;
     for (int k : kCandidates) {
       if (k == dflt || !step_kernel_ok(sp, prec, k)) continue;
       float ms = 0;
-      ts = time_of(k, ms);
+      ts = time_of(j, k, fmt, ms);
+      if (ts != TN_OK) return ts;
+      ms += prev_ms[sk_reads_pieces(k) ? 1 : 0];
+      if (ms < 0.97f * best_ms) {
+        best_ms = ms;
+        best = k;
+      }
+    }
+    ks[j] = best;
+  }
+  // second pass: each step's output format is now final (it follows the next step's choice), so
+  // its kernel is chosen again in that format among those that read their input in the same format
+  for (size_t j = 1; j < p->steps.size() && prec == TN_BF16X6; ++j) {
+    const StepParams &sp = p->steps[j];
+    const int fmt = (j + 1 < ks.size() && sk_reads_pieces(ks[j + 1])) ? 1 : 0;
+    const bool pieces = sk_reads_pieces(ks[j]);
+    float best_ms = 0;
+    tn_status ts = time_of(j, ks[j], fmt, best_ms);
+    if (ts != TN_OK) return ts;
+    int best = ks[j];
+    for (int k : kCandidates) {
+      if (k == ks[j] || sk_reads_pieces(k) != pieces || !step_kernel_ok(sp, prec, k)) continue;
+      float ms = 0;
+      ts = time_of(j, k, fmt, ms);
       if (ts != TN_OK) return ts;
       if (ms < 0.97f * best_ms) {
         best_ms = ms;

@@ -152,8 +152,10 @@ def tn_launch_count(reset: bool = False) -> int:
     return int(LIB.tn_launch_count(1 if reset else 0))
 
 
-def tn_profile_enable(on: bool = True):
-    _check(LIB.tn_profile_enable(1 if on else 0))
+def tn_profile_enable(on: bool = True, per_step: bool = False):
+    """Start (clearing the records) or stop per-kernel tracing; per_step keeps one record per kind
+    and contraction step, named "<kind>#<step>"."""
+    _check(LIB.tn_profile_enable((2 if per_step else 1) if on else 0))
 
 
 def tn_profile_read() -> dict:
@@ -646,7 +648,12 @@ KERNEL_NAMES = {0: "simt_auto", 1: "simt_tile64x64", 2: "simt_tile128x16", 3: "s
                 16: "tcgen05_split",
                 32: "tcgen05_tma_buildb", 33: "tcgen05_tma_buildb_bn128", 34: "tcgen05_tma_buildb_bn64",
                 40: "tcgen05_tma_loadb", 41: "tcgen05_tma_loadb_bn128", 42: "tcgen05_tma_loadb_bn64",
-                48: "tcgen05_tma", 49: "tcgen05_tma_bn128", 50: "tcgen05_tma_bn64"}
+                48: "tcgen05_tma", 49: "tcgen05_tma_bn128", 50: "tcgen05_tma_bn64",
+                56: "tcgen05_tma_persist", 57: "tcgen05_tma_persist_bn128", 58: "tcgen05_tma_persist_bn64",
+                64: "tcgen05_persist_c64", 65: "tcgen05_persist_c64_bn128", 66: "tcgen05_persist_c64_bn64",
+                72: "tcgen05_persist_loadb", 73: "tcgen05_persist_loadb_bn128", 74: "tcgen05_persist_loadb_bn64",
+                80: "tcgen05_persist_c64_loadb", 81: "tcgen05_persist_c64_loadb_bn128",
+                82: "tcgen05_persist_c64_loadb_bn64"}
 KERNEL_IDS = {v: k for k, v in KERNEL_NAMES.items()}
 
 
