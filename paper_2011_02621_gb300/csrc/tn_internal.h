@@ -47,8 +47,9 @@ cudaError_t launch_init_product(double2 *base, int64_t item_stride, int items, c
                                 int n_qubits, const uint64_t *bits, int words, const double2 *init_vec,
                                 cudaStream_t st);
 // rank_out (nullable): item 0 writes the numerical rank of its SVD there
+// fp32: the SVD arithmetic in FP32 (the node tensors stay FP64 in memory), for the complex64 forms
 cudaError_t launch_gate(const GateParams &g, double2 *base, int64_t item_stride, int items,
-                        double2 *gwork, int *errflag, int *rank_out, cudaStream_t st);
+                        double2 *gwork, int *errflag, int *rank_out, cudaStream_t st, bool fp32 = false);
 cudaError_t launch_apply1(const Apply1Params &a, double2 *base, int64_t item_stride, int items, cudaStream_t st);
 cudaError_t launch_to_c64(const double2 *src, float2 *dst, int64_t n, cudaStream_t st);
 
@@ -67,6 +68,7 @@ struct MergeParams {
   int64_t su[TN_MERGE_MAXLEGS], sv[TN_MERGE_MAXLEGS];   // their strides in U and V
 };
 cudaError_t launch_merge(const MergeParams &m, double2 *base, int64_t item_stride, int64_t items, cudaStream_t st);
+cudaError_t launch_merge(const MergeParams &m, float2 *base, int64_t item_stride, int64_t items, cudaStream_t st);
 cudaError_t launch_pack_bits(const uint64_t *src, uint64_t *dst, int64_t n_words, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
