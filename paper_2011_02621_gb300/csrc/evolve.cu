@@ -17,23 +17,6 @@ __device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 c) {  // a
   return make_double2(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
 }
 __device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-__device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 c) {
-  return make_float2(fmaf(a.x, b.x, fmaf(-a.y, b.y, c.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, c.y)));
-}
-__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
-template <typename R> struct CplxOf;
-template <> struct CplxOf<double> { using T = double2; };
-template <> struct CplxOf<float> { using T = float2; };
-template <typename V> __device__ __forceinline__ V mkc(double x, double y) {
-  V v;
-  v.x = (decltype(v.x))x;
-  v.y = (decltype(v.y))y;
-  return v;
-}
-template <typename V, typename W> __device__ __forceinline__ V cvt(W w) { return mkc<V>(w.x, w.y); }
 
 // Row-major view of a node tensor [sigma, legs...] with one distinguished leg `pos`.
 struct NodeView {
@@ -112,12 +95,10 @@ __device__ __forceinline__ double group_sum(double x) {
   return x;
 }
 
-template <int TPI, typename R>
+template <int TPI>
 __global__ void __launch_bounds__(GATE_THREADS) gate_kernel(GateParams g, double2 *base, int64_t item_stride,
                                                             double2 *gwork, int *errflag, int items, int *rank_out) {
-  using V = typename CplxOf<R>::T;
-  extern __shared__ __align__(16) unsigned char gate_smem_raw[];
-  V *smem = reinterpret_cast<V *>(gate_smem_raw);
+  extern __shared__ double2 smem[];
   constexpr bool SUB = TPI <= 32;                 // items within one warp (no block-wide barrier)
   constexpr int GPB = GATE_THREADS / TPI;         // items per block
   const int grp = threadIdx.x / TPI;
@@ -131,9 +112,9 @@ __global__ void __launch_bounds__(GATE_THREADS) gate_kernel(GateParams g, double
   const bool valid = item < items;
   double2 *A = base + (int64_t)(valid ? item : items - 1) * item_stride;
   const WorkLayout L = work_layout(g);
-  V *work = g.use_smem ? smem + (int64_t)grp * L.total : reinterpret_cast<V *>(gwork) + (int64_t)item * g.work_stride;
-  V *Y = work + L.y, *Xo = work + L.xo, *W = work + L.w, *Vp = work + L.vp;
-  R *sig = reinterpret_cast<R *>(work + L.sig);
+  double2 *work = g.use_smem ? smem + (int64_t)grp * L.total : gwork + (int64_t)item * g.work_stride;
+  double2 *Y = work + L.y, *Xo = work + L.xo, *W = work + L.w, *Vp = work + L.vp;
+  double *sig = reinterpret_cast<double *>(work + L.sig);
   int *rank = reinterpret_cast<int *>(work + L.rank);
   int *colof = rank + C_of(L);   // inverse of rank (the rank slots hold 4 ints per column)
 
@@ -159,8 +140,8 @@ __global__ void __launch_bounds__(GATE_THREADS) gate_kernel(GateParams g, double
       int64_t o = r % O;
       int a = c / chi_o, s = c % chi_o;
       int64_t off = other_offset(v, o) + (int64_t)a * v.stride[v.pos];
-      const double2 xd = cfma(Pm[(sp * 2 + 1) * 4 + s], An[off + v.sig], cmul(Pm[(sp * 2 + 0) * 4 + s], An[off]));
-      const V x = cvt<V>(xd);
+      double2 x = cmul(Pm[(sp * 2 + 0) * 4 + s], An[off]);
+      x = cfma(Pm[(sp * 2 + 1) * 4 + s], An[off + v.sig], x);
       if (is_sv) {
         if (!ytrans) Y[(int64_t)c * m + r] = x;              // Y = X, column-major
         else Y[(int64_t)r * n + c] = cconj(x);               // Y = X^H, column-major
@@ -169,10 +150,10 @@ __global__ void __launch_bounds__(GATE_THREADS) gate_kernel(GateParams g, double
       }
     }
   }
-  const int RR = L.R, C = L.C;
+  const int R = L.R, C = L.C;
   for (int64_t idx = tid; idx < (int64_t)C * C; idx += TPI) {
     int i = (int)(idx % C), j = (int)(idx / C);
-    W[idx] = mkc<V>(i == j ? 1.0 : 0.0, 0.0);
+    W[idx] = make_double2(i == j ? 1.0 : 0.0, 0.0);
   }
   item_sync<TPI>();
 
@@ -183,13 +164,13 @@ __global__ void __launch_bounds__(GATE_THREADS) gate_kernel(GateParams g, double
   // are left alone, and a sweep counts as unconverged only for a rotation above 8 tol, so the
   // iteration ends on rounding-dominated pairs (exactly degenerate spectra are common here).
   __shared__ int s_rot_a[GPB];
-  __shared__ R s_fro_a[GPB];
-  __shared__ R s_part_a[GPB][TPI >= 32 ? TPI / 32 : 1];
+  __shared__ double s_fro_a[GPB];
+  __shared__ double s_part_a[GPB][TPI >= 32 ? TPI / 32 : 1];
   int &s_rot = s_rot_a[grp];
-  R &s_fro = s_fro_a[grp];
-  R *s_part = s_part_a[grp];
+  double &s_fro = s_fro_a[grp];
+  double *s_part = s_part_a[grp];
   {
-    R f = 0;
+    double f = 0;
     for (int64_t idx = tid; idx < (int64_t)L.R * L.C; idx += TPI) f = fma(Y[idx].x, Y[idx].x, fma(Y[idx].y, Y[idx].y, f));
     if constexpr (SUB) {
       f = group_sum<TPI>(f);
@@ -199,17 +180,17 @@ __global__ void __launch_bounds__(GATE_THREADS) gate_kernel(GateParams g, double
       if (lane == 0) s_part[warp] = f;
       item_sync<TPI>();
       if (tid == 0) {
-        R t = 0;
+        double t = 0;
         for (int w = 0; w < TPI / 32; ++w) t += s_part[w];
         s_fro = t;
       }
     }
     item_sync<TPI>();
   }
-  const R eps = sizeof(R) == 8 ? (R)2.220446049250313e-16 : (R)1.1920928955078125e-07;   // unit roundoff x 2
-  const R tol = (R)2 * sqrt((R)L.R) * eps;
-  const R floor_ab = (R)1e-30 * s_fro;
-  const R floor_col = (R)16 * (R)L.R * eps * eps * s_fro;
+  const double eps = 2.220446049250313e-16;
+  const double tol = 2.0 * sqrt((double)L.R) * eps;
+  const double floor_ab = 1e-30 * s_fro;
+  const double floor_col = 16.0 * (double)L.R * eps * eps * s_fro;
   const int Cp = (C + 1) & ~1;
   const int rounds = Cp - 1;
   bool converged = (C <= 1);
@@ -235,11 +216,11 @@ __global__ void __launch_bounds__(GATE_THREADS) gate_kernel(GateParams g, double
           if (pi == 0) { p = rd; q = Cp - 1; }
           else { p = (rd + pi) % (Cp - 1); q = (rd - pi + (Cp - 1)) % (Cp - 1); }
           const bool act = pi < npairs && p < C && q < C;
-          V *yp = Y + (int64_t)p * RR, *yq = Y + (int64_t)q * RR;
-          R al = 0, be = 0, gr = 0, gi = 0;
+          double2 *yp = Y + (int64_t)p * R, *yq = Y + (int64_t)q * R;
+          double al = 0, be = 0, gr = 0, gi = 0;
           if (act) {
-            for (int r = sub; r < RR; r += LP) {
-              V a = yp[r], b = yq[r];
+            for (int r = sub; r < R; r += LP) {
+              double2 a = yp[r], b = yq[r];
               al = fma(a.x, a.x, fma(a.y, a.y, al));
               be = fma(b.x, b.x, fma(b.y, b.y, be));
               gr = fma(a.x, b.x, fma(a.y, b.y, gr));    // conj(a) * b
@@ -253,23 +234,23 @@ __global__ void __launch_bounds__(GATE_THREADS) gate_kernel(GateParams g, double
             gi += __shfl_xor_sync(0xffffffffu, gi, o);
           }
           if (!act) continue;
-          const R ga = sqrt(gr * gr + gi * gi);
-          const R nab = sqrt(al * be);
+          const double ga = sqrt(gr * gr + gi * gi);
+          const double nab = sqrt(al * be);
           if (!(ga > tol * nab) || nab <= floor_ab || ga == 0.0 || fmin(al, be) <= floor_col) continue;
-          const R zeta = (be - al) / ((R)2 * ga);
-          const R t = (zeta >= 0 ? (R)1 : (R)-1) / (fabs(zeta) + sqrt((R)1 + zeta * zeta));
-          const R cs = (R)1 / sqrt((R)1 + t * t), sn = cs * t;
-          const V e = mkc<V>(gr / ga, -gi / ga);       // conj(gamma)/|gamma|
-          for (int r = sub; r < RR; r += LP) {
-            V a = yp[r], b = cmul(yq[r], e);
-            yp[r] = mkc<V>(cs * a.x - sn * b.x, cs * a.y - sn * b.y);
-            yq[r] = mkc<V>(sn * a.x + cs * b.x, sn * a.y + cs * b.y);
+          const double zeta = (be - al) / (2.0 * ga);
+          const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
+          const double2 e = make_double2(gr / ga, -gi / ga);       // conj(gamma)/|gamma|
+          for (int r = sub; r < R; r += LP) {
+            double2 a = yp[r], b = cmul(yq[r], e);
+            yp[r] = make_double2(cs * a.x - sn * b.x, cs * a.y - sn * b.y);
+            yq[r] = make_double2(sn * a.x + cs * b.x, sn * a.y + cs * b.y);
           }
-          V *wp = W + (int64_t)p * C, *wq = W + (int64_t)q * C;
+          double2 *wp = W + (int64_t)p * C, *wq = W + (int64_t)q * C;
           for (int r = sub; r < C; r += LP) {
-            V a = wp[r], b = cmul(wq[r], e);
-            wp[r] = mkc<V>(cs * a.x - sn * b.x, cs * a.y - sn * b.y);
-            wq[r] = mkc<V>(sn * a.x + cs * b.x, sn * a.y + cs * b.y);
+            double2 a = wp[r], b = cmul(wq[r], e);
+            wp[r] = make_double2(cs * a.x - sn * b.x, cs * a.y - sn * b.y);
+            wq[r] = make_double2(sn * a.x + cs * b.x, sn * a.y + cs * b.y);
           }
           if (sub == 0 && ga > 8.0 * tol * nab) s_rot = 1;
         }
@@ -279,10 +260,10 @@ __global__ void __launch_bounds__(GATE_THREADS) gate_kernel(GateParams g, double
         if (pi == 0) { p = rd; q = Cp - 1; }
         else { p = (rd + pi) % (Cp - 1); q = (rd - pi + (Cp - 1)) % (Cp - 1); }
         if (p >= C || q >= C) continue;
-        V *yp = Y + (int64_t)p * RR, *yq = Y + (int64_t)q * RR;
-        R al = 0, be = 0, gr = 0, gi = 0;
-        for (int r = lane; r < RR; r += 32) {
-          V a = yp[r], b = yq[r];
+        double2 *yp = Y + (int64_t)p * R, *yq = Y + (int64_t)q * R;
+        double al = 0, be = 0, gr = 0, gi = 0;
+        for (int r = lane; r < R; r += 32) {
+          double2 a = yp[r], b = yq[r];
           al = fma(a.x, a.x, fma(a.y, a.y, al));
           be = fma(b.x, b.x, fma(b.y, b.y, be));
           gr = fma(a.x, b.x, fma(a.y, b.y, gr));    // conj(a) * b
@@ -294,23 +275,23 @@ __global__ void __launch_bounds__(GATE_THREADS) gate_kernel(GateParams g, double
           gr += __shfl_xor_sync(0xffffffffu, gr, o);
           gi += __shfl_xor_sync(0xffffffffu, gi, o);
         }
-        const R ga = sqrt(gr * gr + gi * gi);
-        const R nab = sqrt(al * be);
+        double ga = sqrt(gr * gr + gi * gi);
+        const double nab = sqrt(al * be);
         if (!(ga > tol * nab) || nab <= floor_ab || ga == 0.0 || fmin(al, be) <= floor_col) continue;
-        const R zeta = (be - al) / ((R)2 * ga);
-        const R t = (zeta >= 0 ? (R)1 : (R)-1) / (fabs(zeta) + sqrt((R)1 + zeta * zeta));
-        const R cs = (R)1 / sqrt((R)1 + t * t), sn = cs * t;
-        const V e = mkc<V>(gr / ga, -gi / ga);       // conj(gamma)/|gamma|
-        for (int r = lane; r < RR; r += 32) {
-          V a = yp[r], b = cmul(yq[r], e);
-          yp[r] = mkc<V>(cs * a.x - sn * b.x, cs * a.y - sn * b.y);
-          yq[r] = mkc<V>(sn * a.x + cs * b.x, sn * a.y + cs * b.y);
+        double zeta = (be - al) / (2.0 * ga);
+        double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
+        double2 e = make_double2(gr / ga, -gi / ga);       // conj(gamma)/|gamma|
+        for (int r = lane; r < R; r += 32) {
+          double2 a = yp[r], b = cmul(yq[r], e);
+          yp[r] = make_double2(cs * a.x - sn * b.x, cs * a.y - sn * b.y);
+          yq[r] = make_double2(sn * a.x + cs * b.x, sn * a.y + cs * b.y);
         }
-        V *wp = W + (int64_t)p * C, *wq = W + (int64_t)q * C;
+        double2 *wp = W + (int64_t)p * C, *wq = W + (int64_t)q * C;
         for (int r = lane; r < C; r += 32) {
-          V a = wp[r], b = cmul(wq[r], e);
-          wp[r] = mkc<V>(cs * a.x - sn * b.x, cs * a.y - sn * b.y);
-          wq[r] = mkc<V>(sn * a.x + cs * b.x, sn * a.y + cs * b.y);
+          double2 a = wp[r], b = cmul(wq[r], e);
+          wp[r] = make_double2(cs * a.x - sn * b.x, cs * a.y - sn * b.y);
+          wq[r] = make_double2(sn * a.x + cs * b.x, sn * a.y + cs * b.y);
         }
         if (lane == 0 && ga > 8.0 * tol * nab) s_rot = 1;
       }
@@ -325,36 +306,36 @@ __global__ void __launch_bounds__(GATE_THREADS) gate_kernel(GateParams g, double
   // ---- singular values, descending ranks, truncation count
   if constexpr (SUB) {
     for (int j = 0; j < C; ++j) {
-      const V *yj = Y + (int64_t)j * RR;
-      R s2 = 0;
-      for (int r = tid; r < RR; r += TPI) s2 = fma(yj[r].x, yj[r].x, fma(yj[r].y, yj[r].y, s2));
+      const double2 *yj = Y + (int64_t)j * R;
+      double s2 = 0;
+      for (int r = tid; r < R; r += TPI) s2 = fma(yj[r].x, yj[r].x, fma(yj[r].y, yj[r].y, s2));
       s2 = group_sum<TPI>(s2);
       if (tid == 0) sig[j] = sqrt(s2);
     }
   } else {
     for (int j = warp; j < C; j += nwarp) {
-      const V *yj = Y + (int64_t)j * RR;
-      R s2 = 0;
-      for (int r = lane; r < RR; r += 32) s2 = fma(yj[r].x, yj[r].x, fma(yj[r].y, yj[r].y, s2));
+      const double2 *yj = Y + (int64_t)j * R;
+      double s2 = 0;
+      for (int r = lane; r < R; r += 32) s2 = fma(yj[r].x, yj[r].x, fma(yj[r].y, yj[r].y, s2));
       for (int o = 16; o; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
       if (lane == 0) sig[j] = sqrt(s2);
     }
   }
   item_sync<TPI>();
-  __shared__ R s_max_a[GPB];
+  __shared__ double s_max_a[GPB];
   __shared__ int s_keep_a[GPB];
-  R &s_max = s_max_a[grp];
+  double &s_max = s_max_a[grp];
   int &s_keep = s_keep_a[grp];
   if (tid == 0) {
-    R mx = 0;
+    double mx = 0;
     for (int j = 0; j < C; ++j) mx = fmax(mx, sig[j]);
     int kc = 0;
-    for (int j = 0; j < C; ++j) kc += (sig[j] > (R)g.cutoff * mx) ? 1 : 0;
+    for (int j = 0; j < C; ++j) kc += (sig[j] > g.cutoff * mx) ? 1 : 0;
     s_max = mx;
     s_keep = kc < g.dout ? kc : g.dout;
     if (rank_out && item == 0 && valid) {
       // numerical rank: singular values above the rounding level of the column norms
-      const R thr = (R)4 * sqrt((R)RR) * eps * mx;
+      const double thr = 4.0 * sqrt((double)R) * 2.220446049250313e-16 * mx;
       int nr = 0;
       for (int j = 0; j < C; ++j) nr += (sig[j] > thr) ? 1 : 0;
       *rank_out = nr;
@@ -371,15 +352,15 @@ __global__ void __launch_bounds__(GATE_THREADS) gate_kernel(GateParams g, double
   const int dout = g.dout;
 
   // ---- V' = S V^H rows (dout x n), zero beyond keep
-  for (int64_t idx = tid; idx < (int64_t)dout * n; idx += TPI) Vp[idx] = mkc<V>(0, 0);
+  for (int64_t idx = tid; idx < (int64_t)dout * n; idx += TPI) Vp[idx] = make_double2(0, 0);
   item_sync<TPI>();
   for (int j = 0; j < C; ++j) {
     int t = rank[j];
     if (t >= keep) continue;
     for (int c = tid; c < n; c += TPI) {
-      V v;
-      if (!ytrans) { V w = W[(int64_t)j * C + c]; v = mkc<V>(sig[j] * w.x, -sig[j] * w.y); }
-      else { v = cconj(Y[(int64_t)j * RR + c]); }
+      double2 v;
+      if (!ytrans) { double2 w = W[(int64_t)j * C + c]; v = make_double2(sig[j] * w.x, -sig[j] * w.y); }
+      else { v = cconj(Y[(int64_t)j * R + c]); }
       Vp[(int64_t)t * n + c] = v;
     }
   }
@@ -395,20 +376,20 @@ __global__ void __launch_bounds__(GATE_THREADS) gate_kernel(GateParams g, double
     const int64_t total = (int64_t)m * dout;
     for (int64_t idx = tid; idx < total; idx += TPI) {
       int r = (int)(idx / dout), t = (int)(idx % dout);
-      V u = mkc<V>(0, 0);
+      double2 u = make_double2(0, 0);
       if (t < keep) {
         const int j = colof[t];
         if (!ytrans) {
-          V y = Y[(int64_t)j * RR + r];
-          R inv = sig[j] > 0 ? (R)1 / sig[j] : (R)0;
-          u = mkc<V>(y.x * inv, y.y * inv);
+          double2 y = Y[(int64_t)j * R + r];
+          double inv = sig[j] > 0 ? 1.0 / sig[j] : 0.0;
+          u = make_double2(y.x * inv, y.y * inv);
         } else {
           u = W[(int64_t)j * C + r];
         }
       }
       int sp = (int)(r / O);
       int64_t o = r % O;
-      if (valid) An[sp * nv.sig + other_offset(nv, o) + (int64_t)t * nv.stride[nv.pos]] = cvt<double2>(u);
+      if (valid) An[sp * nv.sig + other_offset(nv, o) + (int64_t)t * nv.stride[nv.pos]] = u;
     }
   }
   item_sync<TPI>();
@@ -424,12 +405,12 @@ __global__ void __launch_bounds__(GATE_THREADS) gate_kernel(GateParams g, double
     const int64_t total = (int64_t)m * dout;
     for (int64_t idx = tid; idx < total; idx += TPI) {
       int r = (int)(idx / dout), t = (int)(idx % dout);
-      V acc = mkc<V>(0, 0);
-      const V *xr = Xo + (int64_t)r * n, *vt = Vp + (int64_t)t * n;
+      double2 acc = make_double2(0, 0);
+      const double2 *xr = Xo + (int64_t)r * n, *vt = Vp + (int64_t)t * n;
       for (int c = 0; c < n; ++c) acc = cfma(xr[c], vt[c], acc);
       int sp = (int)(r / O);
       int64_t o = r % O;
-      if (valid) An[sp * nv.sig + other_offset(nv, o) + (int64_t)t * nv.stride[nv.pos]] = cvt<double2>(acc);
+      if (valid) An[sp * nv.sig + other_offset(nv, o) + (int64_t)t * nv.stride[nv.pos]] = acc;
     }
   }
 }
@@ -478,24 +459,25 @@ int64_t gate_work_elems(const GateParams &g) { return work_layout(g).total; }
 
 namespace {
 
-template <int TPI, typename R>
+template <int TPI>
 cudaError_t launch_items_per_warp(const GateParams &g, const WorkLayout &L, double2 *base, int64_t item_stride,
                                   int items, double2 *gwork, int *errflag, int *rank_out, cudaStream_t st) {
   constexpr int GPB = GATE_THREADS / TPI;
-  const size_t smem = (size_t)GPB * L.total * sizeof(typename CplxOf<R>::T);
+  const size_t smem = (size_t)GPB * L.total * sizeof(double2);
   if (smem > 48 * 1024) {
-    const int lim = tn_smem_optin<gate_kernel<TPI, R>>();
+    const int lim = tn_smem_optin<gate_kernel<TPI>>();
     if (lim < 0 || (size_t)lim < smem) return cudaErrorInvalidValue;
   }
-  gate_kernel<TPI, R><<<(items + GPB - 1) / GPB, GATE_THREADS, smem, st>>>(g, base, item_stride, gwork, errflag,
-                                                                           items, rank_out);
+  gate_kernel<TPI><<<(items + GPB - 1) / GPB, GATE_THREADS, smem, st>>>(g, base, item_stride, gwork, errflag, items,
+                                                                        rank_out);
   tn_count_launch(1);
   return cudaGetLastError();
 }
 
-template <typename R>
-cudaError_t launch_gate_t(const GateParams &g, double2 *base, int64_t item_stride, int items, double2 *gwork,
-                          int *errflag, int *rank_out, cudaStream_t st) {
+}  // namespace
+
+cudaError_t launch_gate(const GateParams &g, double2 *base, int64_t item_stride, int items, double2 *gwork,
+                        int *errflag, int *rank_out, cudaStream_t st) {
   if (items <= 0) return cudaSuccess;
   const WorkLayout L = work_layout(g);
   // small matrices: items inside one warp, as many lanes each as a Jacobi round's pairs cover
@@ -507,28 +489,20 @@ cudaError_t launch_gate_t(const GateParams &g, double2 *base, int64_t item_strid
     while (tpi < 32 && tpi < npairs * L.R) tpi <<= 1;
     while (tpi < 32 && (size_t)(GATE_THREADS / tpi) * L.total * sizeof(double2) > 96 * 1024) tpi <<= 1;
     switch (tpi) {
-      case 4: return launch_items_per_warp<4, R>(g, L, base, item_stride, items, gwork, errflag, rank_out, st);
-      case 8: return launch_items_per_warp<8, R>(g, L, base, item_stride, items, gwork, errflag, rank_out, st);
-      case 16: return launch_items_per_warp<16, R>(g, L, base, item_stride, items, gwork, errflag, rank_out, st);
-      default: return launch_items_per_warp<32, R>(g, L, base, item_stride, items, gwork, errflag, rank_out, st);
+      case 4: return launch_items_per_warp<4>(g, L, base, item_stride, items, gwork, errflag, rank_out, st);
+      case 8: return launch_items_per_warp<8>(g, L, base, item_stride, items, gwork, errflag, rank_out, st);
+      case 16: return launch_items_per_warp<16>(g, L, base, item_stride, items, gwork, errflag, rank_out, st);
+      default: return launch_items_per_warp<32>(g, L, base, item_stride, items, gwork, errflag, rank_out, st);
     }
   }
-  const size_t smem = g.use_smem ? (size_t)L.total * sizeof(typename CplxOf<R>::T) : 0;
+  const size_t smem = g.use_smem ? (size_t)L.total * sizeof(double2) : 0;
   if (smem > 48 * 1024) {
-    const int lim = tn_smem_optin<gate_kernel<128, R>>();
+    const int lim = tn_smem_optin<gate_kernel<128>>();
     if (lim < 0 || (size_t)lim < smem) return cudaErrorInvalidValue;
   }
-  gate_kernel<128, R><<<items, GATE_THREADS, smem, st>>>(g, base, item_stride, gwork, errflag, items, rank_out);
+  gate_kernel<128><<<items, GATE_THREADS, smem, st>>>(g, base, item_stride, gwork, errflag, items, rank_out);
   tn_count_launch(1);
   return cudaGetLastError();
-}
-
-}  // namespace
-
-cudaError_t launch_gate(const GateParams &g, double2 *base, int64_t item_stride, int items, double2 *gwork,
-                        int *errflag, int *rank_out, cudaStream_t st, bool fp32) {
-  return fp32 ? launch_gate_t<float>(g, base, item_stride, items, gwork, errflag, rank_out, st)
-              : launch_gate_t<double>(g, base, item_stride, items, gwork, errflag, rank_out, st);
 }
 
 cudaError_t launch_init_product(double2 *base, int64_t item_stride, int items, const int64_t *node_off_dev,
@@ -572,7 +546,9 @@ __global__ void merge_kernel(MergeParams m, V2 *base, int64_t item_stride, int64
   iu += (r / m.pv) * m.su_p;
   const V2 *U = base + item * item_stride + m.u_off + iu;
   const V2 *V = base + item * item_stride + m.v_off + iv;
-  V2 acc = mkc<V2>(0.0, 0.0);
+  V2 acc;
+  acc.x = 0;
+  acc.y = 0;
   for (int x = 0; x < m.da; ++x) {
     const V2 u = U[x * m.su_a], v = V[x * m.sv_a];
     acc.x = fma(u.x, v.x, fma(-u.y, v.y, acc.x));

@@ -575,15 +575,8 @@ static double gate_flops(const GateParams &g) {
 
 tn_status run_half(const Half &h, int n_qubits, double2 *base, int items, const int64_t *node_off_dev,
                    const uint64_t *bits_dev, int words, double2 *gwork, int *errflag, cudaStream_t st,
-                   int *rank_out_dev, const double2 *init_vec_dev, int64_t item_stride, bool fp32) {
+                   int *rank_out_dev, const double2 *init_vec_dev, int64_t item_stride) {
   const int64_t stride = item_stride > 0 ? item_stride : h.item_elems;
-  // FP32 arithmetic only where no bond bound cuts into a spectrum (every singular value that can
-  // be nonzero is kept unless it falls below the cutoff): where chi caps a bond, the kept subspace
-  // depends on the singular values near the cap, and the FP32 rounding of the gates before it
-  // would move that subspace
-  bool capped = false;
-  for (const GateParams &g : h.gp) capped = capped || g.dout < std::min(g.sv_is_k ? g.m_k : g.m_l, g.n);
-  const bool use32 = fp32 && !capped;
   {
     ProfScope ps("init_product", st, 32.0 * items * n_qubits, 0);
     CUDA_TRY(launch_init_product(base, stride, items, node_off_dev, n_qubits, bits_dev, words, init_vec_dev, st));
@@ -592,9 +585,9 @@ tn_status run_half(const Half &h, int n_qubits, double2 *base, int items, const 
     if (op.first == 2) {
       GateParams g = h.gp[op.second];
       g.max_sweeps = h.max_sweeps;
-      ProfScope ps(use32 ? "gate_svd_fp32" : "gate_svd_fp64", st, gate_bytes(g) * items, gate_flops(g) * items);
+      ProfScope ps("gate_svd_fp64", st, gate_bytes(g) * items, gate_flops(g) * items);
       CUDA_TRY(launch_gate(g, base, stride, items, gwork, errflag, rank_out_dev ? rank_out_dev + op.second : nullptr,
-                           st, use32));
+                           st));
     } else {
       const Apply1Params &a = h.ap[op.second];
       ProfScope ps("apply_1q_fp64", st, 64.0 * a.size_rest * items, 16.0 * a.size_rest * items);
@@ -2622,10 +2615,8 @@ tn_status enqueue_chunk(tn_plan *p, Workspace &w, const uint64_t *bits_dev, int6
     return TN_OK;
   }
   const Net &g = p->net;
-  // the complex64 forms (FP32-level products throughout their contraction) decompose the bra's
-  // matrices in FP32 when chi caps no bond; the FP64 form in FP64
   tn_status s = run_half(c->bra, c->n, (double2 *)w.bra64.p, (int)nb, (const int64_t *)c->bra_off_dev.p, bits_dev,
-                         words, (double2 *)w.gwork.p, (int *)w.err.p, st, nullptr, nullptr, g.bra_elems, kind != 0);
+                         words, (double2 *)w.gwork.p, (int *)w.err.p, st, nullptr, nullptr, g.bra_elems);
   if (s != TN_OK) return s;
   if (g.merged()) {
     // merged nodes: the ket's once per batch (one item) in FP64; the bra's per bitstring, in FP64

@@ -180,7 +180,7 @@ tn_status run_amplitudes(tn_plan *p, Workspace &w, const uint64_t *bits, int64_t
                          tn_c128 *out, cudaStream_t st, int64_t slice_begin = 0, int64_t slice_end = -1);
 tn_status run_half(const Half &h, int n_qubits, double2 *base, int items, const int64_t *node_off_dev,
                    const uint64_t *bits_dev, int words, double2 *gwork, int *errflag, cudaStream_t st,
-                   int *rank_out_dev, const double2 *init_vec_dev, int64_t item_stride = 0, bool fp32 = false);
+                   int *rank_out_dev, const double2 *init_vec_dev, int64_t item_stride = 0);
 
 // tracing: events around launches, attributed to a kernel kind
 // the contraction step whose launches the ProfScopes of this thread belong to, while it lives

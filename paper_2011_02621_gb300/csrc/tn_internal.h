@@ -47,9 +47,8 @@ cudaError_t launch_init_product(double2 *base, int64_t item_stride, int items, c
                                 int n_qubits, const uint64_t *bits, int words, const double2 *init_vec,
                                 cudaStream_t st);
 // rank_out (nullable): item 0 writes the numerical rank of its SVD there
-// fp32: the SVD arithmetic in FP32 (the node tensors stay FP64 in memory), for the complex64 forms
 cudaError_t launch_gate(const GateParams &g, double2 *base, int64_t item_stride, int items,
-                        double2 *gwork, int *errflag, int *rank_out, cudaStream_t st, bool fp32 = false);
+                        double2 *gwork, int *errflag, int *rank_out, cudaStream_t st);
 cudaError_t launch_apply1(const Apply1Params &a, double2 *base, int64_t item_stride, int items, cudaStream_t st);
 cudaError_t launch_to_c64(const double2 *src, float2 *dst, int64_t n, cudaStream_t st);
 
