@@ -542,6 +542,8 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="serving stream length (0: skip)")
     ap.add_argument("--serve", action="store_true", help="serving comparison only: BF16x6 vs FP64 (one line)")
     ap.add_argument("--no-tune", action="store_true", help="keep the shape heuristic's step kernels")
+    ap.add_argument("--force-kernel", action="append", default=[], metavar="STEP=NAME",
+                    help="with --profile-only: run plan step STEP (index of tn_plan_details) on kernel NAME")
     ap.add_argument("--mem-gib", type=float, default=96.0, help="device memory budget of the plan's batches")
     ap.add_argument("--no-batch", action="store_true", help="skip the 32-circuit batched-graph measurement")
     ap.add_argument("--no-two-sided", action="store_true", help="skip the two-sided compression section")
@@ -589,6 +591,14 @@ def main():
     plan = tn.tn_path(c, layers=1 if overlap_only else 2, mem_budget_bytes=args.mem_gib * 2 ** 30)
     info = plan.info
     tuned = None if args.no_tune else tn.tn_autotune(plan, args.prec, B, stream=stream)
+    if args.force_kernel:
+        if not args.profile_only:
+            raise SystemExit("--force-kernel is a profiling option (with --profile-only)")
+        ks = tn.tn_plan_kernels(plan, args.prec)
+        for fk in args.force_kernel:
+            i, name = fk.split("=", 1)
+            ks[int(i)] = name
+        tn.tn_plan_set_kernels(plan, args.prec, ks)
     bits_dev = torch.from_numpy(packed.view(np.int64).copy()).cuda()
     out_dev = torch.empty(B, dtype=torch.complex128, device="cuda")
     bits_pin = torch.from_numpy(packed.view(np.int64).copy()).pin_memory()
