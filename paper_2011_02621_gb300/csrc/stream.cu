@@ -165,6 +165,7 @@ step_box_kernel(StepParams s, ContractArgs a, const typename BoxT<R>::V *ket, co
         const V *xr0 = Ins + r * L.kp;
         const V *xr1 = two ? xr0 + RP * L.kp : xr0;
         const V *cc = Cs + g * TN;
+#pragma unroll 4
         for (int k = 0; k < K; ++k) {
           const V x0 = xr0[k], x1 = xr1[k];
           V cv[TN];
