@@ -329,21 +329,31 @@ tn_status tn_amplitudes_static(tn_plan *p, const uint64_t *bits, int64_t n, tn_p
  * 0 shape heuristic (SIMT), 1-3 SIMT tiles 64x64 / 128x16 / 256x4 (rows x columns),
  * 4 SIMT streaming (K, N <= 16), 5 SIMT streaming with K and N fixed at compile time,
  * 6 SIMT one-CTA-per-item reduction (small outputs), 7 SIMT few-rows kernel (M <= 16, M*K <= 2048,
- * one thread per output column), 16 tcgen05 with the operand split in the
- * kernel (TF32, TF32x3, BF16x3, TF32x6), and the TMA-fed tcgen05 kernels (BF16x6), each with the
- * tile picked by shape / 128-column / 64-column tiles: 32 / 33 / 34 building the overlap operand
- * in shared memory from the node tensors, 40 / 41 / 42 loading it as bf16 pieces formed in HBM,
- * 48 / 49 / 50 reading it as complex64 formed in HBM and splitting it on chip. The paper has
- * no counterpart: which
+ * one thread per output column), 8 SIMT box-tiled streaming step (K*N <= 4096, N <= 256, the plan's
+ * row tiles), 16 tcgen05 with the operand split in the kernel (TF32, TF32x3, BF16x3, TF32x6), and
+ * the TMA-fed tcgen05 kernels (BF16x6), each with the tile picked by shape / 128-column /
+ * 64-column tiles: 32 / 33 / 34 building the overlap operand in shared memory from the node
+ * tensors, 40 / 41 / 42 loading it as bf16 pieces formed in HBM, 48 / 49 / 50 reading it as
+ * complex64 formed in HBM and splitting it on chip; the persistent forms (one CTA per SM walking
+ * the output tiles, K < 256): 56 / 57 / 58 as 48-50, 64 / 65 / 66 the same with the step's input
+ * read as complex64 and split on chip (the previous step then writes complex64, not bf16 pieces),
+ * 72 / 73 / 74 with the operand as bf16 pieces formed in HBM (once per slice for a ket tensor),
+ * 80 / 81 / 82 the same with the input read as complex64. The paper has no counterpart: which
  * kernel runs a pairwise contraction is an implementation choice that changes no result beyond
  * rounding. */
-enum { TN_KERNEL_SIMT = 0, TN_KERNEL_TC = 16, TN_KERNEL_TMA = 32, TN_KERNEL_TMA128 = 33, TN_KERNEL_TMA64 = 34,
-       TN_KERNEL_TMA_LOADB = 40, TN_KERNEL_TMA_LOADB128 = 41, TN_KERNEL_TMA_LOADB64 = 42,
-       TN_KERNEL_TMA_C64B = 48, TN_KERNEL_TMA_C64B128 = 49, TN_KERNEL_TMA_C64B64 = 50 };
+enum { TN_KERNEL_SIMT = 0, TN_KERNEL_SIMT_BOX = 8, TN_KERNEL_TC = 16, TN_KERNEL_TMA = 32, TN_KERNEL_TMA128 = 33,
+       TN_KERNEL_TMA64 = 34, TN_KERNEL_TMA_LOADB = 40, TN_KERNEL_TMA_LOADB128 = 41, TN_KERNEL_TMA_LOADB64 = 42,
+       TN_KERNEL_TMA_C64B = 48, TN_KERNEL_TMA_C64B128 = 49, TN_KERNEL_TMA_C64B64 = 50,
+       TN_KERNEL_PERSIST = 56, TN_KERNEL_PERSIST128 = 57, TN_KERNEL_PERSIST64 = 58,
+       TN_KERNEL_PERSIST_C64 = 64, TN_KERNEL_PERSIST_C64_128 = 65, TN_KERNEL_PERSIST_C64_64 = 66,
+       TN_KERNEL_PERSIST_LOADB = 72, TN_KERNEL_PERSIST_LOADB128 = 73, TN_KERNEL_PERSIST_LOADB64 = 74,
+       TN_KERNEL_PERSIST_C64_LOADB = 80, TN_KERNEL_PERSIST_C64_LOADB128 = 81, TN_KERNEL_PERSIST_C64_LOADB64 = 82 };
 
 /* Time every kernel that supports each contraction step of the plan in precision `prec`, on the
  * plan's workspace with a batch of min(n_bits, chunk) bitstrings (n_bits = 0: the full chunk),
  * and keep the fastest per step (the shape heuristic's kernel unless another is >= 3% faster).
+ * A kernel that reads its input as bf16 pieces is charged the previous step's time writing them;
+ * a second pass re-picks each step in its final output format.
  * The choice is stored in the plan for `prec` and used by every later amplitude, server and batch
  * call on it. kernels (may be NULL): info.n_steps entries, the chosen kernel per step.
  * Synchronises the stream. Errors: TN_ERR_ARG, TN_ERR_STATE, TN_ERR_CUDA, TN_ERR_OOM, TN_ERR_TIMEOUT. */
