@@ -2100,8 +2100,10 @@ static tn_status plan_host(tn_circuit *c, const tn_path_opts &o, tn_plan *p) {
   for (int kind = 0; kind < 2; ++kind) {
     // as many whole bitstrings (all slices) as fit; else one bitstring and groups of its slices
     const int64_t grid_cap = 1LL << 40;   // items * maxT bound keeping every launch grid < 2^31 CTAs
-    int64_t per = plan_ws_bytes(p, kind, 1, p->n_slices);
-    int64_t ch = (int64_t)std::floor(budget / (double)per);
+    // the workspace is a fixed part (the merged ket, flags) plus a part per bitstring
+    const int64_t fixed = plan_ws_bytes(p, kind, 0, p->n_slices);
+    const int64_t per = plan_ws_bytes(p, kind, 1, p->n_slices) - fixed;
+    int64_t ch = (int64_t)std::floor((budget - (double)fixed) / (double)per);
     ch = std::min<int64_t>(ch, 1 << 16);
     while (ch > 1 && ch * p->n_slices * std::max<int64_t>(p->maxT, 1) >= grid_cap) ch /= 2;
     int64_t sc = p->n_slices;
