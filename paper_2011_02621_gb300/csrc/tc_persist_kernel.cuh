@@ -3,25 +3,28 @@
 // The arithmetic is that of the one-tile-per-CTA step kernel: the same operand pieces, the same
 // six products x_i*y_j (i + j <= 2) per 16-real K slice with order 0 spread round-robin over R
 // accumulators and orders 1 and 2 in one more, and the same smallest-first sum in the
-// epilogue, so both kernels give the same bits. What changes is the schedule. Each CTA walks
-// the tiles blockIdx.x, blockIdx.x + gridDim.x, ... (item-major, then 128-row block, then
-// BN-column block) with four roles in separate warps:
-//   warp 0     TMA producer: the A pieces (and in BM 0 the B pieces) of every 64-real K chunk
-//              of every tile into a ring of S shared-memory stages; the ring continues across
-//              tile boundaries, so the next tile's operands load while this one finishes;
+// epilogue; with the same R (128-column tiles, K > 64) both kernels give the same bits. What
+// changes is the schedule. Each CTA walks the tiles blockIdx.x, blockIdx.x + gridDim.x, ...
+// (item-major, then 128-row block, then BN-column block) with roles in separate warps:
+//   warp 0     TMA producer: per 64-real K chunk of every tile, the pieces that come by TMA (the
+//              A pieces unless the input is read as complex64, the B pieces in BM 0) into a
+//              ring of S shared-memory stages, and in the complex64-input form (AC) the
+//              input's box of fp32 pairs (128 rows x 32 complex) into a separate raw ring; the
+//              rings continue across tile boundaries, so the next tile's operands load while
+//              this one finishes;
 //   warp 1     MMA issuer: tcgen05.mma into accumulator set (tile number mod NBUF); before a
 //              tile it waits until the epilogue has drained that set ("tempty"), after it it
 //              commits to "tfull";
-//   warps 2-5  B builders (BM 2): read the overlap tensor as complex64 [N][K], split it into
-//              bf16 pieces and store them swizzled into each stage;
-//   warps 6-9  epilogue: wait "tfull", read the accumulators with tcgen05.ld (warp w reads TMEM
-//              lanes 32 * (w mod 4) ..), sum, store into the next step's layout, arrive "tempty".
-// In the complex64-A form (AC) the producer loads the step's input as complex64 (fp32 pairs, a
-// 128-row x 32-complex box per K chunk) into a separate raw ring; warps 6-9 split it into the
-// three bf16 pieces and store them swizzled into the stage like the B builders (the epilogue moves
-// to warps 10-13). The pieces are those the previous step's epilogue would have written in the
-// pre-split format, so both forms give the same bits, and the previous step writes plain
-// complex64 (8 bytes per value instead of 12).
+//   B builders (BM 2, four warps from warp 2): read the overlap operand as complex64 [N][K],
+//              split it into bf16 pieces and store them swizzled into each stage;
+//   A builders (AC: four warps after the B builders, or eight from warp 2 in BM 0): take the
+//              raw box into registers, hand it back, split it into the three pieces and store
+//              them swizzled into the stage (the pieces the previous step's epilogue would have
+//              written in the pre-split format, so both forms give the same bits, and the
+//              previous step writes 8 bytes per value instead of 12);
+//   the last four warps, epilogue: wait "tfull", read the accumulators with tcgen05.ld (warp w
+//              reads TMEM lanes 32 * (w mod 4) ..), sum, store into the next step's layout,
+//              arrive "tempty".
 // With NBUF = 2 (64-column tiles: 2 x 4 x 64 TMEM columns; 128-column tiles of a short K, one
 // order-0 accumulator: 2 x 2 x 128) the MMAs of one tile run while the epilogue drains the
 // previous one; with NBUF = 1 (128-column tiles of a longer K, all 512 columns) the MMAs wait
