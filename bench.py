@@ -488,7 +488,9 @@ def two_sided_run(tn, np, torch, w, packed, idx, a64, prec, steps, warmup, flush
     B = len(packed)
     c2 = tn.tn_build(w.graph.n, w.graph.edges, w.gates)
     tn.tn_evolve_two_sided(c2, w.split, w.chi, w.cutoff, compress="two_sided")
-    p2 = tn.tn_path(c2, layers=2, mem_budget_bytes=mem_gib * 2 ** 30)
+    # the headline plan keeps its workspace (all 65536 bitstrings in one batch) meanwhile: this
+    # plan gets half the budget and runs the batch in two
+    p2 = tn.tn_path(c2, layers=2, mem_budget_bytes=min(mem_gib, 48.0) * 2 ** 30)
     rms = float(np.sqrt(np.mean(np.abs(a64) ** 2)))
     d64 = tn.tn_amplitudes(p2, packed[idx], "fp64")
     bits_dev = torch.from_numpy(packed.view(np.int64).copy()).cuda()
