@@ -446,3 +446,21 @@ def test_planning_failures_are_statuses_not_exceptions(tn):
     with pytest.raises(tn.TNError) as e:
         tn.tn_plan_estimate(c, w.split, 0, 1e-12)
     assert e.value.status == tn.TN_ERR_UNSUPPORTED and "slices" in str(e.value)
+
+
+@pytest.mark.parametrize("gib", [0.5, 2.0, 8.0])
+def test_batch_size_fills_the_budget(tn, gib):
+    """The plan's device batch is the largest number of bitstrings whose workspace (a fixed part,
+    the merged ket, plus a part per bitstring) fits the budget: the reported workspace fits, one
+    bitstring more would not (unless the 65536 cap binds), and the fixed part is counted once."""
+    w = gen.workload("syc53", n_bits=1)
+    c = tn.tn_build(w.graph.n, w.graph.edges, w.gates, allocator=None)
+    budget = gib * 2 ** 30
+    info = tn.tn_plan_estimate(c, w.split, w.chi, w.cutoff, layers=2, mem_budget_bytes=budget)
+    ch, ws = info["chunk_bitstrings"], info["workspace_bytes"]
+    assert 1 <= ch <= 65536 and ws <= budget
+    small = tn.tn_plan_estimate(c, w.split, w.chi, w.cutoff, layers=2, mem_budget_bytes=2 ** 26)
+    per = (ws - small["workspace_bytes"]) / (ch - small["chunk_bitstrings"])   # one bitstring's share
+    fixed = ws - ch * per
+    assert fixed > 0 and per > 0
+    assert ch == 65536 or fixed + (ch + 1) * per > budget
