@@ -233,7 +233,8 @@ tn_status tn_circuit_bond_dims(const tn_circuit *c, int32_t side, int32_t *out);
  * every bitstring) or one bra tensor. Unless opts->no_merge, partial paths are then joined
  * (supplement, the discussion of Assumption 3): where the path absorbs two tensors of the same
  * layer in a row that share one edge not cut, the pair is contracted with each other first
- * (exactly, in FP64: ket pairs once per batch, bra pairs per bitstring) and absorbed in one step,
+ * (ket pairs once per batch in FP64; bra pairs per bitstring, in FP64 for TN_FP64 and in FP32
+ * for the complex64 precisions, whose contraction carries FP32-level products) and absorbed in one step,
  * when that lowers both the complex multiply-adds and the elements the steps read and write; the
  * amplitudes are the same sums grouped otherwise and no intermediate grows. Explicit cut_edges
  * are not accepted (TN_ERR_UNSUPPORTED); automatic cuts are. The path search holds at most 256 nodes, so the
